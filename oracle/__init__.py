@@ -1,0 +1,150 @@
+"""CPU oracle for the irradiance-matrix hot path (paper Sec. III-B and IV-C).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this package; the product package never does.
+It shares no code with the CUDA library.
+
+Contents
+  irradiance(...)       FP64 brute-force E_ij, per-source visibility and grazing
+                        flags (C, uvc_oracle.c), Eq. (7) and its visibility rule
+  lbvh.*                Morton codes, stable key sort, binary radix tree and
+                        bounding boxes by their definitions (Python/numpy)
+  fluence(A, t)         mu = A^T t in FP64 (Eq. (5))
+  coverage(mu, area..)  area-weighted fraction of patches with mu >= mu_min
+
+Every function here is pinned by tests in tests/test_oracle_*.py against closed
+forms, invariants and brute force; see the module docstrings for which.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "uvc_oracle.c")
+_LIB = os.path.join(_HERE, "libuvc_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def load_library(path: str):
+    """ctypes handle on a compiled copy of uvc_oracle.c."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    lib.uvco_irradiance.argtypes = [P, i64, P, i64, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
+                                    ctypes.c_double, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
+    lib.uvco_irradiance.restype = ctypes.c_int
+    lib.uvco_max_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = load_library(build())
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().uvco_max_threads())
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def grazing_eps(verts, rel: float = 1e-7) -> float:
+    """Grazing distance: rel times the diagonal of the mesh's bounding box."""
+    v = np.asarray(verts, np.float64).reshape(-1, 3)
+    if v.shape[0] == 0:
+        return 0.0
+    return rel * float(np.linalg.norm(v.max(axis=0) - v.min(axis=0)))
+
+
+def irradiance(verts, tris, centroid, normal, excl, cand, offsets, weights, power,
+               pairs=None, eps=None, flags=True, threads=0, lib=None):
+    """FP64 brute-force irradiance.
+
+    pairs: None for the full (nc, np) matrix, else an (npairs, 2) array of (i, j).
+    Returns (E, vis, flag): E float64 (nc,np) or (npairs,), vis uint8 (..., K),
+    flag uint8 grazing bits (or None when flags=False).
+    lib: an alternative compiled copy (load_library), default the built oracle.
+    """
+    lib = lib or _load()
+    verts = _c(verts, np.float32).reshape(-1, 3)
+    tris = _c(tris, np.int32).reshape(-1, 3)
+    centroid = _c(centroid, np.float32).reshape(-1, 3)
+    normal = _c(normal, np.float32).reshape(-1, 3)
+    excl = _c(excl, np.int32).reshape(-1, 2)
+    cand = _c(cand, np.float32).reshape(-1, 3)
+    offsets = _c(offsets, np.float32).reshape(-1, 3)
+    weights = _c(weights, np.float32).reshape(-1)
+    K = offsets.shape[0]
+    assert weights.shape[0] == K
+    nc, np_ = cand.shape[0], centroid.shape[0]
+    if pairs is None:
+        shape = (nc, np_)
+        npairs = nc * np_
+        pp = None
+    else:
+        pp = _c(pairs, np.int64).reshape(-1, 2)
+        npairs = pp.shape[0]
+        shape = (npairs,)
+    if eps is None:
+        eps = grazing_eps(verts)
+    E = np.zeros(npairs, np.float64)
+    vis = np.zeros(npairs * K, np.uint8)
+    flag = np.zeros(npairs, np.uint8) if flags else None
+    ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    rc = lib.uvco_irradiance(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0],
+                             ptr(centroid), ptr(normal), ptr(excl), np_, ptr(cand), nc,
+                             ptr(offsets), ptr(weights), K, float(power),
+                             ptr(pp), npairs, float(eps), ptr(E), ptr(vis), ptr(flag), int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle: invalid input (rc={rc})")
+    E = E.reshape(shape)
+    vis = vis.reshape(shape + (K,))
+    if flag is not None:
+        flag = flag.reshape(shape)
+    return E, vis, flag
+
+
+def irradiance_scene(scene, pairs=None, **kw):
+    """irradiance() on a synth.Scene."""
+    L = scene.lamp
+    return irradiance(scene.verts, scene.tris, scene.centroid, scene.normal, scene.excl,
+                      scene.cand, L.offsets, L.weights, L.power, pairs=pairs, **kw)
+
+
+def fluence(A, t):
+    """mu[v, j] = sum_i t[v, i] A[i, j] in FP64 (Eq. (5): fluence is the dwell-
+    time weighted sum of the irradiance columns)."""
+    A = np.asarray(A, np.float64)
+    t = np.atleast_2d(np.asarray(t, np.float64))
+    return t @ A
+
+
+def coverage(mu, area, mu_min):
+    """Fraction of the surface area whose fluence reaches mu_min, per dwell vector,
+    and the fraction of patches doing so.  The threshold test is taken in FP32
+    (mu and mu_min as FP32), the sums in FP64."""
+    mu = np.atleast_2d(np.asarray(mu, np.float32))
+    area = np.asarray(area, np.float32).astype(np.float64)
+    ok = mu >= np.float32(mu_min)
+    total = area.sum()
+    by_area = (ok * area[None, :]).sum(axis=1) / total if total > 0 else np.zeros(mu.shape[0])
+    by_count = ok.sum(axis=1) / max(1, mu.shape[1])
+    return by_area, by_count

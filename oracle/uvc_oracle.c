@@ -1,0 +1,255 @@
+/*
+ * Independent FP64 CPU oracle for the occlusion-tested irradiance matrix.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link, load or
+ * call this file; only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code, header or constant with the
+ * CUDA library and is deliberately plain: every segment is tested against
+ * every triangle (brute force), in double precision.
+ *
+ * What it computes (paper Sec. IV-C, "Discrete Radiative Fluence"):
+ *
+ *   For candidate i, lamp source m and patch j:
+ *     o   = fl32(c_i + off_m)       source point: the FP32 sum, so that both
+ *                                   sides start from the same point
+ *     v   = o - s_j                 from the patch point to the source
+ *     d   = |v|,  cos = <n_j, v>/d  (n_j points into the free space)
+ *     V   = 1 iff cos > 0 and no triangle other than the patch's own (excl)
+ *           meets the open segment {o + tau (s_j - o) : 0 < tau < 1}
+ *           (visibility rule stated under Eq. (7))
+ *     E_ij = sum_m  w_m P <v, n_j> / (4 pi d^3) * V       (Eq. (7), with the
+ *           printed cases read the other way round: the formula applies when
+ *           the patch is visible, zero otherwise; w_m P is the power of
+ *           source m, equal shares for a line lamp, Sec. IV-C "Non-Point
+ *           Light Sources")
+ *
+ *   Grazing flags (pairs where an FP32 implementation may legitimately
+ *   disagree on V); eps is an absolute distance in metres, OR-ed over the
+ *   facing sources of the pair:
+ *     bit 0  the closed segment [o, s_j] passes within eps of an edge of a
+ *            non-excluded triangle
+ *     bit 1  an endpoint (o or s_j) lies within eps of a non-excluded triangle
+ *     bit 2  |<n_j, v>| <= eps (the facing decision is within eps of flipping)
+ *
+ *   The flag tests skip a triangle only when that is exact: a segment whose
+ *   endpoints are both farther than eps from the triangle's plane on the same
+ *   side, or whose distance to the triangle's bounding sphere exceeds eps,
+ *   cannot come within eps of the triangle.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { double x, y, z; } d3;
+
+static d3 v3(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 vsub(d3 a, d3 b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 vadd(d3 a, d3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 vmul(d3 a, double s) { return v3(a.x * s, a.y * s, a.z * s); }
+static double vdot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static d3 vcross(d3 a, d3 b) {
+    return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double vnorm(d3 a) { return sqrt(vdot(a, a)); }
+static double clamp01(double t) { return t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t); }
+
+/* Does the open segment o + tau*dir, 0 < tau < 1, meet the closed triangle
+ * (a,b,c)?  Moller-Trumbore in FP64: solve o + tau dir = a + u e1 + w e2. */
+static int segment_meets_triangle(d3 o, d3 dir, d3 a, d3 b, d3 c) {
+    d3 e1 = vsub(b, a), e2 = vsub(c, a);
+    d3 p = vcross(dir, e2);
+    double det = vdot(e1, p);
+    if (det == 0.0) return 0;            /* segment parallel to the plane */
+    d3 r = vsub(o, a);
+    double u = vdot(r, p) / det;
+    if (u < 0.0 || u > 1.0) return 0;
+    d3 q = vcross(r, e1);
+    double w = vdot(dir, q) / det;
+    if (w < 0.0 || u + w > 1.0) return 0;
+    double tau = vdot(e2, q) / det;
+    return tau > 0.0 && tau < 1.0;
+}
+
+/* Distance between closed segments [p1,q1] and [p2,q2]: minimise
+ * |p1 + s d1 - p2 - t d2| over s,t in [0,1] (clamp the unconstrained optimum
+ * of one parameter, solve for the other, re-clamp). */
+static double segment_segment_distance(d3 p1, d3 q1, d3 p2, d3 q2) {
+    d3 d1 = vsub(q1, p1), d2 = vsub(q2, p2), r = vsub(p1, p2);
+    double a = vdot(d1, d1), e = vdot(d2, d2), f = vdot(d2, r);
+    double s, t;
+    if (a == 0.0 && e == 0.0) return vnorm(r);
+    if (a == 0.0) {
+        s = 0.0;
+        t = clamp01(f / e);
+    } else {
+        double c = vdot(d1, r);
+        if (e == 0.0) {
+            t = 0.0;
+            s = clamp01(-c / a);
+        } else {
+            double b = vdot(d1, d2);
+            double den = a * e - b * b;
+            s = den > 0.0 ? clamp01((b * f - c * e) / den) : 0.0;
+            t = (b * s + f) / e;
+            if (t < 0.0) {
+                t = 0.0;
+                s = clamp01(-c / a);
+            } else if (t > 1.0) {
+                t = 1.0;
+                s = clamp01((b - c) / a);
+            }
+        }
+    }
+    return vnorm(vsub(vadd(p1, vmul(d1, s)), vadd(p2, vmul(d2, t))));
+}
+
+static double point_segment_distance(d3 p, d3 a, d3 b) {
+    d3 ab = vsub(b, a);
+    double L = vdot(ab, ab);
+    double t = L > 0.0 ? clamp01(vdot(vsub(p, a), ab) / L) : 0.0;
+    return vnorm(vsub(p, vadd(a, vmul(ab, t))));
+}
+
+static double point_triangle_distance(d3 p, d3 a, d3 b, d3 c) {
+    d3 n = vcross(vsub(b, a), vsub(c, a));
+    double nn = vdot(n, n);
+    double de = fmin(point_segment_distance(p, a, b),
+                     fmin(point_segment_distance(p, b, c), point_segment_distance(p, c, a)));
+    if (nn == 0.0) return de;
+    double h = vdot(vsub(p, a), n) / nn;
+    d3 pp = vsub(p, vmul(n, h));          /* projection onto the plane */
+    int inside = vdot(vcross(vsub(b, a), vsub(pp, a)), n) >= 0.0 &&
+                 vdot(vcross(vsub(c, b), vsub(pp, b)), n) >= 0.0 &&
+                 vdot(vcross(vsub(a, c), vsub(pp, c)), n) >= 0.0;
+    return inside ? fabs(h) * sqrt(nn) : de;
+}
+
+typedef struct {
+    d3 a, b, c;        /* vertices */
+    d3 n;              /* unit plane normal (zero for degenerate triangles) */
+    d3 center;         /* bounding-sphere centre (vertex mean) */
+    double radius;     /* bounding-sphere radius */
+} tri64;
+
+static int build_tris(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, tri64* T) {
+    for (int64_t t = 0; t < nt; ++t) {
+        int32_t ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv) return -1;
+        T[t].a = v3(verts[3 * ia], verts[3 * ia + 1], verts[3 * ia + 2]);
+        T[t].b = v3(verts[3 * ib], verts[3 * ib + 1], verts[3 * ib + 2]);
+        T[t].c = v3(verts[3 * ic], verts[3 * ic + 1], verts[3 * ic + 2]);
+        d3 n = vcross(vsub(T[t].b, T[t].a), vsub(T[t].c, T[t].a));
+        double nl = vnorm(n);
+        T[t].n = nl > 0.0 ? vmul(n, 1.0 / nl) : v3(0, 0, 0);
+        T[t].center = vmul(vadd(vadd(T[t].a, T[t].b), T[t].c), 1.0 / 3.0);
+        T[t].radius = fmax(vnorm(vsub(T[t].a, T[t].center)),
+                           fmax(vnorm(vsub(T[t].b, T[t].center)), vnorm(vsub(T[t].c, T[t].center))));
+    }
+    return 0;
+}
+
+/* Grazing test of the closed segment [o,s] against one triangle (bits 0,1). */
+static int grazing_bits(const tri64* t, d3 o, d3 s, double eps) {
+    /* exact skip 1: both endpoints farther than eps from the plane, same side */
+    if (t->n.x != 0.0 || t->n.y != 0.0 || t->n.z != 0.0) {
+        double da = vdot(vsub(o, t->a), t->n), db = vdot(vsub(s, t->a), t->n);
+        if ((da > eps && db > eps) || (da < -eps && db < -eps)) return 0;
+    }
+    /* exact skip 2: segment farther than eps from the bounding sphere */
+    if (point_segment_distance(t->center, o, s) > t->radius + eps) return 0;
+    int bits = 0;
+    if (segment_segment_distance(o, s, t->a, t->b) <= eps ||
+        segment_segment_distance(o, s, t->b, t->c) <= eps ||
+        segment_segment_distance(o, s, t->c, t->a) <= eps)
+        bits |= 1;
+    if (point_triangle_distance(o, t->a, t->b, t->c) <= eps ||
+        point_triangle_distance(s, t->a, t->b, t->c) <= eps)
+        bits |= 2;
+    return bits;
+}
+
+/*
+ * Irradiance entries for a list of (candidate, patch) pairs.
+ *   pairs    npairs*2 int64 (i, j); NULL means every pair, i major (k = i*np + j)
+ *   E_out    npairs doubles (W/m^2)
+ *   vis_out  npairs*K bytes (1 = source m sees the patch point), may be NULL
+ *   flag_out npairs bytes of grazing bits, may be NULL (then no flag work)
+ * Returns 0, or -1 on an index out of range.
+ */
+int uvco_irradiance(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const float* centroid, const float* normal, const int32_t* excl, int64_t np,
+                    const float* cand, int64_t nc,
+                    const float* offsets, const float* weights, int32_t K, double power,
+                    const int64_t* pairs, int64_t npairs, double eps,
+                    double* E_out, uint8_t* vis_out, uint8_t* flag_out, int nthreads) {
+    if (K < 1 || nt < 0 || np < 0 || nc < 0) return -1;
+    if (pairs == NULL) npairs = nc * np;
+    for (int64_t j = 0; j < np; ++j)
+        for (int q = 0; q < 2; ++q)
+            if (excl[2 * j + q] < -1 || excl[2 * j + q] >= nt) return -1;
+    if (pairs != NULL)
+        for (int64_t k = 0; k < npairs; ++k)
+            if (pairs[2 * k] < 0 || pairs[2 * k] >= nc || pairs[2 * k + 1] < 0 || pairs[2 * k + 1] >= np)
+                return -1;
+    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
+    if (!T) return -2;
+    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
+    const double four_pi = 4.0 * M_PI;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+#endif
+    for (int64_t k = 0; k < npairs; ++k) {
+        int64_t i = pairs ? pairs[2 * k] : k / np;
+        int64_t j = pairs ? pairs[2 * k + 1] : k % np;
+        d3 s = v3(centroid[3 * j], centroid[3 * j + 1], centroid[3 * j + 2]);
+        d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
+        int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
+        double E = 0.0;
+        int flags = 0;
+        for (int m = 0; m < K; ++m) {
+            /* the source point in FP32 (one IEEE single add per coordinate) */
+            float ox = cand[3 * i] + offsets[3 * m];
+            float oy = cand[3 * i + 1] + offsets[3 * m + 1];
+            float oz = cand[3 * i + 2] + offsets[3 * m + 2];
+            d3 o = v3(ox, oy, oz);
+            d3 v = vsub(o, s);
+            double d = vnorm(v);
+            double nv_ = vdot(n, v);
+            int visible = 0;
+            if (flag_out && fabs(nv_) <= eps) flags |= 4;
+            if (nv_ > 0.0 && d > 0.0) {
+                visible = 1;
+                d3 dir = vsub(s, o);
+                for (int64_t t = 0; t < nt; ++t) {
+                    if (t == ex0 || t == ex1) continue;
+                    if (segment_meets_triangle(o, dir, T[t].a, T[t].b, T[t].c)) { visible = 0; break; }
+                }
+                if (flag_out)
+                    for (int64_t t = 0; t < nt; ++t) {
+                        if (t == ex0 || t == ex1) continue;
+                        flags |= grazing_bits(&T[t], o, s, eps);
+                    }
+                if (visible) E += (double)weights[m] * power * nv_ / (four_pi * d * d * d);
+            }
+            if (vis_out) vis_out[k * K + m] = (uint8_t)visible;
+        }
+        E_out[k] = E;
+        if (flag_out) flag_out[k] = (uint8_t)flags;
+    }
+    free(T);
+    return 0;
+}
+
+/* Number of threads an OpenMP region will use (1 without OpenMP). */
+int uvco_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

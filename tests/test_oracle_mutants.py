@@ -1,0 +1,54 @@
+"""Each plausible mistake planted in a copy of the C oracle must be caught by
+at least one pin: evidence that the pins constrain every term of Eq. (7), the
+visibility rule, the source layout and the grazing flags.  Runs on the CPU."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import _pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "uvc_oracle.c")
+
+MUTANTS = {
+    "no_cosine": ("power * nv_ / (four_pi * d * d * d)", "power / (four_pi * d * d)"),
+    "inverse_square_of_d_only": ("(four_pi * d * d * d)", "(four_pi * d * d)"),
+    "two_pi": ("const double four_pi = 4.0 * M_PI;", "const double four_pi = 2.0 * M_PI;"),
+    "ignore_source_weights": ("(double)weights[m] * power", "power"),
+    "facing_sign_flipped": ("if (nv_ > 0.0 && d > 0.0) {", "if (nv_ < 0.0 && d > 0.0) {"),
+    "no_exclusion": ("if (t == ex0 || t == ex1) continue;\n                    if (segment_meets_triangle",
+                     "if (segment_meets_triangle"),
+    "ray_not_segment": ("return tau > 0.0 && tau < 1.0;", "return tau > 0.0;"),
+    "closed_segment": ("return tau > 0.0 && tau < 1.0;", "return tau >= 0.0 && tau <= 1.0;"),
+    "source_in_fp64": ("float ox = cand[3 * i] + offsets[3 * m];",
+                       "double ox = (double)cand[3 * i] + (double)offsets[3 * m] + 1e-9;"),
+    "barycentric_bound": ("if (w < 0.0 || u + w > 1.0) return 0;", "if (w < 0.0 || u + w > 1.5) return 0;"),
+    "edge_flag_lost": ("        bits |= 1;", "        bits |= 0;"),
+    "facing_flag_lost": ("flags |= 4;", "flags |= 0;"),
+    "endpoint_flag_lost": ("        bits |= 2;", "        bits |= 0;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                           str(mutated), "-o", str(so), "-lm"])
+    lib = oracle.load_library(str(so))
+
+    def irr(*a, **kw):
+        return oracle.irradiance(*a, lib=lib, **kw)
+
+    caught = []
+    for pin in _pins.ALL_PINS:
+        try:
+            pin(irr)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"mutant {name} passed every pin"
