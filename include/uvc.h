@@ -1,0 +1,227 @@
+/*
+ * uvc.h - C ABI of the GB300 irradiance-matrix library (libuvc.so).
+ *
+ * The library computes the discrete irradiance matrix of the UV coverage
+ * planner of Correia Marques, Ramalingam, Pan and Hauser, "Optimized
+ * Coverage Planning for UV Surface Disinfection" (arXiv:2103.14137): for
+ * candidate lamp positions x_i and
+ * surface patches j, the irradiance I_j(x_i) of Eq. (4), evaluated by the
+ * inverse-square law of Eq. (7) with its visibility rule, summed over the
+ * point sources of a lamp (Sec. IV-C, "Non-Point Light Sources"); the fluence
+ * mu_j(t) = sum_i I_j(x_i) t_i of Eq. (5); and the covered surface fraction
+ * (the area with mu_j >= mu_min, the constraint of Eq. (8)).
+ *
+ * Conventions shared by every call
+ *   - All array arguments are DEVICE pointers (CUDA global memory of the
+ *     current device), C-contiguous, owned by the caller.  The library never
+ *     writes an input, never frees a caller buffer and keeps no pointer to a
+ *     caller buffer after the call returns (uvc_build_scene copies what it
+ *     needs).
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and runs asynchronously; results are valid once the stream has
+ *     reached that point.  Argument checks happen synchronously on the host.
+ *     uvc_build_scene additionally synchronises `stream` once (it reads the
+ *     tree depth and its validation result back to the host).
+ *   - Every call returns a status code (UVC_OK = 0).  No C++ exception crosses
+ *     the ABI.  Device-side failures (a traversal that exceeded its visit cap)
+ *     are recorded in the scene's status word; uvc_scene_status reads it.
+ *   - Sizes are int64_t; every count must be >= 0 and < 2^31.
+ *   - The GPU path uses FP32 (with error-free transformations where needed);
+ *     it contains no FP64 arithmetic and has no CPU fallback.
+ */
+#ifndef UVC_H
+#define UVC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* uvc_stream_t; /* same type as cudaStream_t */
+
+/* status codes */
+#define UVC_OK 0
+#define UVC_E_INVAL 1    /* bad argument: NULL, negative/oversized count, bad index, NaN */
+#define UVC_E_NOMEM 2    /* device allocation failed */
+#define UVC_E_CUDA 3     /* a CUDA runtime call failed (launch, copy, sync) */
+#define UVC_E_STACK 4    /* traversal stack would overflow (tree deeper than supported) */
+#define UVC_E_TIMEOUT 5  /* a traversal hit its node-visit cap; affected entries are NaN */
+
+#define UVC_MAX_SOURCES 32
+
+/*
+ * A lamp as K point sources (Sec. IV-C, "Non-Point Light Sources": a light
+ * of any shape is approximated by point sources, each emitting a fraction of
+ * the total radiant flux).  Source m of a lamp placed at candidate point c
+ * sits at fl32(c + offsets[m]) (one FP32 add per coordinate) and emits
+ * weight[m] * power watts.  A point lamp is K = 1, offsets = 0, weight = 1.
+ * Host struct, passed by pointer, read during the call only.
+ */
+typedef struct {
+    int32_t K;                            /* 1 <= K <= UVC_MAX_SOURCES */
+    float power;                          /* total radiant flux P in watts, finite, >= 0 */
+    float offsets[UVC_MAX_SOURCES][3];    /* metres, first K used */
+    float weight[UVC_MAX_SOURCES];        /* fractions of P, first K used, finite, >= 0 */
+} uvc_lamp;
+
+/*
+ * Surface patches (Sec. III-B: the surface is a simplicial complex; each
+ * irradiance entry integrates over one patch, Eq. (4)).  The library samples
+ * each patch at one point.  Device pointers, np entries each:
+ *   centroid  float[np][3]  sample point s_j (metres)
+ *   normal    float[np][3]  unit normal n_j pointing INTO the free space
+ *   area      float[np]     patch area (m^2), used by uvc_coverage
+ *   excl      int32[np][2]  triangles the patch lies on; they never occlude
+ *                           their own patch (-1 = unused slot)
+ */
+typedef struct {
+    const float* centroid;
+    const float* normal;
+    const float* area;
+    const int32_t* excl;
+} uvc_patches;
+
+typedef struct uvc_scene uvc_scene; /* opaque; owns its device buffers */
+
+/*
+ * uvc_build_scene - upload the environment and build its bounding-volume
+ * hierarchy (a linear BVH: Morton codes, radix sort, binary radix tree,
+ * bottom-up box refit).  The paper's environment boundary E is the triangle
+ * mesh of Sec. III-B; the hierarchy replaces the paper's rasterised visibility
+ * cube (Sec. IV-C, Fig. 2) as the means of answering "does another surface
+ * lie closer to the source along the ray" (the visibility rule of Eq. (7)).
+ *
+ *   verts  float[nv][3] vertex positions (metres), finite
+ *   tris   int32[nt][3] vertex indices, each in [0, nv)
+ *   patches, np         see uvc_patches; excl entries in [-1, nt)
+ *   out                 receives the new scene (freed with uvc_free_scene)
+ *
+ * nt may be 0 (nothing occludes).  Returns UVC_E_INVAL for NULL pointers,
+ * counts out of range, an index out of range or a non-finite coordinate
+ * (checked on the device, then reported after one stream synchronisation),
+ * UVC_E_NOMEM when device memory runs out.  On error *out is NULL.
+ */
+int uvc_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const uvc_patches* patches, int64_t np, uvc_stream_t stream, uvc_scene** out);
+
+/* uvc_free_scene - release a scene's device buffers (synchronises the device
+ * work that may still use them).  NULL is accepted. */
+int uvc_free_scene(uvc_scene* scene);
+
+/*
+ * uvc_irradiance_matrix - the irradiance matrix (Sec. IV-C, Eq. (4) and (7)):
+ *
+ *   A[i][j] = sum_m  w_m P <o_im - s_j, n_j> / (4 pi |o_im - s_j|^3) * V_ijm
+ *
+ * with o_im = fl32(cand_i + offsets_m), and V_ijm = 1 iff <o_im - s_j, n_j> > 0
+ * and no triangle other than the patch's excl triangles meets the open
+ * segment between o_im and s_j (watertight FP32 segment/triangle test).
+ * The paper prints the two cases of Eq. (7) the other way round; the formula
+ * applies to visible patches.  The matrix is the transpose of the paper's
+ * I_j(x_i): one row per candidate.
+ *
+ *   cand  float[nc][3]  candidate lamp positions (the lamp's reference point)
+ *   lamp  host struct   K sources, see uvc_lamp
+ *   A     float[nc][lda], lda >= np; row i, columns [0, np) are written,
+ *         columns >= np untouched
+ *   vis   uint32[K][nc][ceil(np/32)] or NULL: bit (j % 32) of word
+ *         vis[m][i][j / 32] is V_ijm; bits for j >= np are 0
+ *
+ * nc = 0 or np = 0 is a no-op.  Errors: UVC_E_INVAL (NULL scene/cand/A with
+ * nc*np > 0, K out of range, non-finite lamp data, lda < np), UVC_E_CUDA.
+ */
+int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                          float* A, int64_t lda, uint32_t* vis, uvc_stream_t stream);
+
+/*
+ * uvc_irradiance_counters - the same computation as uvc_irradiance_matrix
+ * (writes A, no visibility words) with traversal instrumentation, for
+ * profiling and for the benchmark's algorithmic byte count; slower than the
+ * plain call because of the counting atomics.  Synchronises `stream`.
+ *   counters  HOST uint64[6]: [0] node visits (per warp packet), [1] leaf
+ *             triangle loads (per warp packet), [2] packet traversals,
+ *             [3] per-segment box tests, [4] per-segment triangle tests,
+ *             [5] facing segments (those that needed a search)
+ * A packet is one warp: 32 patches and one lamp source (Sec. IV-C: each
+ * segment is one source-to-patch visibility query of Eq. (7)).
+ */
+int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                            float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream);
+
+/*
+ * uvc_fluence - fluence of every patch for nvec dwell-time vectors (Eq. (5)):
+ *
+ *   mu[v][j] = sum_i t[v][i] * A[i][j]
+ *
+ *   A   float[nc][lda] as written by uvc_irradiance_matrix (np columns used)
+ *   t   float[nvec][nc] dwell times (seconds)
+ *   mu  float[nvec][np] output (J/m^2)
+ *
+ * FP32 with compensated accumulation.  nvec in [1, 256].  Uses temporary
+ * device memory from the stream-ordered allocator.  Errors: UVC_E_INVAL,
+ * UVC_E_NOMEM, UVC_E_CUDA.
+ */
+int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda, const float* t,
+                int32_t nvec, float* mu, uvc_stream_t stream);
+
+/*
+ * uvc_fluence_streamed - the same mu as uvc_fluence of uvc_irradiance_matrix's
+ * A, without storing A (Eq. (5) with Eq. (7) evaluated on the fly); for
+ * matrices too large to keep.  Candidates are split into chunks whose partial
+ * sums go to temporary device memory (stream-ordered allocator) and are then
+ * added in a fixed order, so the result is deterministic.
+ *   cand, lamp as in uvc_irradiance_matrix; t, nvec, mu as in uvc_fluence.
+ */
+int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                         const float* t, int32_t nvec, float* mu, uvc_stream_t stream);
+
+/*
+ * uvc_coverage - covered fraction of the surface for each dwell vector: the
+ * patches meeting the dose constraint mu_j >= mu_min of Eq. (8) (inclusive),
+ * weighted by area (the "disinfected area" of Sec. V-C) and by count.
+ *
+ *   mu         float[nvec][np]  fluence (e.g. from uvc_fluence)
+ *   cov_area   float[nvec]      sum_j a_j [mu_vj >= mu_min] / sum_j a_j
+ *   cov_count  float[nvec] or NULL: fraction of patches meeting it
+ *
+ * Deterministic FP32 reductions with compensated sums.  nvec in [1, 65535].
+ */
+int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu_min, float* cov_area,
+                 float* cov_count, uvc_stream_t stream);
+
+/* uvc_status_string - static text for a status code (never NULL). */
+const char* uvc_status_string(int status);
+
+/*
+ * uvc_scene_status - synchronise `stream`, then return and clear the scene's
+ * device status word: UVC_OK, or the first device-side error recorded since
+ * the last call (UVC_E_TIMEOUT, UVC_E_STACK).
+ */
+int uvc_scene_status(const uvc_scene* scene, uvc_stream_t stream);
+
+/*
+ * uvc_scene_info - host-side facts about a built scene: triangle and patch
+ * counts, depth of the hierarchy (edges from the root to the deepest leaf).
+ * Any output pointer may be NULL.
+ */
+int uvc_scene_info(const uvc_scene* scene, int64_t* nt, int64_t* np, int32_t* depth);
+
+/*
+ * uvc_scene_export_bvh - copy the hierarchy to HOST buffers for inspection
+ * and testing (synchronises the scene's build stream).  Any pointer may be
+ * NULL to skip that array.  For nt >= 2 there are nt-1 internal nodes:
+ *   keys      uint64[nt]  sorted Morton keys
+ *   order     int32[nt]   triangle index at each sorted position
+ *   children  int32[nt-1][2]  child references: >= 0 internal node index,
+ *                          < 0 leaf ~k (sorted position k)
+ *   boxes     float[nt-1][12] left child lo.xyz, hi.xyz, right child lo.xyz, hi.xyz
+ */
+int uvc_scene_export_bvh(const uvc_scene* scene, uint64_t* keys, int32_t* order, int32_t* children,
+                         float* boxes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UVC_H */

@@ -1,0 +1,175 @@
+// extern "C" entry points of libuvc: argument checks, lamp conversion, and
+// dispatch to the kernels.  See include/uvc.h for the contract of each call.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "uvc_internal.cuh"
+
+namespace uvc {
+
+int sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+    return n;
+}
+
+int status_from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return UVC_OK;
+    return e == cudaErrorMemoryAllocation ? UVC_E_NOMEM : UVC_E_CUDA;
+}
+
+namespace {
+
+const int64_t kLimit = int64_t(1) << 31;
+
+bool count_ok(int64_t n) { return n >= 0 && n < kLimit; }
+
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
+    if (!lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES) return UVC_E_INVAL;
+    if (!std::isfinite(lamp->power) || lamp->power < 0.f) return UVC_E_INVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->K = lamp->K;
+    for (int m = 0; m < lamp->K; ++m) {
+        const float w = lamp->weight[m];
+        if (!std::isfinite(w) || w < 0.f) return UVC_E_INVAL;
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(lamp->offsets[m][k])) return UVC_E_INVAL;
+        out->ox[m] = lamp->offsets[m][0];
+        out->oy[m] = lamp->offsets[m][1];
+        out->oz[m] = lamp->offsets[m][2];
+        out->pw[m] = w * lamp->power;   // source power w_m P (one FP32 rounding)
+    }
+    return UVC_OK;
+}
+
+}  // namespace
+}  // namespace uvc
+
+extern "C" {
+
+int uvc_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
+                    int64_t np, uvc_stream_t stream, uvc_scene** out) {
+    return uvc::build_scene(verts, nv, tris, nt, patches, np, (cudaStream_t)stream, out);
+}
+
+int uvc_free_scene(uvc_scene* scene) {
+    if (!scene) return UVC_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (scene->block) cudaFree(scene->block);
+    delete scene;
+    return uvc::status_from_cuda(e);
+}
+
+int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp, float* A,
+                          int64_t lda, uint32_t* vis, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc)) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (lda < scene->np) return UVC_E_INVAL;
+    if (nc == 0 || scene->np == 0) return UVC_OK;
+    if (!cand || !A) return UVC_E_INVAL;
+    return uvc::irradiance_matrix(scene, cand, nc, L, A, lda, vis, (cudaStream_t)stream);
+}
+
+int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                            float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || !counters) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (lda < scene->np) return UVC_E_INVAL;
+    if (nc > 0 && scene->np > 0 && (!cand || !A)) return UVC_E_INVAL;
+    return uvc::irradiance_counters(scene, cand, nc, L, A, lda, reinterpret_cast<unsigned long long*>(counters),
+                                    (cudaStream_t)stream);
+}
+
+int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
+                float* mu, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256 || lda < scene->np) return UVC_E_INVAL;
+    if (scene->np == 0) return UVC_OK;
+    if (!mu || (nc > 0 && (!A || !t))) return UVC_E_INVAL;
+    return uvc::fluence(scene, A, nc, lda, t, nvec, mu, (cudaStream_t)stream);
+}
+
+int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                         const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (scene->np == 0) return UVC_OK;
+    if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;
+    return uvc::fluence_streamed(scene, cand, nc, L, t, nvec, mu, (cudaStream_t)stream);
+}
+
+int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu_min, float* cov_area,
+                 float* cov_count, uvc_stream_t stream) {
+    if (!scene || nvec < 1 || nvec > 65535 || !cov_area || !std::isfinite(mu_min)) return UVC_E_INVAL;
+    if (scene->np > 0 && !mu) return UVC_E_INVAL;
+    return uvc::coverage(scene, mu, nvec, mu_min, cov_area, cov_count, (cudaStream_t)stream);
+}
+
+const char* uvc_status_string(int status) {
+    switch (status) {
+        case UVC_OK: return "ok";
+        case UVC_E_INVAL: return "invalid argument";
+        case UVC_E_NOMEM: return "out of device memory";
+        case UVC_E_CUDA: return "CUDA runtime error";
+        case UVC_E_STACK: return "traversal stack overflow";
+        case UVC_E_TIMEOUT: return "traversal exceeded its node-visit cap";
+        default: return "unknown status";
+    }
+}
+
+int uvc_scene_status(const uvc_scene* scene, uvc_stream_t stream) {
+    if (!scene) return UVC_E_INVAL;
+    int v = 0;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, scene->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(scene->status, 0, sizeof(int));
+    if (e != cudaSuccess) return uvc::status_from_cuda(e);
+    return v;
+}
+
+int uvc_scene_info(const uvc_scene* scene, int64_t* nt, int64_t* np, int32_t* depth) {
+    if (!scene) return UVC_E_INVAL;
+    if (nt) *nt = scene->nt;
+    if (np) *np = scene->np;
+    if (depth) *depth = scene->depth;
+    return UVC_OK;
+}
+
+int uvc_scene_export_bvh(const uvc_scene* scene, uint64_t* keys, int32_t* order, int32_t* children, float* boxes) {
+    if (!scene) return UVC_E_INVAL;
+    const int64_t n = scene->nt, ni = n > 1 ? n - 1 : 0;
+    cudaError_t e = cudaStreamSynchronize(scene->build_stream);
+    if (e == cudaSuccess && keys && n)
+        e = cudaMemcpy(keys, scene->keys, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && order && n)
+        e = cudaMemcpy(order, scene->order, sizeof(int32_t) * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && (children || boxes) && ni) {
+        uvc::Node* h = new (std::nothrow) uvc::Node[ni];
+        if (!h) return UVC_E_NOMEM;
+        e = cudaMemcpy(h, scene->nodes, sizeof(uvc::Node) * ni, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            for (int64_t k = 0; k < ni; ++k) {
+                if (children) {
+                    children[2 * k] = h[k].r.x;
+                    children[2 * k + 1] = h[k].r.y;
+                }
+                if (boxes) {
+                    const float v[12] = {h[k].a.x, h[k].a.y, h[k].a.z, h[k].a.w, h[k].b.x, h[k].b.y,
+                                         h[k].b.z, h[k].b.w, h[k].c.x, h[k].c.y, h[k].c.z, h[k].c.w};
+                    std::memcpy(boxes + 12 * k, v, sizeof(v));
+                }
+            }
+        }
+        delete[] h;
+    }
+    return uvc::status_from_cuda(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,516 @@
+// Scene upload and linear-BVH construction on the GPU.
+//
+// The environment boundary is a triangle mesh (paper Sec. III-B).  Occlusion
+// queries (the visibility rule stated with Eq. (7), Sec. IV-C) are answered by
+// a bounding-volume hierarchy built here in five data-parallel steps:
+//   1. per triangle: bounding box, reference point (box centre), scene bounds
+//   2. 63-bit Morton key of the reference point (21 bits per axis)
+//   3. stable LSD radix sort of (key, triangle) in eight 8-bit passes
+//   4. binary radix tree over the sorted keys (Karras, HPG 2012): every
+//      internal node finds its own key range and split independently
+//   5. bottom-up box refit: the second child to finish merges both boxes
+// Nodes hold the boxes of both children so that one 64-byte load serves a
+// traversal step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "uvc_internal.cuh"
+
+namespace uvc {
+namespace {
+
+constexpr int kSortItems = 8;                      // keys per thread per tile
+constexpr int kSortTile = kThreads * kSortItems;   // 2048 keys per tile
+constexpr int kRadixBits = 8;
+constexpr int kRadixBins = 1 << kRadixBits;
+constexpr int kSortPasses = 8;                     // 64 bits of key
+
+enum : int { kErrTriIndex = 1, kErrVertex = 2, kErrExcl = 4, kErrPatch = 8 };
+
+// Order-preserving map of floats to unsigned integers (for atomic min/max).
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+    unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ __forceinline__ bool finite3(float x, float y, float z) {
+    return isfinite(x) && isfinite(y) && isfinite(z);
+}
+
+// Step 1: triangle boxes and reference points; scene bounds of the references.
+__global__ void k_prepare_tris(const float* __restrict__ verts, int64_t nv, const int32_t* __restrict__ tris,
+                               int nt, float4* __restrict__ tri_lo, float4* __restrict__ tri_hi,
+                               float4* __restrict__ ref, unsigned int* bounds, int* err) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned int mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu};
+    unsigned int mx[3] = {0u, 0u, 0u};
+    if (t < nt) {
+        int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+        float3 lo = make_float3(0.f, 0.f, 0.f), hi = lo, p = lo;
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= nv || ib >= nv || ic >= nv) {
+            atomicOr(err, kErrTriIndex);
+        } else {
+            float ax = verts[3 * ia], ay = verts[3 * ia + 1], az = verts[3 * ia + 2];
+            float bx = verts[3 * ib], by = verts[3 * ib + 1], bz = verts[3 * ib + 2];
+            float cx = verts[3 * ic], cy = verts[3 * ic + 1], cz = verts[3 * ic + 2];
+            if (!finite3(ax, ay, az) || !finite3(bx, by, bz) || !finite3(cx, cy, cz)) atomicOr(err, kErrVertex);
+            lo = make_float3(fminf(fminf(ax, bx), cx), fminf(fminf(ay, by), cy), fminf(fminf(az, bz), cz));
+            hi = make_float3(fmaxf(fmaxf(ax, bx), cx), fmaxf(fmaxf(ay, by), cy), fmaxf(fmaxf(az, bz), cz));
+            p = make_float3(__fmul_rn(__fadd_rn(lo.x, hi.x), 0.5f), __fmul_rn(__fadd_rn(lo.y, hi.y), 0.5f),
+                            __fmul_rn(__fadd_rn(lo.z, hi.z), 0.5f));
+            mn[0] = mx[0] = float_to_ordered(p.x);
+            mn[1] = mx[1] = float_to_ordered(p.y);
+            mn[2] = mx[2] = float_to_ordered(p.z);
+        }
+        tri_lo[t] = make_float4(lo.x, lo.y, lo.z, 0.f);
+        tri_hi[t] = make_float4(hi.x, hi.y, hi.z, 0.f);
+        ref[t] = make_float4(p.x, p.y, p.z, 0.f);
+    }
+    for (int k = 0; k < 3; ++k) {
+        unsigned int a = __reduce_min_sync(0xffffffffu, mn[k]);
+        unsigned int b = __reduce_max_sync(0xffffffffu, mx[k]);
+        if ((threadIdx.x & 31) == 0) {
+            if (a != 0xffffffffu) atomicMin(&bounds[k], a);
+            if (b != 0u) atomicMax(&bounds[3 + k], b);
+        }
+    }
+}
+
+// Patches: validate and pack into the scene's layout.
+__global__ void k_pack_patches(uvc_patches p, int np, int nt, float4* __restrict__ ps, float4* __restrict__ pn,
+                               int2* __restrict__ pe, int* err) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    float sx = p.centroid[3 * j], sy = p.centroid[3 * j + 1], sz = p.centroid[3 * j + 2];
+    float nx = p.normal[3 * j], ny = p.normal[3 * j + 1], nz = p.normal[3 * j + 2];
+    float a = p.area[j];
+    int e0 = p.excl[2 * j], e1 = p.excl[2 * j + 1];
+    if (!finite3(sx, sy, sz) || !finite3(nx, ny, nz) || !isfinite(a)) atomicOr(err, kErrPatch);
+    if (e0 < -1 || e0 >= nt || e1 < -1 || e1 >= nt) atomicOr(err, kErrExcl);
+    ps[j] = make_float4(sx, sy, sz, a);
+    pn[j] = make_float4(nx, ny, nz, 0.f);
+    pe[j] = make_int2(e0, e1);
+}
+
+__device__ __forceinline__ uint64_t spread21(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | (x << 32)) & 0x001f00000000ffffull;
+    x = (x | (x << 16)) & 0x001f0000ff0000ffull;
+    x = (x | (x << 8)) & 0x100f00f00f00f00full;
+    x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+    x = (x | (x << 2)) & 0x1249249249249249ull;
+    return x;
+}
+
+// Step 2: Morton keys.  q = floor((p - lo) * (2^21 / (hi - lo))) in FP32 steps.
+__global__ void k_morton(const float4* __restrict__ ref, int nt, const unsigned int* __restrict__ bounds,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    float lo[3], scale[3];
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = ordered_to_float(bounds[k]);
+        float ext = __fsub_rn(ordered_to_float(bounds[3 + k]), lo[k]);
+        scale[k] = ext > 0.f ? __fdiv_rn(2097152.0f, ext) : 0.f;
+    }
+    float4 p = ref[t];
+    float pc[3] = {p.x, p.y, p.z};
+    uint32_t q[3];
+    for (int k = 0; k < 3; ++k) {
+        float f = floorf(__fmul_rn(__fsub_rn(pc[k], lo[k]), scale[k]));
+        q[k] = f >= 2097151.0f ? 2097151u : (uint32_t)f;
+    }
+    keys[t] = (spread21(q[0]) << 2) | (spread21(q[1]) << 1) | spread21(q[2]);
+    vals[t] = (uint32_t)t;
+}
+
+// Step 3a: per-tile digit histograms, laid out [digit][tile].
+__global__ void __launch_bounds__(kThreads) k_radix_hist(const uint64_t* __restrict__ keys, int n, int shift,
+                                                         int ntiles, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[kRadixBins];
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) h[d] = 0;
+    __syncthreads();
+    int base = blockIdx.x * kSortTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        int idx = base + k * kThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (kRadixBins - 1)], 1u);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) hist[(size_t)d * ntiles + blockIdx.x] = h[d];
+}
+
+// Step 3b: exclusive scan of each digit's row of tile counts; row totals.
+__global__ void __launch_bounds__(1024) k_radix_rowscan(uint32_t* __restrict__ hist, int ntiles,
+                                                        uint32_t* __restrict__ totals) {
+    __shared__ uint32_t warp_sums[32];
+    __shared__ uint32_t carry;
+    uint32_t* row = hist + (size_t)blockIdx.x * ntiles;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < ntiles; base += 1024) {
+        int idx = base + threadIdx.x;
+        uint32_t v = idx < ntiles ? row[idx] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = warp_sums[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_sums[lane] = w;
+        }
+        __syncthreads();
+        uint32_t excl = carry + (warp ? warp_sums[warp - 1] : 0u) + x - v;
+        if (idx < ntiles) row[idx] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+// Step 3c: stable scatter.  Within a tile, keys are ranked in index order
+// (warp chunk, then iteration, then lane) using warp match masks.
+__global__ void __launch_bounds__(kThreads) k_radix_scatter(const uint64_t* __restrict__ keys_in,
+                                                            const uint32_t* __restrict__ vals_in,
+                                                            uint64_t* __restrict__ keys_out,
+                                                            uint32_t* __restrict__ vals_out, int n, int shift,
+                                                            int ntiles, const uint32_t* __restrict__ hist,
+                                                            const uint32_t* __restrict__ totals) {
+    __shared__ uint32_t tile_off[kRadixBins];
+    __shared__ uint32_t cnt[kWarpsPerBlock][kRadixBins];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // digit base = exclusive scan of totals (256 values, by warp 0)
+    if (warp == 0) {
+        uint32_t v[8], run = 0;
+        for (int k = 0; k < 8; ++k) { v[k] = totals[lane * 8 + k]; run += v[k]; }
+        uint32_t x = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        uint32_t b = x - run;
+        for (int k = 0; k < 8; ++k) {
+            int d = lane * 8 + k;
+            tile_off[d] = b + hist[(size_t)d * ntiles + blockIdx.x];
+            b += v[k];
+        }
+    }
+    for (int d = lane; d < kRadixBins; d += 32) cnt[warp][d] = 0;
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    const int base = blockIdx.x * kSortTile + warp * (32 * kSortItems);
+    uint64_t key[kSortItems];
+    uint32_t val[kSortItems], rank[kSortItems], dig[kSortItems];
+    for (int k = 0; k < kSortItems; ++k) {
+        int idx = base + k * 32 + lane;
+        bool ok = idx < n;
+        key[k] = ok ? keys_in[idx] : 0ull;
+        val[k] = ok ? vals_in[idx] : 0u;
+        uint32_t d = ok ? (uint32_t)((key[k] >> shift) & (kRadixBins - 1)) : (uint32_t)(kRadixBins + lane);
+        dig[k] = d;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = ok ? cnt[warp][d] : 0u;
+        __syncwarp();
+        rank[k] = before + __popc(peers & lt);
+        if (ok && (31 - __clz(peers)) == lane) cnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // exclusive prefix over warps, per digit
+    for (int d = threadIdx.x; d < kRadixBins; d += blockDim.x) {
+        uint32_t run = 0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) {
+            uint32_t c = cnt[w][d];
+            cnt[w][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < kSortItems; ++k) {
+        int idx = base + k * 32 + lane;
+        if (idx >= n) continue;
+        uint32_t d = dig[k];
+        uint32_t pos = tile_off[d] + cnt[warp][d] + rank[k];
+        keys_out[pos] = key[k];
+        vals_out[pos] = val[k];
+    }
+}
+
+// Sorted triangle records and leaf boxes.
+__global__ void k_gather_tris(const uint32_t* __restrict__ order, const float* __restrict__ verts, int64_t nv,
+                              const int32_t* __restrict__ tris, int nt, const float4* __restrict__ tri_lo,
+                              const float4* __restrict__ tri_hi, float4* __restrict__ tri_out,
+                              int32_t* __restrict__ order_out, float4* __restrict__ leaf_lo,
+                              float4* __restrict__ leaf_hi) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nt) return;
+    int t = (int)order[k];
+    int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
+    // invalid indices were flagged by k_prepare_tris (the build then fails);
+    // clamp so that no read leaves the vertex array meanwhile
+    if (ia < 0 || ia >= nv) ia = 0;
+    if (ib < 0 || ib >= nv) ib = 0;
+    if (ic < 0 || ic >= nv) ic = 0;
+    tri_out[3 * k] = make_float4(verts[3 * ia], verts[3 * ia + 1], verts[3 * ia + 2], __int_as_float(t));
+    tri_out[3 * k + 1] = make_float4(verts[3 * ib], verts[3 * ib + 1], verts[3 * ib + 2], 0.f);
+    tri_out[3 * k + 2] = make_float4(verts[3 * ic], verts[3 * ic + 1], verts[3 * ic + 2], 0.f);
+    order_out[k] = t;
+    leaf_lo[k] = tri_lo[t];
+    leaf_hi[k] = tri_hi[t];
+}
+
+// Common prefix of the extended keys (key, position) at sorted positions i, j;
+// -1 when j lies outside [0, n).
+__device__ __forceinline__ int prefix_len(const uint64_t* __restrict__ keys, int n, int i, int64_t j) {
+    if (j < 0 || j >= n) return -1;
+    uint64_t a = keys[i], b = keys[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz(i ^ (int)j);
+}
+
+// Step 4: binary radix tree, one thread per internal node (Karras 2012).
+__global__ void k_karras(const uint64_t* __restrict__ keys, int n, int2* __restrict__ children,
+                         int* __restrict__ parent_int, int* __restrict__ parent_leaf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = (prefix_len(keys, n, i, i + 1) - prefix_len(keys, n, i, i - 1)) > 0 ? 1 : -1;
+    int dmin = prefix_len(keys, n, i, i - d);
+    int64_t lmax = 2;
+    while (prefix_len(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+    int64_t l = 0;
+    for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+        if (prefix_len(keys, n, i, i + (l + t) * d) > dmin) l += t;
+    int j = (int)(i + l * d);
+    int dnode = prefix_len(keys, n, i, j);
+    int64_t s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (prefix_len(keys, n, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    int gamma = (int)(i + s * d + min(d, 0));
+    int lo = min(i, j), hi = max(i, j);
+    int left = (lo == gamma) ? ~gamma : gamma;
+    int right = (hi == gamma + 1) ? ~(gamma + 1) : gamma + 1;
+    children[i] = make_int2(left, right);
+    if (left < 0) parent_leaf[~left] = i; else parent_int[left] = i;
+    if (right < 0) parent_leaf[~right] = i; else parent_int[right] = i;
+    if (i == 0) parent_int[0] = -1;
+}
+
+// Step 5: bottom-up refit; one thread per leaf climbs while it is the second
+// child to arrive at a node.  Also computes subtree heights (tree depth).
+__global__ void k_refit(int n, const int2* __restrict__ children, const int* __restrict__ parent_int,
+                        const int* __restrict__ parent_leaf, const float4* __restrict__ leaf_lo,
+                        const float4* __restrict__ leaf_hi, float4* node_lo, float4* node_hi, int* height,
+                        int* flags, int* depth_out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int p = parent_leaf[k];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;   // first arrival: the sibling finishes p
+        __threadfence();
+        int2 c = children[p];
+        float4 llo, lhi, rlo, rhi;
+        int hl = 0, hr = 0;
+        if (c.x < 0) { llo = leaf_lo[~c.x]; lhi = leaf_hi[~c.x]; }
+        else { llo = __ldcg(&node_lo[c.x]); lhi = __ldcg(&node_hi[c.x]); hl = __ldcg(&height[c.x]); }
+        if (c.y < 0) { rlo = leaf_lo[~c.y]; rhi = leaf_hi[~c.y]; }
+        else { rlo = __ldcg(&node_lo[c.y]); rhi = __ldcg(&node_hi[c.y]); hr = __ldcg(&height[c.y]); }
+        __stcg(&node_lo[p], make_float4(fminf(llo.x, rlo.x), fminf(llo.y, rlo.y), fminf(llo.z, rlo.z), 0.f));
+        __stcg(&node_hi[p], make_float4(fmaxf(lhi.x, rhi.x), fmaxf(lhi.y, rhi.y), fmaxf(lhi.z, rhi.z), 0.f));
+        int h = 1 + max(hl, hr);
+        __stcg(&height[p], h);
+        if (p == 0) { *depth_out = h; return; }
+        p = parent_int[p];
+    }
+}
+
+__global__ void k_pack_nodes(int n, const int2* __restrict__ children, const int* __restrict__ parent_int,
+                             const float4* __restrict__ leaf_lo, const float4* __restrict__ leaf_hi,
+                             const float4* __restrict__ node_lo, const float4* __restrict__ node_hi,
+                             Node* __restrict__ nodes) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int2 c = children[i];
+    float4 L0 = c.x < 0 ? leaf_lo[~c.x] : node_lo[c.x];
+    float4 L1 = c.x < 0 ? leaf_hi[~c.x] : node_hi[c.x];
+    float4 R0 = c.y < 0 ? leaf_lo[~c.y] : node_lo[c.y];
+    float4 R1 = c.y < 0 ? leaf_hi[~c.y] : node_hi[c.y];
+    Node nd;
+    nd.a = make_float4(L0.x, L0.y, L0.z, L1.x);
+    nd.b = make_float4(L1.y, L1.z, R0.x, R0.y);
+    nd.c = make_float4(R0.z, R1.x, R1.y, R1.z);
+    nd.r = make_int4(c.x, c.y, parent_int[i], 0);
+    nodes[i] = nd;
+}
+
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
+                int64_t np, cudaStream_t stream, uvc_scene** out) {
+    if (!out) return UVC_E_INVAL;
+    *out = nullptr;
+    const int64_t lim = int64_t(1) << 31;
+    if (nv < 0 || nt < 0 || np < 0 || nv >= lim || nt >= lim || np >= lim || !patches) return UVC_E_INVAL;
+    if ((nt > 0 && (!verts || !tris || nv == 0)) || (nv > 0 && !verts)) return UVC_E_INVAL;
+    if (np > 0 && (!patches->centroid || !patches->normal || !patches->area || !patches->excl)) return UVC_E_INVAL;
+
+    uvc_scene* sc = new (std::nothrow) uvc_scene();
+    if (!sc) return UVC_E_NOMEM;
+    cudaGetDevice(&sc->device);
+    sc->nt = nt;
+    sc->np = np;
+    sc->build_stream = stream;
+    const int n = (int)nt;
+    const int ni = n > 1 ? n - 1 : 0;
+
+    // persistent buffers
+    size_t bytes = align256(sizeof(float4) * 3 * (size_t)n) + align256(sizeof(Node) * (size_t)ni) +
+                   align256(sizeof(uint64_t) * (size_t)n) + align256(sizeof(int32_t) * (size_t)n) +
+                   2 * align256(sizeof(float4) * (size_t)np) + align256(sizeof(int2) * (size_t)np) +
+                   align256(sizeof(float)) + align256(sizeof(int)) + 256;
+    if (cudaMallocAsync(&sc->block, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        delete sc;
+        return UVC_E_NOMEM;
+    }
+    Carver pc(sc->block);
+    sc->tri = pc.take<float4>(3 * (size_t)n);
+    sc->nodes = pc.take<Node>(ni);
+    sc->keys = pc.take<uint64_t>(n);
+    sc->order = pc.take<int32_t>(n);
+    sc->patch_s = pc.take<float4>(np);
+    sc->patch_n = pc.take<float4>(np);
+    sc->patch_excl = pc.take<int2>(np);
+    sc->area_total = pc.take<float>(1);
+    sc->status = pc.take<int>(1);
+
+    // temporaries
+    const int ntiles = (n + kSortTile - 1) / kSortTile;
+    size_t tbytes = 3 * align256(sizeof(float4) * (size_t)n) +            // tri_lo, tri_hi, ref
+                    align256(sizeof(uint64_t) * (size_t)n) +                // keys alt
+                    2 * align256(sizeof(uint32_t) * (size_t)n) +            // vals, vals alt
+                    align256(sizeof(uint32_t) * kRadixBins * (size_t)ntiles) + align256(sizeof(uint32_t) * kRadixBins) +
+                    align256(sizeof(int2) * (size_t)ni) + align256(sizeof(int) * (size_t)ni) +   // children, parent_int
+                    align256(sizeof(int) * (size_t)n) +                      // parent_leaf
+                    2 * align256(sizeof(float4) * (size_t)n) +               // leaf lo/hi
+                    2 * align256(sizeof(float4) * (size_t)ni) +              // node lo/hi
+                    2 * align256(sizeof(int) * (size_t)ni) +                 // height, flags
+                    align256(sizeof(unsigned int) * 6) + align256(sizeof(int) * 2) + 256;
+    void* tblock = nullptr;
+    if (cudaMallocAsync(&tblock, tbytes, stream) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeAsync(sc->block, stream);
+        delete sc;
+        return UVC_E_NOMEM;
+    }
+    Carver tc(tblock);
+    float4* tri_lo = tc.take<float4>(n);
+    float4* tri_hi = tc.take<float4>(n);
+    float4* ref = tc.take<float4>(n);
+    uint64_t* keys_alt = tc.take<uint64_t>(n);
+    uint32_t* vals = tc.take<uint32_t>(n);
+    uint32_t* vals_alt = tc.take<uint32_t>(n);
+    uint32_t* hist = tc.take<uint32_t>(kRadixBins * (size_t)ntiles);
+    uint32_t* totals = tc.take<uint32_t>(kRadixBins);
+    int2* children = tc.take<int2>(ni);
+    int* parent_int = tc.take<int>(ni);
+    int* parent_leaf = tc.take<int>(n);
+    float4* leaf_lo = tc.take<float4>(n);
+    float4* leaf_hi = tc.take<float4>(n);
+    float4* node_lo = tc.take<float4>(ni);
+    float4* node_hi = tc.take<float4>(ni);
+    int* height = tc.take<int>(ni);
+    int* flags = tc.take<int>(ni);
+    unsigned int* bounds = tc.take<unsigned int>(6);
+    int* errdepth = tc.take<int>(2);   // [0] = error bits, [1] = depth
+
+    cudaError_t e = cudaSuccess;
+    unsigned int init_bounds[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    e = cudaMemcpyAsync(bounds, init_bounds, sizeof(init_bounds), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(errdepth, 0, 2 * sizeof(int), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), stream);
+    if (e == cudaSuccess && ni) e = cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)ni, stream);
+    const int B = 256;
+    if (e == cudaSuccess && np > 0)
+        k_pack_patches<<<(int)((np + B - 1) / B), B, 0, stream>>>(*patches, (int)np, n, sc->patch_s, sc->patch_n,
+                                                                   sc->patch_excl, errdepth);
+    launch_area_total(sc->patch_s, np, sc->area_total, stream);
+    if (e == cudaSuccess && n > 0) {
+        k_prepare_tris<<<(n + B - 1) / B, B, 0, stream>>>(verts, nv, tris, n, tri_lo, tri_hi, ref, bounds, errdepth);
+        k_morton<<<(n + B - 1) / B, B, 0, stream>>>(ref, n, bounds, sc->keys, vals);
+        uint64_t* kin = sc->keys;
+        uint64_t* kout = keys_alt;
+        uint32_t* vin = vals;
+        uint32_t* vout = vals_alt;
+        for (int pass = 0; pass < kSortPasses; ++pass) {
+            int shift = pass * kRadixBits;
+            k_radix_hist<<<ntiles, kThreads, 0, stream>>>(kin, n, shift, ntiles, hist);
+            k_radix_rowscan<<<kRadixBins, 1024, 0, stream>>>(hist, ntiles, totals);
+            k_radix_scatter<<<ntiles, kThreads, 0, stream>>>(kin, vin, kout, vout, n, shift, ntiles, hist, totals);
+            uint64_t* tk = kin; kin = kout; kout = tk;
+            uint32_t* tv = vin; vin = vout; vout = tv;
+        }
+        // eight passes: the sorted keys are back in sc->keys, values in `vals`
+        k_gather_tris<<<(n + B - 1) / B, B, 0, stream>>>(vin, verts, nv, tris, n, tri_lo, tri_hi, sc->tri, sc->order,
+                                                         leaf_lo, leaf_hi);
+        if (n > 1) {
+            k_karras<<<(ni + B - 1) / B, B, 0, stream>>>(sc->keys, n, children, parent_int, parent_leaf);
+            k_refit<<<(n + B - 1) / B, B, 0, stream>>>(n, children, parent_int, parent_leaf, leaf_lo, leaf_hi,
+                                                       node_lo, node_hi, height, flags, errdepth + 1);
+            k_pack_nodes<<<(ni + B - 1) / B, B, 0, stream>>>(n, children, parent_int, leaf_lo, leaf_hi, node_lo,
+                                                             node_hi, sc->nodes);
+        }
+        e = cudaGetLastError();
+    }
+    int host_ed[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_ed, errdepth, sizeof(host_ed), cudaMemcpyDeviceToHost, stream);
+    cudaFreeAsync(tblock, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(sc->block);
+        delete sc;
+        return UVC_E_CUDA;
+    }
+    if (host_ed[0] != 0) {
+        cudaFree(sc->block);
+        delete sc;
+        return UVC_E_INVAL;
+    }
+    sc->depth = host_ed[1];
+    sc->root = n == 1 ? ~0 : 0;
+    *out = sc;
+    return UVC_OK;
+}
+
+}  // namespace uvc

@@ -1,0 +1,463 @@
+// Irradiance matrix (paper Sec. IV-C, Eq. (4) and Eq. (7)) by BVH segment
+// queries, and the streamed fluence (Eq. (5)) that never stores the matrix.
+//
+// Work unit: one warp = one candidate i, one lamp source m at a time, and 32
+// consecutive patches (one per lane).  All 32 segments of a warp start at the
+// same source point, so the warp walks the hierarchy as a packet: one shared
+// node stack, every node box tested by every still-searching lane, a child
+// entered when any lane's segment overlaps it (ballot), and each lane leaving
+// the search at its first occluder (any-hit).  Node and triangle loads are
+// warp-uniform, i.e. one 16-byte transaction serves 32 lanes.  A row tile of
+// A is written as one coalesced 128-byte store per warp; the visibility word
+// of the 32 lanes is the warp ballot itself.
+//
+// Arithmetic (FP32 only):
+//   source      o = fl32(c_i + off_m)
+//   v = o - s   as an exact float pair (TwoSum), <n, v> with an error-free
+//               dot product (TwoProduct + TwoSum), so the facing test and the
+//               cosine keep full relative accuracy even for grazing angles
+//   E          += w_m P <n, v> / (4 pi |v|^3)   for facing, unoccluded sources
+//   occlusion   open segment o + tau (s - o), 0 < tau < 1, against every
+//               triangle except the patch's own (excl), watertight
+//               ray/triangle test of Woop, Benthin and Wald (JCGT 2013) with
+//               the edge functions evaluated without contraction, and a
+//               conservatively widened slab test for the boxes.
+#include <algorithm>
+#include <cmath>
+
+#include "uvc_internal.cuh"
+
+namespace uvc {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr float kFourPi = 12.566370614359172f;
+// 1 + 2^-20: widening of the far slab distance; covers the relative rounding
+// of (b - o) * (1/d) (three roundings) with a wide margin.
+constexpr float kFarScale = 1.0f + 9.5367431640625e-07f;
+
+struct SceneView {
+    const float4* __restrict__ tri;
+    const Node* __restrict__ nodes;
+    const float4* __restrict__ ps;
+    const float4* __restrict__ pn;
+    const int2* __restrict__ pe;
+    int nt, np, root, stack_cap, visit_cap;
+    int* status;
+};
+
+SceneView view_of(const uvc_scene* sc) {
+    SceneView v;
+    v.tri = sc->tri;
+    v.nodes = sc->nodes;
+    v.ps = sc->patch_s;
+    v.pn = sc->patch_n;
+    v.pe = sc->patch_excl;
+    v.nt = (int)sc->nt;
+    v.np = (int)sc->np;
+    v.root = sc->root;
+    v.stack_cap = sc->depth + 1;
+    v.visit_cap = (int)sc->nt + 64;
+    v.status = sc->status;
+    return v;
+}
+
+struct Ray {
+    float ox, oy, oz;   // segment start (the source point, warp-uniform)
+    float dx, dy, dz;   // segment vector: end = start + d
+    float ix, iy, iz;   // 1/d with zero components replaced by +-1e-30
+    float sx, sy, sz;   // shear constants of the watertight test
+    int kx, ky, kz;     // axis permutation of the watertight test
+    int ex0, ex1;       // triangles that never occlude this segment
+};
+
+__device__ __forceinline__ float pick(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
+
+__device__ __forceinline__ float safe_rcp(float d) {
+    float a = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+    return __frcp_rn(a);
+}
+
+__device__ __forceinline__ void setup_ray(Ray& r) {
+    r.ix = safe_rcp(r.dx);
+    r.iy = safe_rcp(r.dy);
+    r.iz = safe_rcp(r.dz);
+    float ax = fabsf(r.dx), ay = fabsf(r.dy), az = fabsf(r.dz);
+    int kz = ax > ay ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dkz = pick(r.dx, r.dy, r.dz, kz);
+    if (dkz < 0.f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.sx = __fdiv_rn(pick(r.dx, r.dy, r.dz, kx), dkz);
+    r.sy = __fdiv_rn(pick(r.dx, r.dy, r.dz, ky), dkz);
+    r.sz = __fdiv_rn(1.0f, dkz);
+}
+
+// Does the segment overlap box [lo, hi] (conservatively)?
+__device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz, float hx, float hy, float hz) {
+    float t0x = __fmul_rn(__fsub_rn(lx, r.ox), r.ix), t1x = __fmul_rn(__fsub_rn(hx, r.ox), r.ix);
+    float t0y = __fmul_rn(__fsub_rn(ly, r.oy), r.iy), t1y = __fmul_rn(__fsub_rn(hy, r.oy), r.iy);
+    float t0z = __fmul_rn(__fsub_rn(lz, r.oz), r.iz), t1z = __fmul_rn(__fsub_rn(hz, r.oz), r.iz);
+    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
+    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), 1.f));
+    return tn <= tf * kFarScale;
+}
+
+// Watertight segment/triangle test: hit iff the segment's line passes through
+// the closed triangle (all edge functions of one sign, non-degenerate) and
+// the parameter tau = T/det lies in the open interval (0, 1).
+__device__ __forceinline__ bool seg_tri(const Ray& r, float4 a, float4 b, float4 c) {
+    float Ax = __fsub_rn(a.x, r.ox), Ay = __fsub_rn(a.y, r.oy), Az = __fsub_rn(a.z, r.oz);
+    float Bx = __fsub_rn(b.x, r.ox), By = __fsub_rn(b.y, r.oy), Bz = __fsub_rn(b.z, r.oz);
+    float Cx = __fsub_rn(c.x, r.ox), Cy = __fsub_rn(c.y, r.oy), Cz = __fsub_rn(c.z, r.oz);
+    float akz = pick(Ax, Ay, Az, r.kz), bkz = pick(Bx, By, Bz, r.kz), ckz = pick(Cx, Cy, Cz, r.kz);
+    float ax = __fmaf_rn(-r.sx, akz, pick(Ax, Ay, Az, r.kx));
+    float ay = __fmaf_rn(-r.sy, akz, pick(Ax, Ay, Az, r.ky));
+    float bx = __fmaf_rn(-r.sx, bkz, pick(Bx, By, Bz, r.kx));
+    float by = __fmaf_rn(-r.sy, bkz, pick(Bx, By, Bz, r.ky));
+    float cx = __fmaf_rn(-r.sx, ckz, pick(Cx, Cy, Cz, r.kx));
+    float cy = __fmaf_rn(-r.sy, ckz, pick(Cx, Cy, Cz, r.ky));
+    float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+    float det = U + V + W;
+    if (det == 0.f) return false;
+    float T = U * __fmul_rn(r.sz, akz) + V * __fmul_rn(r.sz, bkz) + W * __fmul_rn(r.sz, ckz);
+    // tau = T / det in (0, 1), compared without dividing
+    unsigned sgn = __float_as_uint(det) & 0x80000000u;
+    float Ts = __uint_as_float(__float_as_uint(T) ^ sgn);
+    float ds = __uint_as_float(__float_as_uint(det) ^ sgn);
+    return Ts > 0.f && Ts < ds;
+}
+
+__device__ __forceinline__ uint32_t test_leaf(const SceneView& S, int k, const Ray& r, uint32_t mask, int lane) {
+    const float4* t = S.tri + 3 * (size_t)k;
+    float4 a = __ldg(t), b = __ldg(t + 1), c = __ldg(t + 2);
+    int id = __float_as_int(a.w);
+    bool hit = ((mask >> lane) & 1u) && id != r.ex0 && id != r.ex1 && seg_tri(r, a, b, c);
+    return __ballot_sync(kFull, hit);
+}
+
+__device__ __forceinline__ float box_dist2(float px, float py, float pz, float lx, float ly, float lz, float hx,
+                                           float hy, float hz) {
+    float dx = fmaxf(fmaxf(lx - px, px - hx), 0.f);
+    float dy = fmaxf(fmaxf(ly - py, py - hy), 0.f);
+    float dz = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Traversal counters of the instrumented variant (one launch, outside timing):
+// [0] warp node visits, [1] warp leaf tests, [2] warp traversals,
+// [3] lane box tests (alive lanes x 2 per node), [4] lane triangle tests,
+// [5] facing segments.
+constexpr int kNumCounters = 6;
+
+// Packet traversal: returns the lanes (of `alive`) whose segment is occluded;
+// lanes whose search hit the visit cap are returned in `failed`.
+template <bool COUNT>
+__device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t alive, int* stack, int lane,
+                                  uint32_t& failed, unsigned long long* ctr) {
+    failed = 0;
+    if (COUNT && lane == 0) atomicAdd(&ctr[5], (unsigned long long)__popc(alive));
+    if (S.nt == 0 || alive == 0) return 0;
+    if (S.root < 0) {
+        if (COUNT && lane == 0) {
+            atomicAdd(&ctr[1], 1ull);
+            atomicAdd(&ctr[2], 1ull);
+            atomicAdd(&ctr[4], (unsigned long long)__popc(alive));
+        }
+        return test_leaf(S, ~S.root, r, alive, lane);
+    }
+    uint32_t occl = 0;
+    int top = 0, node = 0, visits = 0;
+    unsigned long long c_leaf = 0, c_box = 0, c_tri = 0;
+    while (true) {
+        if (++visits > S.visit_cap) {
+            failed = alive;
+            if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
+            break;
+        }
+        const Node* nd = S.nodes + node;
+        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
+        int4 rr = __ldg(&nd->r);
+        bool me = (alive >> lane) & 1u;
+        if (COUNT) c_box += 2 * __popc(alive);
+        bool hl = me && slab(r, a.x, a.y, a.z, a.w, b.x, b.y);
+        bool hr = me && slab(r, b.z, b.w, c.x, c.y, c.z, c.w);
+        uint32_t ml = __ballot_sync(kFull, hl), mr = __ballot_sync(kFull, hr);
+        if (ml && rr.x < 0) {
+            if (COUNT) { ++c_leaf; c_tri += __popc(ml); }
+            uint32_t h = test_leaf(S, ~rr.x, r, ml, lane);
+            occl |= h; alive &= ~h; ml = 0;
+        }
+        if (mr && rr.y < 0) {
+            if (COUNT) { ++c_leaf; c_tri += __popc(mr & alive); }
+            uint32_t h = test_leaf(S, ~rr.y, r, mr & alive, lane);
+            occl |= h; alive &= ~h; mr = 0;
+        }
+        ml &= alive;
+        mr &= alive;
+        if (!alive) break;
+        if (ml && mr) {
+            float dl = box_dist2(r.ox, r.oy, r.oz, a.x, a.y, a.z, a.w, b.x, b.y);
+            float dr = box_dist2(r.ox, r.oy, r.oz, b.z, b.w, c.x, c.y, c.z, c.w);
+            int first = dl <= dr ? rr.x : rr.y;
+            int second = dl <= dr ? rr.y : rr.x;
+            if (top >= S.stack_cap) {
+                failed = alive;
+                if (lane == 0) atomicCAS(S.status, 0, UVC_E_STACK);
+                break;
+            }
+            if (lane == 0) stack[top] = second;
+            ++top;
+            node = first;
+        } else if (ml) {
+            node = rr.x;
+        } else if (mr) {
+            node = rr.y;
+        } else {
+            if (top == 0) break;
+            --top;
+            __syncwarp();
+            node = stack[top];
+        }
+    }
+    if (COUNT && lane == 0) {
+        atomicAdd(&ctr[0], (unsigned long long)visits);
+        atomicAdd(&ctr[1], c_leaf);
+        atomicAdd(&ctr[2], 1ull);
+        atomicAdd(&ctr[3], c_box);
+        atomicAdd(&ctr[4], c_tri);
+    }
+    return occl;
+}
+
+// Irradiance of candidate i at this lane's patch (lanes beyond np give 0).
+// Writes the K visibility words when vis != nullptr.  Returns NaN for a lane
+// whose search failed (and records UVC_E_TIMEOUT / UVC_E_STACK).
+template <bool COUNT = false>
+__device__ __forceinline__ float irradiance_entry(const SceneView& S, const float* __restrict__ cand, int nc,
+                                                  const LampDev& L, int i, int jb, int lane, int* stack,
+                                                  uint32_t* __restrict__ vis, int nwords,
+                                                  unsigned long long* ctr = nullptr) {
+    const int j = jb * 32 + lane;
+    const bool valid = j < S.np;
+    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f), n4 = s4;
+    int2 ex = make_int2(-1, -1);
+    if (valid) {
+        s4 = __ldg(&S.ps[j]);
+        n4 = __ldg(&S.pn[j]);
+        ex = __ldg(&S.pe[j]);
+    }
+    const float cx = __ldg(&cand[3 * (size_t)i]), cy = __ldg(&cand[3 * (size_t)i + 1]),
+                cz = __ldg(&cand[3 * (size_t)i + 2]);
+    float E = 0.f;
+    bool bad = false;
+    for (int m = 0; m < L.K; ++m) {
+        const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
+        // v = o - s exactly as hi + lo (TwoSum)
+        float hx = __fsub_rn(ox, s4.x), hy = __fsub_rn(oy, s4.y), hz = __fsub_rn(oz, s4.z);
+        float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
+        float lx = __fadd_rn(__fsub_rn(ox, __fsub_rn(hx, qx)), __fsub_rn(-s4.x, qx));
+        float ly = __fadd_rn(__fsub_rn(oy, __fsub_rn(hy, qy)), __fsub_rn(-s4.y, qy));
+        float lz = __fadd_rn(__fsub_rn(oz, __fsub_rn(hz, qz)), __fsub_rn(-s4.z, qz));
+        // <n, v> with TwoProduct / TwoSum (error-free dot product)
+        float p = __fmul_rn(n4.x, hx);
+        float err = __fmaf_rn(n4.x, hx, -p);
+        err = __fmaf_rn(n4.x, lx, err);
+        float acc = p;
+        {
+            float p2 = __fmul_rn(n4.y, hy);
+            float e2 = __fmaf_rn(n4.y, hy, -p2);
+            float s = __fadd_rn(acc, p2);
+            float z = __fsub_rn(s, acc);
+            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p2, z));
+            acc = s;
+            err = __fadd_rn(err, __fadd_rn(q, e2));
+            err = __fmaf_rn(n4.y, ly, err);
+        }
+        {
+            float p3 = __fmul_rn(n4.z, hz);
+            float e3 = __fmaf_rn(n4.z, hz, -p3);
+            float s = __fadd_rn(acc, p3);
+            float z = __fsub_rn(s, acc);
+            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p3, z));
+            acc = s;
+            err = __fadd_rn(err, __fadd_rn(q, e3));
+            err = __fmaf_rn(n4.z, lz, err);
+        }
+        const float nv = __fadd_rn(acc, err);
+        const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+        const bool facing = valid && nv > 0.f && d2 > 0.f;
+        Ray r;
+        r.ox = ox; r.oy = oy; r.oz = oz;
+        r.dx = -hx; r.dy = -hy; r.dz = -hz;
+        r.ex0 = ex.x; r.ex1 = ex.y;
+        setup_ray(r);
+        uint32_t failed;
+        const uint32_t facing_mask = __ballot_sync(kFull, facing);
+        const uint32_t occl = warp_occluded<COUNT>(S, r, facing_mask, stack, lane, failed, ctr);
+        const uint32_t visible = facing_mask & ~occl & ~failed;
+        if (vis && lane == 0) vis[((size_t)m * nc + i) * nwords + jb] = visible;
+        if ((failed >> lane) & 1u) bad = true;
+        if ((visible >> lane) & 1u) {
+            const float d = sqrtf(d2);
+            E = __fadd_rn(E, __fmul_rn(L.pw[m], __fdiv_rn(nv, __fmul_rn(__fmul_rn(kFourPi, d2), d))));
+        }
+    }
+    return bad ? __int_as_float(0x7fffffff) : E;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kThreads) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
+                                                         LampDev L, float* __restrict__ A, int64_t lda,
+                                                         uint32_t* __restrict__ vis, unsigned long long* ctr) {
+    extern __shared__ int smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* stack = smem + warp * S.stack_cap;
+    const int njb = (S.np + 31) >> 5;
+    const int64_t ntask = (int64_t)nc * njb;
+    for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
+         task += (int64_t)gridDim.x * kWarpsPerBlock) {
+        const int i = (int)(task / njb), jb = (int)(task % njb);
+        const float E = irradiance_entry<COUNT>(S, cand, nc, L, i, jb, lane, stack, vis, njb, ctr);
+        const int j = jb * 32 + lane;
+        if (j < S.np) A[(size_t)i * lda + j] = E;
+    }
+}
+
+// Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
+// E values of up to 32 candidates are staged in shared memory, multiplied by
+// the dwell times and added to the chunk's partial sums partial[s][v][j].
+__global__ void __launch_bounds__(kThreads) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
+                                                       LampDev L, const float* __restrict__ t, int nvec,
+                                                       float* __restrict__ partial, int nsplit, int chunk) {
+    extern __shared__ int smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* stack = smem + warp * S.stack_cap;
+    float* Et = reinterpret_cast<float*>(smem + kWarpsPerBlock * S.stack_cap) + warp * 32 * 32;
+    const int njb = (S.np + 31) >> 5;
+    const int64_t ntask = (int64_t)nsplit * njb;
+    for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
+         task += (int64_t)gridDim.x * kWarpsPerBlock) {
+        const int s = (int)(task / njb), jb = (int)(task % njb);
+        const int j = jb * 32 + lane;
+        const int i0 = s * chunk, i1 = min(nc, i0 + chunk);
+        for (int ib = i0; ib < i1; ib += 32) {
+            const int nb = min(32, i1 - ib);
+            for (int q = 0; q < nb; ++q)
+                Et[q * 32 + lane] = irradiance_entry(S, cand, nc, L, ib + q, jb, lane, stack, nullptr, 0);
+            __syncwarp();
+            if (j < S.np) {
+                for (int v = 0; v < nvec; ++v) {
+                    const float* tv = t + (size_t)v * nc + ib;
+                    float sum = 0.f;
+                    for (int q = 0; q < nb; ++q) sum = __fmaf_rn(__ldg(tv + q), Et[q * 32 + lane], sum);
+                    float* pp = partial + ((size_t)s * nvec + v) * S.np + j;
+                    *pp = (ib == i0) ? sum : __fadd_rn(*pp, sum);
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Streamed fluence, pass 2: mu[v][j] = sum over chunks (fixed order, Kahan).
+__global__ void k_reduce_partials(const float* __restrict__ partial, int nsplit, int nvec, int np,
+                                  float* __restrict__ mu) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)nvec * np) return;
+    const size_t stride = (size_t)nvec * np;
+    float sum = 0.f, c = 0.f;
+    for (int s = 0; s < nsplit; ++s) {
+        float y = __fsub_rn(partial[(size_t)s * stride + idx], c);
+        float t = __fadd_rn(sum, y);
+        c = __fsub_rn(__fsub_rn(t, sum), y);
+        sum = t;
+    }
+    mu[idx] = sum;
+}
+
+int grid_for(const void* kernel, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    return per_sm * sm_count();
+}
+
+}  // namespace
+
+int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
+                      int64_t lda, uint32_t* vis, cudaStream_t stream) {
+    if (nc == 0 || sc->np == 0) return UVC_OK;
+    SceneView S = view_of(sc);
+    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
+    const int njb = (S.np + 31) / 32;
+    const int64_t ntask = nc * njb;
+    int grid = grid_for((const void*)k_irradiance<false>, smem);
+    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    k_irradiance<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, vis, nullptr);
+    return status_from_cuda(cudaGetLastError());
+}
+
+int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
+                        int64_t lda, unsigned long long* out6, cudaStream_t stream) {
+    for (int k = 0; k < kNumCounters; ++k) out6[k] = 0;
+    if (nc == 0 || sc->np == 0) return UVC_OK;
+    SceneView S = view_of(sc);
+    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
+    unsigned long long* dctr = nullptr;
+    if (cudaMallocAsync(&dctr, sizeof(unsigned long long) * kNumCounters, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return UVC_E_NOMEM;
+    }
+    cudaError_t e = cudaMemsetAsync(dctr, 0, sizeof(unsigned long long) * kNumCounters, stream);
+    const int njb = (S.np + 31) / 32;
+    const int64_t ntask = nc * njb;
+    int grid = grid_for((const void*)k_irradiance<true>, smem);
+    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (e == cudaSuccess) {
+        k_irradiance<true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, nullptr, dctr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out6, dctr, sizeof(unsigned long long) * kNumCounters, cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    cudaFreeAsync(dctr, stream);
+    return status_from_cuda(e);
+}
+
+int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
+                     int32_t nvec, float* mu, cudaStream_t stream) {
+    if (sc->np == 0) return UVC_OK;
+    SceneView S = view_of(sc);
+    if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)nvec * S.np, stream));
+    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap + sizeof(float) * kWarpsPerBlock * 32 * 32;
+    const int njb = (S.np + 31) / 32;
+    int grid = grid_for((const void*)k_streamed, smem);
+    // enough (chunk, block) tasks to fill the persistent grid several times over
+    const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
+    int64_t nsplit = (want + njb - 1) / njb;
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (nc + 31) / 32));
+    const int64_t cap = (int64_t(1) << 31) / (4 * (int64_t)nvec * S.np);   // partials <= 2 GiB
+    nsplit = std::max<int64_t>(1, std::min(nsplit, cap));
+    const int chunk = (int)((nc + nsplit - 1) / nsplit);
+    nsplit = (nc + chunk - 1) / chunk;
+    float* partial = nullptr;
+    if (cudaMallocAsync(&partial, sizeof(float) * (size_t)nsplit * nvec * S.np, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return UVC_E_NOMEM;
+    }
+    const int64_t ntask = nsplit * njb;
+    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    k_streamed<<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit, chunk);
+    const int64_t total = (int64_t)nvec * S.np;
+    k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(partial, stream);
+    return status_from_cuda(e);
+}
+
+}  // namespace uvc

@@ -1,0 +1,77 @@
+// Internal declarations of libuvc (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/uvc.h"
+
+namespace uvc {
+
+// One internal BVH node: the boxes of both children and both child
+// references, 64 bytes, loaded with four 16-byte loads.
+//   a = (L.lo.x, L.lo.y, L.lo.z, L.hi.x)
+//   b = (L.hi.y, L.hi.z, R.lo.x, R.lo.y)
+//   c = (R.lo.z, R.hi.x, R.hi.y, R.hi.z)
+//   r = (left ref, right ref, parent, 0); ref >= 0 internal node, ref < 0 leaf ~k
+struct __align__(16) Node {
+    float4 a, b, c;
+    int4 r;
+};
+
+// Lamp as seen by the kernels: source offsets and source powers w_m * P.
+struct LampDev {
+    int K;
+    float ox[UVC_MAX_SOURCES], oy[UVC_MAX_SOURCES], oz[UVC_MAX_SOURCES];
+    float pw[UVC_MAX_SOURCES];
+};
+
+}  // namespace uvc
+
+struct uvc_scene {
+    int device = 0;
+    int64_t nt = 0, np = 0;
+    int32_t depth = 0;     // edges from the root to the deepest leaf
+    int32_t root = 0;      // root reference (0, or ~0 for a single triangle)
+    // device buffers, carved out of one allocation
+    void* block = nullptr;
+    float4* tri = nullptr;        // [nt][3]: (v0, id bits), (v1, 0), (v2, 0) in sorted order
+    uvc::Node* nodes = nullptr;   // [nt-1]
+    uint64_t* keys = nullptr;     // [nt] sorted Morton keys
+    int32_t* order = nullptr;     // [nt] triangle index per sorted position
+    float4* patch_s = nullptr;    // [np] (centroid, area)
+    float4* patch_n = nullptr;    // [np] (normal, 0)
+    int2* patch_excl = nullptr;   // [np]
+    float* area_total = nullptr;  // [1]
+    int* status = nullptr;        // [1] device status word (0 = ok)
+    cudaStream_t build_stream = nullptr;
+};
+
+namespace uvc {
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kThreads = kWarpsPerBlock * 32;
+
+int sm_count();
+int status_from_cuda(cudaError_t e);
+
+// BVH build (build_bvh.cu)
+int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
+                int64_t np, cudaStream_t stream, uvc_scene** out);
+
+// irradiance (irradiance.cu)
+int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
+                      int64_t lda, uint32_t* vis, cudaStream_t stream);
+int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
+                        int64_t lda, unsigned long long* out6, cudaStream_t stream);
+int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
+                     int32_t nvec, float* mu, cudaStream_t stream);
+
+// fluence and coverage (fluence.cu)
+int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
+            float* mu, cudaStream_t stream);
+int coverage(const uvc_scene* sc, const float* mu, int32_t nvec, float mu_min, float* cov_area,
+             float* cov_count, cudaStream_t stream);
+void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream_t stream);
+
+}  // namespace uvc

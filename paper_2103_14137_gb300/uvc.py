@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libuvc (include/uvc.h): argument marshalling only.
+
+Every computation runs in the CUDA library; PyTorch supplies device memory and
+the current CUDA stream.  Functions carry the C-ABI names without the `uvc_`
+prefix.  If libuvc.so is missing the import of this module still works, but
+every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libuvc.so")
+MAX_SOURCES = 32
+
+UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT = range(6)
+
+
+class UvcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+class _Lamp(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int32), ("power", ctypes.c_float),
+                ("offsets", (ctypes.c_float * 3) * MAX_SOURCES), ("weight", ctypes.c_float * MAX_SOURCES)]
+
+
+class _Patches(ctypes.Structure):
+    _fields_ = [("centroid", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("area", ctypes.c_void_p), ("excl", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library():
+    """The loaded libuvc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libuvc.so is not built ({LIB_PATH}); run paper_2103_14137_gb300.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "uvc_build_scene": [P, i64, P, i64, ctypes.POINTER(_Patches), i64, P, ctypes.POINTER(P)],
+        "uvc_free_scene": [P],
+        "uvc_irradiance_matrix": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
+        "uvc_fluence": [P, P, i64, i64, P, i32, P, P],
+        "uvc_irradiance_counters": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
+        "uvc_fluence_streamed": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
+        "uvc_coverage": [P, P, i32, ctypes.c_float, P, P, P],
+        "uvc_scene_status": [P, P],
+        "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
+        "uvc_scene_export_bvh": [P, P, P, P, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.uvc_status_string.argtypes = [ctypes.c_int]
+    lib.uvc_status_string.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return library().uvc_status_string(int(status)).decode()
+
+
+def _check(rc: int, what: str):
+    if rc != UVC_OK:
+        raise UvcError(rc, what)
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x: torch.Tensor, dtype, name, shape=None):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(x.shape)}")
+    return ctypes.c_void_p(x.data_ptr() if x.numel() else 0)
+
+
+class Lamp:
+    """K point sources: offsets (K,3) metres from the candidate point, weights
+    (K,) fractions of the total power P (paper Sec. IV-C, non-point lights)."""
+
+    def __init__(self, offsets, weights, power: float):
+        self.offsets = np.asarray(offsets, np.float32).reshape(-1, 3)
+        self.weights = np.asarray(weights, np.float32).reshape(-1)
+        self.power = float(power)
+        if not 1 <= self.offsets.shape[0] <= MAX_SOURCES or self.weights.shape[0] != self.offsets.shape[0]:
+            raise ValueError("a lamp has 1..32 sources with one weight each")
+
+    @property
+    def K(self) -> int:
+        return int(self.offsets.shape[0])
+
+    def _c(self) -> _Lamp:
+        c = _Lamp()
+        c.K = self.K
+        c.power = self.power
+        for m in range(self.K):
+            for k in range(3):
+                c.offsets[m][k] = float(self.offsets[m, k])
+            c.weight[m] = float(self.weights[m])
+        return c
+
+
+def point_lamp(power: float) -> Lamp:
+    return Lamp(np.zeros((1, 3)), np.ones(1), power)
+
+
+def line_lamp(length: float, K: int, power: float) -> Lamp:
+    """Vertical tube from the candidate point up to +length: K equal-power
+    sources at the midpoints of K equal pieces."""
+    z = length * (np.arange(K, dtype=np.float64) + 0.5) / K
+    off = np.zeros((K, 3))
+    off[:, 2] = z
+    return Lamp(off, np.full(K, 1.0 / K), power)
+
+
+class Scene:
+    """A built scene (uvc_build_scene); owns device memory until free()."""
+
+    def __init__(self, handle, keepalive=()):
+        self._h = handle
+        nt, np_, depth = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        _check(library().uvc_scene_info(handle, ctypes.byref(nt), ctypes.byref(np_), ctypes.byref(depth)),
+               "uvc_scene_info")
+        self.nt, self.np, self.depth = nt.value, np_.value, depth.value
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("scene already freed")
+        return self._h
+
+    def free(self):
+        if self._h is not None:
+            library().uvc_free_scene(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def build_scene(verts, tris, centroid, normal, area, excl, stream=None) -> Scene:
+    nv, nt, np_ = verts.shape[0], tris.shape[0], centroid.shape[0]
+    p = _Patches(_dev(centroid, torch.float32, "centroid", (np_, 3)), _dev(normal, torch.float32, "normal", (np_, 3)),
+                 _dev(area, torch.float32, "area", (np_,)), _dev(excl, torch.int32, "excl", (np_, 2)))
+    out = ctypes.c_void_p()
+    rc = library().uvc_build_scene(_dev(verts, torch.float32, "verts", (nv, 3)), nv,
+                                   _dev(tris, torch.int32, "tris", (nt, 3)), nt, ctypes.byref(p), np_,
+                                   _stream(stream), ctypes.byref(out))
+    _check(rc, "uvc_build_scene")
+    return Scene(out)
+
+
+def irradiance_matrix(scene: Scene, cand, lamp: Lamp, A=None, vis=None, with_vis=False, stream=None):
+    """A (nc, np) float32 and, if requested, vis (K, nc, ceil(np/32)) uint32 bitmask.
+    A may be a larger (nc, lda) buffer; only columns [0, np) are written."""
+    nc = cand.shape[0]
+    if A is None:
+        A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
+    if with_vis and vis is None:
+        vis = torch.empty((lamp.K, nc, (scene.np + 31) // 32), dtype=torch.int32, device=cand.device)
+    if A.dim() != 2 or A.shape[0] != nc:
+        raise ValueError("A must be (nc, lda)")
+    vptr = None if vis is None else _dev(vis, torch.int32, "vis", (lamp.K, nc, (scene.np + 31) // 32))
+    L = lamp._c()
+    rc = library().uvc_irradiance_matrix(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                         ctypes.byref(L), _dev(A, torch.float32, "A"), A.shape[1], vptr,
+                                         _stream(stream))
+    _check(rc, "uvc_irradiance_matrix")
+    return A, vis
+
+
+COUNTER_NAMES = ("node_visits", "leaf_tests", "traversals", "lane_box_tests", "lane_tri_tests", "facing_segments")
+
+
+def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> dict:
+    """Instrumented irradiance run: traversal counts (see uvc_irradiance_counters)."""
+    nc = cand.shape[0]
+    if A is None:
+        A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
+    out = np.zeros(6, np.uint64)
+    L = lamp._c()
+    rc = library().uvc_irradiance_counters(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                           ctypes.byref(L), _dev(A, torch.float32, "A"), A.shape[1],
+                                           ctypes.c_void_p(out.ctypes.data), _stream(stream))
+    _check(rc, "uvc_irradiance_counters")
+    return dict(zip(COUNTER_NAMES, (int(x) for x in out)))
+
+
+def fluence(scene: Scene, A, t, mu=None, stream=None):
+    """mu (nvec, np) = t (nvec, nc) @ A (nc, np)."""
+    nvec, nc = t.shape
+    if mu is None:
+        mu = torch.empty((nvec, scene.np), dtype=torch.float32, device=t.device)
+    rc = library().uvc_fluence(scene.handle, _dev(A, torch.float32, "A"), nc, A.shape[1] if A.dim() == 2 else 0,
+                               _dev(t, torch.float32, "t", (nvec, nc)), nvec,
+                               _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
+    _check(rc, "uvc_fluence")
+    return mu
+
+
+def fluence_streamed(scene: Scene, cand, lamp: Lamp, t, mu=None, stream=None):
+    nvec, nc = t.shape
+    if mu is None:
+        mu = torch.empty((nvec, scene.np), dtype=torch.float32, device=t.device)
+    L = lamp._c()
+    rc = library().uvc_fluence_streamed(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                        ctypes.byref(L), _dev(t, torch.float32, "t", (nvec, nc)), nvec,
+                                        _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
+    _check(rc, "uvc_fluence_streamed")
+    return mu
+
+
+def coverage(scene: Scene, mu, mu_min: float, stream=None):
+    """(cov_area, cov_count), each (nvec,) float32 on the device."""
+    nvec = mu.shape[0]
+    ca = torch.empty(nvec, dtype=torch.float32, device=mu.device)
+    cc = torch.empty(nvec, dtype=torch.float32, device=mu.device)
+    rc = library().uvc_coverage(scene.handle, _dev(mu, torch.float32, "mu", (nvec, scene.np)), nvec,
+                                float(mu_min), _dev(ca, torch.float32, "cov_area"),
+                                _dev(cc, torch.float32, "cov_count"), _stream(stream))
+    _check(rc, "uvc_coverage")
+    return ca, cc
+
+
+def scene_status(scene: Scene, stream=None) -> int:
+    return int(library().uvc_scene_status(scene.handle, _stream(stream)))
+
+
+def scene_export_bvh(scene: Scene) -> dict:
+    """Host copies of the hierarchy: keys, order, children (nt-1,2), boxes (nt-1,12)."""
+    n = scene.nt
+    ni = max(n - 1, 0)
+    keys = np.zeros(n, np.uint64)
+    order = np.zeros(n, np.int32)
+    children = np.zeros((ni, 2), np.int32)
+    boxes = np.zeros((ni, 12), np.float32)
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a.size else None  # noqa: E731
+    _check(library().uvc_scene_export_bvh(scene.handle, ptr(keys), ptr(order), ptr(children), ptr(boxes)),
+           "uvc_scene_export_bvh")
+    return dict(keys=keys, order=order, children=children, boxes=boxes)
+
+
+def vis_to_bool(vis: torch.Tensor, np_: int) -> np.ndarray:
+    """Unpack a (K, nc, nwords) bitmask to a bool array (nc, np, K) on the host."""
+    w = vis.cpu().numpy().view(np.uint32)
+    K, nc, nwords = w.shape
+    bits = ((w[..., None] >> np.arange(32, dtype=np.uint32)) & 1).astype(bool)
+    bits = bits.reshape(K, nc, nwords * 32)[:, :, :np_]
+    return np.transpose(bits, (1, 2, 0))

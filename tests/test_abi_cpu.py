@@ -1,0 +1,98 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point declared in include/uvc.h, and the binding's host logic."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2103_14137_gb300 as uvc
+    uvc.build()
+    return uvc.library()
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(uvc_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_entry_points()
+    for required in ("uvc_build_scene", "uvc_irradiance_matrix", "uvc_fluence", "uvc_fluence_streamed",
+                     "uvc_coverage", "uvc_free_scene", "uvc_status_string", "uvc_scene_status"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_entry_points():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    import paper_2103_14137_gb300 as uvc
+    assert uvc.status_string(0) == "ok"
+    assert "invalid" in uvc.status_string(1)
+    assert uvc.status_string(999) == "unknown status"
+
+
+def test_null_arguments_rejected_without_gpu(lib):
+    P = ctypes.c_void_p
+    out = P()
+    # NULL out pointer and negative counts are rejected on the host
+    assert lib.uvc_build_scene(None, 0, None, 0, None, 0, None, None) == 1
+    assert lib.uvc_build_scene(None, -1, None, 0, None, 0, None, ctypes.byref(out)) == 1
+    assert lib.uvc_irradiance_matrix(None, None, 0, None, None, 0, None, None) == 1
+    assert lib.uvc_fluence(None, None, 0, 0, None, 1, None, None) == 1
+    assert lib.uvc_coverage(None, None, 1, 1.0, None, None, None) == 1
+    assert lib.uvc_scene_status(None, None) == 1
+    assert lib.uvc_free_scene(None) == 0
+
+
+def test_lamp_struct_layout():
+    from paper_2103_14137_gb300.uvc import _Lamp, line_lamp
+    assert ctypes.sizeof(_Lamp) == 4 + 4 + 32 * 3 * 4 + 32 * 4
+    L = line_lamp(1.2, 8, 120.0)
+    c = L._c()
+    assert c.K == 8 and abs(c.power - 120.0) < 1e-6
+    assert np.allclose([c.offsets[m][2] for m in range(8)], 1.2 * (np.arange(8) + 0.5) / 8)
+    assert np.isclose(sum(c.weight[m] for m in range(8)), 1.0)
+
+
+def test_product_line_lamp_matches_generator():
+    """The binding's line lamp and the input generator's are written separately;
+    they must describe the same sources."""
+    from paper_2103_14137_gb300.uvc import line_lamp
+    from synth import line_lamp as gen_line_lamp
+    a, b = line_lamp(1.8, 12, 80.0), gen_line_lamp(1.8, 12, 80.0)
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.weights, b.weights)
+
+
+def test_vis_unpacking():
+    import torch
+    from paper_2103_14137_gb300.uvc import vis_to_bool
+    w = torch.tensor([[[0b101, -2147483648]]], dtype=torch.int32)   # K=1, nc=1, 2 words
+    b = vis_to_bool(w, 40)
+    assert b.shape == (1, 40, 1)
+    assert b[0, :, 0].nonzero()[0].tolist() == [0, 2]
+    w = torch.tensor([[[0, -2147483648]]], dtype=torch.int32)
+    assert vis_to_bool(w, 64)[0, :, 0].nonzero()[0].tolist() == [63]
+
+
+def test_product_never_imports_oracle():
+    pkg = os.path.join(ROOT, "paper_2103_14137_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in txt.replace("no oracle", ""), f

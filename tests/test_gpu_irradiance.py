@@ -1,0 +1,188 @@
+"""Irradiance matrix on the GPU (through the C ABI) against the FP64 oracle:
+full matrices on small scenes (several warp tiles plus a ragged tail), sampled
+entries on the full-size ward workload in the benchmark's launch
+configuration, and the degenerate cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2103_14137_gb300 as uvc
+from synth import tiny_room, ward_room
+from synth.scenes import line_lamp
+from tests import _pins
+from tests._compare import compare_irradiance
+from tests.gpu_util import T, build, build_arrays, gpu_matrix, lamp_of
+
+pytestmark = pytest.mark.gpu
+
+
+def _full_parity(verts, tris, cen, nrm, area, excl, cand, L):
+    sc = build_arrays(verts, tris, cen, nrm, area, excl)
+    A, visg = gpu_matrix(sc, cand, uvc.Lamp(L.offsets, L.weights, L.power))
+    E, ovis, flag = oracle.irradiance(verts, tris, cen, nrm, excl, cand, L.offsets, L.weights, L.power)
+    sc.free()
+    return compare_irradiance(A, visg, E, ovis, flag)
+
+
+def test_tiny_room_full_matrix_bit_exact_visibility():
+    s = tiny_room()
+    st = _full_parity(s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, s.cand, s.lamp)
+    assert st["excused_bits"] == 0 and st["pairs"] == 200 * s.np_
+    assert s.np_ % 32 != 0          # ragged last warp tile
+
+
+def test_tiny_room_line_lamp_ragged():
+    s = tiny_room(n_cand=37)
+    L = line_lamp(0.9, 5, 120.0)
+    cand = s.cand.copy()
+    cand[:, 2] = 0.8
+    _full_parity(s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, cand, L)
+
+
+def test_mirror_room_gpu_symmetric_and_matches_oracle():
+    verts, tris, cen, nrm, excl, cand, mc, mp = _pins.mirror_room()
+    area = np.ones(cen.shape[0], np.float32)
+    from synth.scenes import point_lamp
+    L = point_lamp(80.0)
+    _full_parity(verts, tris, cen, nrm, area, excl, cand, L)
+    sc = build_arrays(verts, tris, cen, nrm, area, excl)
+    A, visg = gpu_matrix(sc, cand, lamp_of(L))
+    _, _, flag = oracle.irradiance(verts, tris, cen, nrm, excl, cand, L.offsets, L.weights, L.power)
+    ok = (flag == 0) & (flag[mc][:, mp] == 0)
+    # squares and products are sign-symmetric: the GPU mirror image is bitwise equal
+    assert np.array_equal(A[ok], A[mc][:, mp][ok])
+    sc.free()
+
+
+def test_half_plane_occluder_halves_visibility():
+    verts, tris, cen, nrm, excl, _ = _pins._half_plane_scene()
+    area = np.ones(cen.shape[0], np.float32)
+    sc = build_arrays(verts, tris, cen, nrm, area, excl)
+    A, visg = gpu_matrix(sc, np.array([[0, 0, 2]], np.float32), uvc.point_lamp(80.0))
+    assert np.array_equal(visg[0, :, 0], cen[:, 0] > 0)
+    assert np.all(A[0, cen[:, 0] < 0] == 0)
+    sc.free()
+
+
+def test_hand_checked_scene():
+    d, verts, tris, p = _pins._hand_scene()
+    cases = d["point_lamp_cases"]
+    cand = np.array([c["lamp"] for c in cases], np.float32)
+    sc = build_arrays(verts, tris, [p["centroid"]], [p["normal"]], [p["area"]], [p["excl"]])
+    A, visg = gpu_matrix(sc, cand, uvc.point_lamp(d["power_W"]))
+    for k, c in enumerate(cases):
+        want = _pins._expr(c["E"])
+        assert visg[k, 0, 0] == bool(c["visible"])
+        assert abs(A[k, 0] - want) <= 1e-6 * max(want, 1e-30), (c, A[k, 0], want)
+    sc.free()
+
+
+def test_ward_full_size_sampled_pairs():
+    """Full ward (2,000 x ~102k pairs, K=8, ~51k triangles) computed in the
+    benchmark's configuration; 1,500 seeded pairs checked against brute force."""
+    s = ward_room()
+    sc = build(s)
+    A, vis = uvc.irradiance_matrix(sc, T(s.cand), lamp_of(s.lamp), with_vis=True)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    rng = np.random.default_rng(7)
+    pairs = np.stack([rng.integers(0, s.nc, 1500), rng.integers(0, s.np_, 1500)], axis=1)
+    Ag = A[torch.from_numpy(pairs[:, 0]).cuda(), torch.from_numpy(pairs[:, 1]).cuda()].cpu().numpy()
+    v = vis.cpu().numpy().view(np.uint32)          # (K, nc, nwords)
+    words = v[:, pairs[:, 0], pairs[:, 1] // 32]     # (K, P)
+    visg = ((words >> (pairs[:, 1] % 32).astype(np.uint32)) & 1).astype(bool).T
+    E, ovis, flag = oracle.irradiance_scene(s, pairs=pairs)
+    st = compare_irradiance(Ag, visg, E, ovis, flag)
+    assert 0.05 < st["visible_frac"] < 0.95
+    # properties that hold at any size: finite, non-negative, zero where no source sees the patch
+    Af = A.cpu().numpy()
+    assert np.all(np.isfinite(Af)) and np.all(Af >= 0)
+    anyvis = np.zeros(Af.shape, bool)
+    full = uvc.vis_to_bool(vis, s.np_)
+    anyvis = full.any(axis=-1)
+    assert np.all(Af[~anyvis] == 0) and np.all(Af[anyvis] > 0)
+    sc.free()
+
+
+def test_lda_larger_than_np_leaves_padding_untouched():
+    s = tiny_room(n_cand=5)
+    sc = build(s)
+    A = torch.full((5, s.np_ + 7), -3.0, device="cuda")
+    uvc.irradiance_matrix(sc, T(s.cand), lamp_of(s.lamp), A=A)
+    torch.cuda.synchronize()
+    A0, _ = uvc.irradiance_matrix(sc, T(s.cand), lamp_of(s.lamp))
+    assert torch.equal(A[:, :s.np_], A0)
+    assert torch.all(A[:, s.np_:] == -3.0)
+    sc.free()
+
+
+def test_empty_and_degenerate_inputs():
+    s = tiny_room(n_cand=3)
+    # no occluders: every facing source is visible
+    sc = build_arrays(np.zeros((0, 3)), np.zeros((0, 3)), s.centroid, s.normal, s.area,
+                      -np.ones_like(s.excl))
+    A, visg = gpu_matrix(sc, s.cand, lamp_of(s.lamp))
+    E, ovis, flag = oracle.irradiance(np.zeros((0, 3)), np.zeros((0, 3)), s.centroid, s.normal,
+                                      -np.ones_like(s.excl), s.cand, s.lamp.offsets, s.lamp.weights, s.lamp.power)
+    compare_irradiance(A, visg, E, ovis, flag)
+    # with nothing to occlude, visible == facing (the table's far sides face away)
+    assert visg.mean() > 0.9
+    # nc = 0 is a no-op
+    A0, _ = uvc.irradiance_matrix(sc, torch.zeros((0, 3), device="cuda"), lamp_of(s.lamp))
+    assert A0.shape == (0, s.np_)
+    sc.free()
+    # one and two triangles
+    for k in (1, 2):
+        verts = np.array([[-1, -1, 1], [1, -1, 1], [0, 1, 1], [-1, 1, 1.5], [1, 1, 1.5], [0, 3, 1.5]], np.float32)
+        tris = np.arange(3 * k, dtype=np.int32).reshape(-1, 3)
+        rng = np.random.default_rng(k)
+        cen = np.concatenate([rng.uniform(-2, 2, (45, 2)), np.zeros((45, 1))], axis=1).astype(np.float32)
+        nrm = np.tile(np.array([[0, 0, 1]], np.float32), (45, 1))
+        ex = -np.ones((45, 2), np.int32)
+        cand = np.concatenate([rng.uniform(-1, 1, (9, 2)), np.full((9, 1), 2.5)], axis=1).astype(np.float32)
+        from synth.scenes import point_lamp
+        _full_parity(verts, tris, cen, nrm, np.ones(45, np.float32), ex, cand, point_lamp(10.0))
+
+
+def test_duplicate_triangles_identical_morton_keys():
+    """Many copies of the same occluder (equal keys; the tree splits by index)."""
+    tri = np.array([[-0.5, -0.5, 1], [0.5, -0.5, 1], [0, 0.5, 1]], np.float32)
+    verts = np.tile(tri, (300, 1))
+    tris = np.arange(900, dtype=np.int32).reshape(-1, 3)
+    g = np.linspace(-1.5, 1.5, 12)
+    cen = np.array([[x, y, 0] for x in g for y in g], np.float32)
+    nrm = np.tile(np.array([[0, 0, 1]], np.float32), (cen.shape[0], 1))
+    ex = -np.ones((cen.shape[0], 2), np.int32)
+    cand = np.array([[0.05, 0.02, 2.0], [0.9, -0.3, 2.5]], np.float32)
+    from synth.scenes import point_lamp
+    _full_parity(verts, tris, cen, nrm, np.ones(cen.shape[0], np.float32), ex, cand, point_lamp(50.0))
+
+
+def test_max_sources():
+    s = tiny_room(n_cand=4)
+    L = line_lamp(1.0, 32, 100.0)
+    cand = s.cand.copy()
+    cand[:, 2] = 0.9
+    _full_parity(s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, cand, L)
+
+
+def test_invalid_inputs_are_reported():
+    s = tiny_room(n_cand=2)
+    bad = s.tris.copy()
+    bad[3, 1] = s.verts.shape[0] + 5
+    with pytest.raises(uvc.UvcError) as e:
+        build_arrays(s.verts, bad, s.centroid, s.normal, s.area, s.excl)
+    assert e.value.status == uvc.uvc.UVC_E_INVAL
+    v = s.verts.copy()
+    v[0, 0] = np.nan
+    with pytest.raises(uvc.UvcError):
+        build_arrays(v, s.tris, s.centroid, s.normal, s.area, s.excl)
+    ex = s.excl.copy()
+    ex[0, 1] = s.nt
+    with pytest.raises(uvc.UvcError):
+        build_arrays(s.verts, s.tris, s.centroid, s.normal, s.area, ex)
+    sc = build(s)
+    with pytest.raises(uvc.UvcError):
+        uvc.irradiance_matrix(sc, T(s.cand), uvc.Lamp(np.zeros((1, 3)), [1.0], float("nan")))
+    sc.free()
