@@ -1,0 +1,440 @@
+#!/usr/bin/env python3
+"""Benchmark of the irradiance-matrix hot path (arXiv:2103.14137, Sec. IV-C).
+
+One step = one pass of the whole path over one synthetic ward-sized room:
+upload/build the scene hierarchy (uvc_build_scene), the occlusion-tested
+irradiance matrix with per-source visibility bits (uvc_irradiance_matrix),
+the fluence A^T t for 16 dwell vectors (uvc_fluence) and the covered-area
+fraction (uvc_coverage).  The metric is occlusion-tested (candidate, patch)
+pairs per second, in Gpairs/s, for the whole job.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload ward|tiny|large]
+
+Under torchrun (N > 1) every rank runs its own seeded room of the same size
+(independent problems, weak scaling, no data-path collective); rank 0 prints
+one JSON line.  `--impl reference` times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "irradiance-matrix Gpairs/s (occlusion-tested) and % roofline; rooms/sec batched+learned vs plain"
+UNIT = "Gpairs/s"
+MU_MIN = 100.0          # 10 mJ/cm^2
+NVEC = 16
+L2_BYTES = 129 * 2 ** 20
+# ALU work per segment operation (FP32 arithmetic, min/max and compare
+# instructions of the kernels, per lane): see the design doc for the count.
+OPS_BOX_TEST = 26
+OPS_TRI_TEST = 40
+OPS_SEGMENT_SETUP = 60
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["ward", "tiny", "large"], default="ward")
+    p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def make_workload(name: str, rank: int):
+    from synth import dwell_vectors, large_floor, tiny_room, ward_room
+    if name == "tiny":
+        s = tiny_room(seed=0 + 1000 * rank)
+    elif name == "large":
+        s = large_floor(seed=3 + 1000 * rank)
+    else:
+        s = ward_room(seed=1 + 1000 * rank)
+    nvec = 64 if name == "large" else NVEC
+    t = dwell_vectors(nvec, s.nc, seed=2 + 1000 * rank)
+    return s, t
+
+
+def workload_config(name, s, nvec, world):
+    desc = {
+        "ward": "plain method, ward-sized room: 10x8x3 m, 6 beds, 4 cabinets, 2 partitions; K=8 line lamp 1.2 m, P=120 W",
+        "tiny": "plain method, tiny room: 4x4x3 m with a table; point lamp P=80 W",
+        "large": "large floor: 30x30x3 m, 20 rooms + corridor; K=8 line lamp; streamed A^T t (A not stored)",
+    }[name]
+    return {"workload": desc, "triangles": s.nt, "patches": s.np_, "candidates": s.nc, "sources_K": s.lamp.K,
+            "dwell_vectors": nvec, "mu_min_J_m2": MU_MIN, "global_batch_rooms": world,
+            "parallelism": f"independent rooms x{world}" if world > 1 else "single GPU",
+            "l2": "flushed between steps (256 MiB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        load = [x for x in sm if x > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2103_14137_gb300 as uvc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    s, t_host = make_workload(args.workload, rank)
+    if args.candidates:
+        s.cand = s.cand[: args.candidates]
+        t_host = np.ascontiguousarray(t_host[:, : args.candidates])
+    nvec = t_host.shape[0]
+    lamp = uvc.Lamp(s.lamp.offsets, s.lamp.weights, s.lamp.power)
+    streamed = args.workload == "large"
+
+    host = {"verts": s.verts, "tris": s.tris, "centroid": s.centroid, "normal": s.normal, "area": s.area,
+            "excl": s.excl, "cand": s.cand, "t": t_host}
+    d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
+    nwords = (s.np_ + 31) // 32
+    A = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32, device=dev)
+    vis = None if streamed else torch.empty((s.lamp.K, s.nc, nwords), dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    launches_per_step = [0]
+
+    def step(irr_events=None):
+        sc = uvc.build_scene(d["verts"], d["tris"], d["centroid"], d["normal"], d["area"], d["excl"])
+        n = 2 + (28 if s.nt > 0 else 0) + (3 if s.nt > 1 else 0)
+        if irr_events:
+            irr_events[0].record(stream)
+        if streamed:
+            mu = uvc.fluence_streamed(sc, d["cand"], lamp, d["t"])
+            n += 2
+        else:
+            uvc.irradiance_matrix(sc, d["cand"], lamp, A=A, vis=vis)
+            n += 1
+        if irr_events:
+            irr_events[1].record(stream)
+        if not streamed:
+            mu = uvc.fluence(sc, A, d["t"])
+            n += (nvec + 15) // 16
+        ca, cc = uvc.coverage(sc, mu, MU_MIN)
+        n += 1
+        launches_per_step[0] = n
+        return sc, mu, ca
+
+    for _ in range(args.warmup):
+        sc, _, _ = step()
+        sc.free()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    step_ms, irr_ms = [], []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    wall0 = time.perf_counter()
+    scenes = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = ev(), ev()
+        ie = (ev(), ev())
+        a.record(stream)
+        sc, mu, ca = step(ie)
+        b.record(stream)
+        scenes.append(sc)
+        step_ms.append((a, b, ie))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    status = uvc.scene_status(scenes[-1])
+    for sc in scenes[:-1]:
+        sc.free()
+    per_step = [a.elapsed_time(b) for a, b, _ in step_ms]
+    irr_ms = [ie[0].elapsed_time(ie[1]) for _, _, ie in step_ms]
+    mean_ms = sum(per_step) / len(per_step)
+    cov = ca.cpu().numpy().tolist()
+    t_max = torch.tensor([mean_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step = float(t_max.item())
+    pairs = s.nc * s.np_
+    value = world * pairs / (ms_step * 1e-3) / 1e9
+
+    # instrumented run (outside timing) for the dominant kernel's algorithmic work
+    sc = scenes[-1]
+    if streamed:
+        roof = None
+        cnt = None
+    else:
+        cnt = uvc.irradiance_counters(sc, d["cand"], lamp, A=A)
+        segments = pairs * s.lamp.K
+        ops = (cnt["lane_box_tests"] * OPS_BOX_TEST + cnt["lane_tri_tests"] * OPS_TRI_TEST
+               + segments * OPS_SEGMENT_SETUP)
+        irr_s = (sum(irr_ms) / len(irr_ms)) * 1e-3
+        pk = measured_peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * sm_max * 1e6 / 1e12      # lane-instructions per second, in T/s
+        achieved = ops / irr_s / 1e12
+        traffic = measured_traffic(pairs)
+        roof = {"bound": "alu", "kernel": "k_irradiance", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "Tops/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
+                "ops_per_launch": ops, "launch_ms": round(irr_s * 1e3, 3),
+                "counters": cnt}
+    sc.free()
+
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args.workload, s, nvec, world),
+        "roofline": roof,
+        "clocks": clk,
+        "gpu_launches": launches_per_step[0] * args.steps,
+        "breakdown_ms": {"irradiance_or_streamed": round(sum(irr_ms) / len(irr_ms), 3),
+                         "rest_of_step": round(mean_ms - sum(irr_ms) / len(irr_ms), 3)},
+        "status": uvc.status_string(status),
+        "coverage_last_step": [round(c, 5) for c in cov[:4]],
+        "wall_s": round(wall, 3),
+    }
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(args, s, host, lamp, streamed, nvec, world, dist if world > 1 else None)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
+    """Same metric through the public API from pinned host buffers: inputs
+    copied host->device and results (A, mu, coverage) device->host inside the
+    timed region of every step."""
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    dev = torch.cuda.current_device()
+    pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
+    dbuf = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in pin.items()}
+    A = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32, device=dev)
+    A_host = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32).pin_memory()
+    mu_host = torch.empty((nvec, s.np_), dtype=torch.float32).pin_memory()
+    cov_host = torch.empty((nvec,), dtype=torch.float32).pin_memory()
+    h2d = sum(v.numel() * v.element_size() for v in pin.values())
+    d2h = mu_host.numel() * 4 + cov_host.numel() * 4 + (0 if streamed else A_host.numel() * 4)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for k in pin:
+            dbuf[k].copy_(pin[k], non_blocking=True)
+        sc = uvc.build_scene(dbuf["verts"], dbuf["tris"], dbuf["centroid"], dbuf["normal"], dbuf["area"],
+                             dbuf["excl"])
+        if streamed:
+            mu = uvc.fluence_streamed(sc, dbuf["cand"], lamp, dbuf["t"])
+        else:
+            uvc.irradiance_matrix(sc, dbuf["cand"], lamp, A=A)
+            mu = uvc.fluence(sc, A, dbuf["t"])
+            A_host.copy_(A, non_blocking=True)
+        ca, _ = uvc.coverage(sc, mu, MU_MIN)
+        mu_host.copy_(mu, non_blocking=True)
+        cov_host.copy_(ca, non_blocking=True)
+        return sc
+
+    for _ in range(max(1, min(args.warmup, 2))):
+        step().free()
+    torch.cuda.synchronize()
+    n = max(1, min(args.steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    scs = [step() for _ in range(n)]
+    b.record(stream)
+    torch.cuda.synchronize()
+    for sc in scs:
+        sc.free()
+    ms = a.elapsed_time(b) / n
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return {"value": round(world * s.nc * s.np_ / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
+            "steps": n}
+
+
+_KERNEL_FILES = ("irradiance.cu", "uvc_internal.cuh")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_irradiance_ward.txt")
+
+
+def measured_traffic(pairs):
+    """DRAM bytes of one full launch, scaled from the committed ncu summary of
+    a smaller launch of the same kernel (null once the kernel has changed)."""
+    try:
+        kv = dict(line.split(":", 1) for line in open(TRAFFIC_SUMMARY) if ":" in line)
+        if kv.get("kernel_source_hash", "").strip() != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_pair"]) * pairs
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in _KERNEL_FILES:
+        h.update(open(os.path.join(ROOT, "paper_2103_14137_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_rate(s, n_pairs, seed, threads):
+    import oracle
+    rng = np.random.default_rng(seed)
+    pairs = np.stack([rng.integers(0, s.nc, n_pairs), rng.integers(0, s.np_, n_pairs)], axis=1)
+    t0 = time.perf_counter()
+    oracle.irradiance_scene(s, pairs=pairs, flags=False, threads=threads)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(s, seconds: float):
+    """The FP64 brute-force oracle as it stands, on all host cores, on a seeded
+    sample of the workload's pairs sized to about `seconds` of CPU time."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.build()
+    probe = 64
+    dt = _oracle_rate(s, probe, 101, threads)
+    n = int(min(max(probe, probe * seconds / max(dt, 1e-6)), 2_000_000))
+    dt = _oracle_rate(s, n, 102, threads)
+    rate = n / dt
+    return {"value": round(rate / 1e9, 9), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{n} seeded (candidate, patch) pairs of the same workload, K={s.lamp.K} sources, "
+                      f"brute force against all {s.nt} triangles, FP64, {dt:.1f} s",
+            "threads_available": oracle.max_threads()}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    s, _ = make_workload(args.workload, 0)
+    import oracle
+    oracle.build()
+    threads = os.cpu_count() or 1
+    # size each step so that warmup + steps end within a few minutes
+    per_step_s = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    dt = _oracle_rate(s, 64, 7, threads)
+    n = int(min(max(64, 64 * per_step_s / max(dt, 1e-6)), 2_000_000))
+    for k in range(args.warmup):
+        _oracle_rate(s, max(64, n // 8), 1000 + k, threads)
+    times = [_oracle_rate(s, n, 2000 + k, threads) for k in range(args.steps)]
+    mean = sum(times) / len(times)
+    value = n / mean / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 9), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(args.workload, s, NVEC, 1),
+           "cpu_baseline": {"value": round(value, 9), "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": f"{n} seeded pairs per step, K={s.lamp.K}, brute force over {s.nt} triangles"},
+           "e2e": {"value": round(value, 9), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

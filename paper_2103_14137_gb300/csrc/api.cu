@@ -161,8 +161,9 @@ int uvc_scene_export_bvh(const uvc_scene* scene, uint64_t* keys, int32_t* order,
                     children[2 * k + 1] = h[k].r.y;
                 }
                 if (boxes) {
-                    const float v[12] = {h[k].a.x, h[k].a.y, h[k].a.z, h[k].a.w, h[k].b.x, h[k].b.y,
-                                         h[k].b.z, h[k].b.w, h[k].c.x, h[k].c.y, h[k].c.z, h[k].c.w};
+                    const uvc::Node& q = h[k];
+                    const float v[12] = {q.x.x, q.y.x, q.z.x, q.x.z, q.y.z, q.z.z,    // left lo, hi
+                                         q.x.y, q.y.y, q.z.y, q.x.w, q.y.w, q.z.w};   // right lo, hi
                     std::memcpy(boxes + 12 * k, v, sizeof(v));
                 }
             }

@@ -351,9 +351,9 @@ __global__ void k_pack_nodes(int n, const int2* __restrict__ children, const int
     float4 R0 = c.y < 0 ? leaf_lo[~c.y] : node_lo[c.y];
     float4 R1 = c.y < 0 ? leaf_hi[~c.y] : node_hi[c.y];
     Node nd;
-    nd.a = make_float4(L0.x, L0.y, L0.z, L1.x);
-    nd.b = make_float4(L1.y, L1.z, R0.x, R0.y);
-    nd.c = make_float4(R0.z, R1.x, R1.y, R1.z);
+    nd.x = make_float4(L0.x, R0.x, L1.x, R1.x);
+    nd.y = make_float4(L0.y, R0.y, L1.y, R1.y);
+    nd.z = make_float4(L0.z, R0.z, L1.z, R1.z);
     nd.r = make_int4(c.x, c.y, parent_int[i], 0);
     nodes[i] = nd;
 }

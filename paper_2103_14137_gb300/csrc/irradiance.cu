@@ -94,14 +94,15 @@ __device__ __forceinline__ void setup_ray(Ray& r) {
     r.sz = __fdiv_rn(1.0f, dkz);
 }
 
-// Does the segment overlap box [lo, hi] (conservatively)?
-__device__ __forceinline__ bool slab(const Ray& r, float lx, float ly, float lz, float hx, float hy, float hz) {
-    float t0x = __fmul_rn(__fsub_rn(lx, r.ox), r.ix), t1x = __fmul_rn(__fsub_rn(hx, r.ox), r.ix);
-    float t0y = __fmul_rn(__fsub_rn(ly, r.oy), r.iy), t1y = __fmul_rn(__fsub_rn(hy, r.oy), r.iy);
-    float t0z = __fmul_rn(__fsub_rn(lz, r.oz), r.iz), t1z = __fmul_rn(__fsub_rn(hz, r.oz), r.iz);
-    float tn = fmaxf(fmaxf(fminf(t0x, t1x), fminf(t0y, t1y)), fmaxf(fminf(t0z, t1z), 0.f));
-    float tf = fminf(fminf(fmaxf(t0x, t1x), fmaxf(t0y, t1y)), fminf(fmaxf(t0z, t1z), 1.f));
-    return tn <= tf * kFarScale;
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
 }
 
 // Watertight segment/triangle test: hit iff the segment's line passes through
@@ -140,14 +141,6 @@ __device__ __forceinline__ uint32_t test_leaf(const SceneView& S, int k, const R
     return __ballot_sync(kFull, hit);
 }
 
-__device__ __forceinline__ float box_dist2(float px, float py, float pz, float lx, float ly, float lz, float hx,
-                                           float hy, float hz) {
-    float dx = fmaxf(fmaxf(lx - px, px - hx), 0.f);
-    float dy = fmaxf(fmaxf(ly - py, py - hy), 0.f);
-    float dz = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
-    return dx * dx + dy * dy + dz * dz;
-}
-
 // Traversal counters of the instrumented variant (one launch, outside timing):
 // [0] warp node visits, [1] warp leaf tests, [2] warp traversals,
 // [3] lane box tests (alive lanes x 2 per node), [4] lane triangle tests,
@@ -156,9 +149,14 @@ constexpr int kNumCounters = 6;
 
 // Packet traversal: returns the lanes (of `alive`) whose segment is occluded;
 // lanes whose search hit the visit cap are returned in `failed`.
+//
+// Node test: both children's slab intervals at once with packed FP32x2
+// (t = (b - o) * (1/d), one rounding per operation), then per child
+// t_near = max(0, per-axis minima), t_far = min(1, per-axis maxima), and the
+// child is entered when t_near <= t_far * (1 + 2^-20) (conservative).
 template <bool COUNT>
 __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t alive, int* stack, int lane,
-                                  uint32_t& failed, unsigned long long* ctr) {
+                                  uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
     failed = 0;
     if (COUNT && lane == 0) atomicAdd(&ctr[5], (unsigned long long)__popc(alive));
     if (S.nt == 0 || alive == 0) return 0;
@@ -168,8 +166,12 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
             atomicAdd(&ctr[2], 1ull);
             atomicAdd(&ctr[4], (unsigned long long)__popc(alive));
         }
-        return test_leaf(S, ~S.root, r, alive, lane);
+        const uint32_t h = test_leaf(S, ~S.root, r, alive, lane);
+        if ((h >> lane) & 1u) hit_tri = ~S.root;
+        return h;
     }
+    const float2 nox = make_float2(-r.ox, -r.ox), noy = make_float2(-r.oy, -r.oy), noz = make_float2(-r.oz, -r.oz);
+    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
     uint32_t occl = 0;
     int top = 0, node = 0, visits = 0;
     unsigned long long c_leaf = 0, c_box = 0, c_tri = 0;
@@ -180,31 +182,47 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
             break;
         }
         const Node* nd = S.nodes + node;
-        float4 a = __ldg(&nd->a), b = __ldg(&nd->b), c = __ldg(&nd->c);
-        int4 rr = __ldg(&nd->r);
-        bool me = (alive >> lane) & 1u;
+        const float4 bx = __ldg(&nd->x), by = __ldg(&nd->y), bz = __ldg(&nd->z);
+        const int4 rr = __ldg(&nd->r);
+        const float2 t0x = __fmul2_rn(__fadd2_rn(make_float2(bx.x, bx.y), nox), ix);
+        const float2 t1x = __fmul2_rn(__fadd2_rn(make_float2(bx.z, bx.w), nox), ix);
+        const float2 t0y = __fmul2_rn(__fadd2_rn(make_float2(by.x, by.y), noy), iy);
+        const float2 t1y = __fmul2_rn(__fadd2_rn(make_float2(by.z, by.w), noy), iy);
+        const float2 t0z = __fmul2_rn(__fadd2_rn(make_float2(bz.x, bz.y), noz), iz);
+        const float2 t1z = __fmul2_rn(__fadd2_rn(make_float2(bz.z, bz.w), noz), iz);
+        const float tnL = max3f(fminf(t0x.x, t1x.x), fminf(t0y.x, t1y.x), fmaxf(fminf(t0z.x, t1z.x), 0.f));
+        const float tfL = min3f(fmaxf(t0x.x, t1x.x), fmaxf(t0y.x, t1y.x), fminf(fmaxf(t0z.x, t1z.x), 1.f));
+        const float tnR = max3f(fminf(t0x.y, t1x.y), fminf(t0y.y, t1y.y), fmaxf(fminf(t0z.y, t1z.y), 0.f));
+        const float tfR = min3f(fmaxf(t0x.y, t1x.y), fmaxf(t0y.y, t1y.y), fminf(fmaxf(t0z.y, t1z.y), 1.f));
+        const bool me = (alive >> lane) & 1u;
         if (COUNT) c_box += 2 * __popc(alive);
-        bool hl = me && slab(r, a.x, a.y, a.z, a.w, b.x, b.y);
-        bool hr = me && slab(r, b.z, b.w, c.x, c.y, c.z, c.w);
-        uint32_t ml = __ballot_sync(kFull, hl), mr = __ballot_sync(kFull, hr);
-        if (ml && rr.x < 0) {
-            if (COUNT) { ++c_leaf; c_tri += __popc(ml); }
-            uint32_t h = test_leaf(S, ~rr.x, r, ml, lane);
-            occl |= h; alive &= ~h; ml = 0;
+        uint32_t ml = __ballot_sync(kFull, me && tnL <= tfL * kFarScale);
+        uint32_t mr = __ballot_sync(kFull, me && tnR <= tfR * kFarScale);
+        // leaf children: test their triangle now (one copy of the test code)
+        const bool leafL = rr.x < 0, leafR = rr.y < 0;
+        uint32_t pend = (leafL && ml ? 1u : 0u) | (leafR && mr ? 2u : 0u);
+        while (pend) {
+            const int c = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const uint32_t m = (c ? mr : ml) & alive;
+            if (COUNT) { ++c_leaf; c_tri += __popc(m); }
+            const int leaf = ~(c ? rr.y : rr.x);
+            const uint32_t h = test_leaf(S, leaf, r, m, lane);
+            if ((h >> lane) & 1u) hit_tri = leaf;
+            occl |= h;
+            alive &= ~h;
         }
-        if (mr && rr.y < 0) {
-            if (COUNT) { ++c_leaf; c_tri += __popc(mr & alive); }
-            uint32_t h = test_leaf(S, ~rr.y, r, mr & alive, lane);
-            occl |= h; alive &= ~h; mr = 0;
-        }
+        if (leafL) ml = 0;
+        if (leafR) mr = 0;
         ml &= alive;
         mr &= alive;
         if (!alive) break;
         if (ml && mr) {
-            float dl = box_dist2(r.ox, r.oy, r.oz, a.x, a.y, a.z, a.w, b.x, b.y);
-            float dr = box_dist2(r.ox, r.oy, r.oz, b.z, b.w, c.x, c.y, c.z, c.w);
-            int first = dl <= dr ? rr.x : rr.y;
-            int second = dl <= dr ? rr.y : rr.x;
+            // near child first, judged on one lane that enters both
+            const int src = __ffs(ml & mr) - 1;
+            const float a = __shfl_sync(kFull, tnL, src), b = __shfl_sync(kFull, tnR, src);
+            const int first = a <= b ? rr.x : rr.y;
+            const int second = a <= b ? rr.y : rr.x;
             if (top >= S.stack_cap) {
                 failed = alive;
                 if (lane == 0) atomicCAS(S.status, 0, UVC_E_STACK);
@@ -234,23 +252,39 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
     return occl;
 }
 
+// The patch of one lane: sample point, normal, excluded triangles.
+struct PatchLane {
+    float4 s, n;
+    int2 ex;
+    bool valid;
+};
+
+__device__ __forceinline__ PatchLane load_patch(const SceneView& S, int j) {
+    PatchLane P;
+    P.valid = j < S.np;
+    P.s = make_float4(0.f, 0.f, 0.f, 0.f);
+    P.n = P.s;
+    P.ex = make_int2(-1, -1);
+    if (P.valid) {
+        P.s = __ldg(&S.ps[j]);
+        P.n = __ldg(&S.pn[j]);
+        P.ex = __ldg(&S.pe[j]);
+    }
+    return P;
+}
+
 // Irradiance of candidate i at this lane's patch (lanes beyond np give 0).
 // Writes the K visibility words when vis != nullptr.  Returns NaN for a lane
 // whose search failed (and records UVC_E_TIMEOUT / UVC_E_STACK).
+// `cache` is the lane's last occluding triangle (sorted index, -1 = none): it
+// is tested first, and a hit settles the segment without a traversal (the
+// same predicate the traversal would apply to that triangle).
 template <bool COUNT = false>
 __device__ __forceinline__ float irradiance_entry(const SceneView& S, const float* __restrict__ cand, int nc,
                                                   const LampDev& L, int i, int jb, int lane, int* stack,
-                                                  uint32_t* __restrict__ vis, int nwords,
-                                                  unsigned long long* ctr = nullptr) {
-    const int j = jb * 32 + lane;
-    const bool valid = j < S.np;
-    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f), n4 = s4;
-    int2 ex = make_int2(-1, -1);
-    if (valid) {
-        s4 = __ldg(&S.ps[j]);
-        n4 = __ldg(&S.pn[j]);
-        ex = __ldg(&S.pe[j]);
-    }
+                                                  uint32_t* __restrict__ vis, int nwords, const PatchLane& P,
+                                                  int& cache, unsigned long long* ctr = nullptr) {
+    const float4 s4 = P.s, n4 = P.n;
     const float cx = __ldg(&cand[3 * (size_t)i]), cy = __ldg(&cand[3 * (size_t)i + 1]),
                 cz = __ldg(&cand[3 * (size_t)i + 2]);
     float E = 0.f;
@@ -290,15 +324,24 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
         }
         const float nv = __fadd_rn(acc, err);
         const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
-        const bool facing = valid && nv > 0.f && d2 > 0.f;
+        const bool facing = P.valid && nv > 0.f && d2 > 0.f;
         Ray r;
         r.ox = ox; r.oy = oy; r.oz = oz;
         r.dx = -hx; r.dy = -hy; r.dz = -hz;
-        r.ex0 = ex.x; r.ex1 = ex.y;
+        r.ex0 = P.ex.x; r.ex1 = P.ex.y;
         setup_ray(r);
-        uint32_t failed;
+        bool cached_hit = false;
+        if (facing && cache >= 0) {
+            const float4* t = S.tri + 3 * (size_t)cache;
+            cached_hit = seg_tri(r, __ldg(t), __ldg(t + 1), __ldg(t + 2));
+        }
         const uint32_t facing_mask = __ballot_sync(kFull, facing);
-        const uint32_t occl = warp_occluded<COUNT>(S, r, facing_mask, stack, lane, failed, ctr);
+        const uint32_t cached_mask = __ballot_sync(kFull, cached_hit);
+        uint32_t failed;
+        int hit_tri = -1;
+        const uint32_t occl =
+            cached_mask | warp_occluded<COUNT>(S, r, facing_mask & ~cached_mask, stack, lane, failed, ctr, hit_tri);
+        if (hit_tri >= 0) cache = hit_tri;
         const uint32_t visible = facing_mask & ~occl & ~failed;
         if (vis && lane == 0) vis[((size_t)m * nc + i) * nwords + jb] = visible;
         if ((failed >> lane) & 1u) bad = true;
@@ -310,28 +353,38 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
     return bad ? __int_as_float(0x7fffffff) : E;
 }
 
+// Candidates per warp task: the warp keeps its 32 patches (and its occluder
+// cache) over this many consecutive candidates.
+constexpr int kCandPerTask = 8;
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kThreads) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
+__global__ void __launch_bounds__(kThreads, 4) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
                                                          LampDev L, float* __restrict__ A, int64_t lda,
                                                          uint32_t* __restrict__ vis, unsigned long long* ctr) {
     extern __shared__ int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
     const int njb = (S.np + 31) >> 5;
-    const int64_t ntask = (int64_t)nc * njb;
+    const int nchunk = (nc + kCandPerTask - 1) / kCandPerTask;
+    const int64_t ntask = (int64_t)nchunk * njb;
     for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
          task += (int64_t)gridDim.x * kWarpsPerBlock) {
-        const int i = (int)(task / njb), jb = (int)(task % njb);
-        const float E = irradiance_entry<COUNT>(S, cand, nc, L, i, jb, lane, stack, vis, njb, ctr);
+        const int jb = (int)(task / nchunk), ic = (int)(task % nchunk);
         const int j = jb * 32 + lane;
-        if (j < S.np) A[(size_t)i * lda + j] = E;
+        const PatchLane P = load_patch(S, j);
+        int cache = -1;
+        const int i1 = min(nc, (ic + 1) * kCandPerTask);
+        for (int i = ic * kCandPerTask; i < i1; ++i) {
+            const float E = irradiance_entry<COUNT>(S, cand, nc, L, i, jb, lane, stack, vis, njb, P, cache, ctr);
+            if (P.valid) A[(size_t)i * lda + j] = E;
+        }
     }
 }
 
 // Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
 // E values of up to 32 candidates are staged in shared memory, multiplied by
 // the dwell times and added to the chunk's partial sums partial[s][v][j].
-__global__ void __launch_bounds__(kThreads) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
+__global__ void __launch_bounds__(kThreads, 4) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,
                                                        float* __restrict__ partial, int nsplit, int chunk) {
     extern __shared__ int smem[];
@@ -344,11 +397,13 @@ __global__ void __launch_bounds__(kThreads) k_streamed(SceneView S, const float*
          task += (int64_t)gridDim.x * kWarpsPerBlock) {
         const int s = (int)(task / njb), jb = (int)(task % njb);
         const int j = jb * 32 + lane;
+        const PatchLane P = load_patch(S, j);
+        int cache = -1;
         const int i0 = s * chunk, i1 = min(nc, i0 + chunk);
         for (int ib = i0; ib < i1; ib += 32) {
             const int nb = min(32, i1 - ib);
             for (int q = 0; q < nb; ++q)
-                Et[q * 32 + lane] = irradiance_entry(S, cand, nc, L, ib + q, jb, lane, stack, nullptr, 0);
+                Et[q * 32 + lane] = irradiance_entry(S, cand, nc, L, ib + q, jb, lane, stack, nullptr, 0, P, cache);
             __syncwarp();
             if (j < S.np) {
                 for (int v = 0; v < nvec; ++v) {
@@ -395,7 +450,7 @@ int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const 
     SceneView S = view_of(sc);
     const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
     const int njb = (S.np + 31) / 32;
-    const int64_t ntask = nc * njb;
+    const int64_t ntask = ((nc + kCandPerTask - 1) / kCandPerTask) * njb;
     int grid = grid_for((const void*)k_irradiance<false>, smem);
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
     k_irradiance<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, vis, nullptr);
@@ -415,7 +470,7 @@ int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, cons
     }
     cudaError_t e = cudaMemsetAsync(dctr, 0, sizeof(unsigned long long) * kNumCounters, stream);
     const int njb = (S.np + 31) / 32;
-    const int64_t ntask = nc * njb;
+    const int64_t ntask = ((nc + kCandPerTask - 1) / kCandPerTask) * njb;
     int grid = grid_for((const void*)k_irradiance<true>, smem);
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (e == cudaSuccess) {

@@ -9,13 +9,15 @@
 namespace uvc {
 
 // One internal BVH node: the boxes of both children and both child
-// references, 64 bytes, loaded with four 16-byte loads.
-//   a = (L.lo.x, L.lo.y, L.lo.z, L.hi.x)
-//   b = (L.hi.y, L.hi.z, R.lo.x, R.lo.y)
-//   c = (R.lo.z, R.hi.x, R.hi.y, R.hi.z)
+// references, 64 bytes, loaded with four 16-byte loads.  Bounds are grouped
+// by axis with the left and right child side by side, so that both children
+// are tested with packed FP32x2 arithmetic:
+//   x = (L.lo.x, R.lo.x, L.hi.x, R.hi.x)
+//   y = (L.lo.y, R.lo.y, L.hi.y, R.hi.y)
+//   z = (L.lo.z, R.lo.z, L.hi.z, R.hi.z)
 //   r = (left ref, right ref, parent, 0); ref >= 0 internal node, ref < 0 leaf ~k
 struct __align__(16) Node {
-    float4 a, b, c;
+    float4 x, y, z;
     int4 r;
 };
 
