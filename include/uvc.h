@@ -47,6 +47,7 @@ typedef struct CUstream_st* uvc_stream_t; /* same type as cudaStream_t */
 #define UVC_E_CUDA 3     /* a CUDA runtime call failed (launch, copy, sync) */
 #define UVC_E_STACK 4    /* traversal stack would overflow (tree deeper than supported) */
 #define UVC_E_TIMEOUT 5  /* a traversal hit its node-visit cap; affected entries are NaN */
+#define UVC_E_SCRATCH 6  /* nvec*np too large for uvc_fluence_streamed_noalloc's fixed scratch */
 
 #define UVC_MAX_SOURCES 32
 
@@ -175,6 +176,31 @@ int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda,
  */
 int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
                          const float* t, int32_t nvec, float* mu, uvc_stream_t stream);
+
+/*
+ * uvc_fluence_streamed_noalloc - uvc_fluence_streamed for callers that cannot
+ * allocate device memory during the call: a host program whose own allocator
+ * already holds all the device memory it may use, or a control loop that
+ * forbids allocation after start-up because an allocation can block,
+ * synchronise the device or fail mid-run.  This call allocates nothing: the
+ * per-chunk partial sums go to one fixed device array of 64 MiB that the
+ * library defines (every GPU that loads the library holds it until exit).
+ * The paper has no counterpart; this is an interface convenience.
+ *
+ *   Same arguments, result and determinism as uvc_fluence_streamed; fewer
+ *   candidate chunks may be used (at most 64 MiB / (4 * nvec * np) of them),
+ *   so the last bits of mu may differ from uvc_fluence_streamed's.
+ *   Limit: 4 * nvec * np must not exceed 64 MiB (67,108,864 bytes), else
+ *   UVC_E_SCRATCH and nothing is launched.
+ *   The first call on a device looks up the array's device address for that
+ *   device (cudaGetSymbolAddress) and caches it; make that first call before
+ *   any stream capture.  All calls share the one array, which keeps the last
+ *   call's contents (each call writes every partial before reading it), so
+ *   calls whose work overlaps on the GPU (e.g. on two streams at once) race
+ *   and corrupt each other: serialise them.
+ */
+int uvc_fluence_streamed_noalloc(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                                 const float* t, int32_t nvec, float* mu, uvc_stream_t stream);
 
 /*
  * uvc_coverage - covered fraction of the surface for each dwell vector: the

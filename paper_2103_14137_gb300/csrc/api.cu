@@ -105,6 +105,17 @@ int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, 
     return uvc::fluence_streamed(scene, cand, nc, L, t, nvec, mu, (cudaStream_t)stream);
 }
 
+int uvc_fluence_streamed_noalloc(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                                 const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (scene->np == 0) return UVC_OK;
+    if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;
+    return uvc::fluence_streamed_noalloc(scene, cand, nc, L, t, nvec, mu, (cudaStream_t)stream);
+}
+
 int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu_min, float* cov_area,
                  float* cov_count, uvc_stream_t stream) {
     if (!scene || nvec < 1 || nvec > 65535 || !cov_area || !std::isfinite(mu_min)) return UVC_E_INVAL;
@@ -120,6 +131,7 @@ const char* uvc_status_string(int status) {
         case UVC_E_CUDA: return "CUDA runtime error";
         case UVC_E_STACK: return "traversal stack overflow";
         case UVC_E_TIMEOUT: return "traversal exceeded its node-visit cap";
+        case UVC_E_SCRATCH: return "problem too large for the fixed scratch of the allocation-free call";
         default: return "unknown status";
     }
 }

@@ -23,7 +23,9 @@
 //               the edge functions evaluated without contraction, and a
 //               conservatively widened slab test for the boxes.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 
 #include "uvc_internal.cuh"
 
@@ -513,6 +515,86 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(partial, stream);
     return status_from_cuda(e);
+}
+
+}  // namespace uvc
+
+// ---------------------------------------------------------------------------
+// Allocation-free streamed fluence
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory while they run: a host
+// application whose own allocator has already claimed the device memory it is
+// allowed to use, or a control loop that forbids allocation after start-up
+// because cudaMalloc/cudaMallocAsync may block, synchronise or fail at a bad
+// moment.  For them the chunk partial sums of the streamed fluence live in
+// this fixed array instead.  Every GPU that loads the library holds it until
+// the process exits.
+namespace uvc {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
+
+// Device address of g_noalloc_scratch per device ordinal, resolved once per
+// device (the host-side name of the array is only a stand-in, not a device
+// address).
+constexpr int kMaxDevices = 64;
+std::atomic<float*> g_noalloc_ptr[kMaxDevices];
+std::mutex g_noalloc_mutex;
+
+int noalloc_scratch(float** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        cudaGetLastError();
+        return UVC_E_CUDA;
+    }
+    float* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            void* addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+            if (e != cudaSuccess || !addr) {
+                cudaGetLastError();
+                return UVC_E_CUDA;
+            }
+            p = static_cast<float*>(addr);
+            g_noalloc_ptr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return UVC_OK;
+}
+
+}  // namespace
+
+int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
+                             int32_t nvec, float* mu, cudaStream_t stream) {
+    if (sc->np == 0) return UVC_OK;
+    const size_t per_split = sizeof(float) * (size_t)nvec * (size_t)sc->np;
+    if (per_split > kNoAllocScratchBytes) return UVC_E_SCRATCH;
+    float* partial = nullptr;
+    int rc = noalloc_scratch(&partial);
+    if (rc != UVC_OK) return rc;
+    SceneView S = view_of(sc);
+    if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, per_split, stream));
+    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap + sizeof(float) * kWarpsPerBlock * 32 * 32;
+    const int njb = (S.np + 31) / 32;
+    int grid = grid_for((const void*)k_streamed, smem);
+    const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
+    int64_t nsplit = (want + njb - 1) / njb;
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (nc + 31) / 32));
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (int64_t)(kNoAllocScratchBytes / per_split)));
+    const int chunk = (int)((nc + nsplit - 1) / nsplit);
+    nsplit = (nc + chunk - 1) / chunk;
+    const int64_t ntask = nsplit * njb;
+    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    // every partial is written before it is read, so the array needs no clearing
+    k_streamed<<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit, chunk);
+    const int64_t total = (int64_t)nvec * S.np;
+    k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
+    return status_from_cuda(cudaGetLastError());
 }
 
 }  // namespace uvc

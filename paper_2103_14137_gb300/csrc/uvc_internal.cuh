@@ -68,6 +68,8 @@ int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, cons
                         int64_t lda, unsigned long long* out6, cudaStream_t stream);
 int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
                      int32_t nvec, float* mu, cudaStream_t stream);
+int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
+                             int32_t nvec, float* mu, cudaStream_t stream);
 
 // fluence and coverage (fluence.cu)
 int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libuvc.so")
 MAX_SOURCES = 32
 
-UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT = range(6)
+UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT, UVC_E_SCRATCH = range(7)
 
 
 class UvcError(RuntimeError):
@@ -55,6 +55,7 @@ def library():
         "uvc_fluence": [P, P, i64, i64, P, i32, P, P],
         "uvc_irradiance_counters": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence_streamed": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
+        "uvc_fluence_streamed_noalloc": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
         "uvc_coverage": [P, P, i32, ctypes.c_float, P, P, P],
         "uvc_scene_status": [P, P],
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
@@ -232,6 +233,21 @@ def fluence_streamed(scene: Scene, cand, lamp: Lamp, t, mu=None, stream=None):
                                         ctypes.byref(L), _dev(t, torch.float32, "t", (nvec, nc)), nvec,
                                         _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
     _check(rc, "uvc_fluence_streamed")
+    return mu
+
+
+def fluence_streamed_noalloc(scene: Scene, cand, lamp: Lamp, t, mu, stream=None):
+    """fluence_streamed for callers that cannot allocate device memory during
+    the call (their allocator holds the device, or allocation is forbidden
+    after start-up): the library's partial sums go to its fixed 64 MiB device
+    array.  `mu` (nvec, np) must be supplied by the caller; nothing is
+    allocated here.  Raises UvcError(UVC_E_SCRATCH) when 4*nvec*np > 64 MiB."""
+    nvec, nc = t.shape
+    L = lamp._c()
+    rc = library().uvc_fluence_streamed_noalloc(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                                ctypes.byref(L), _dev(t, torch.float32, "t", (nvec, nc)), nvec,
+                                                _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
+    _check(rc, "uvc_fluence_streamed_noalloc")
     return mu
 
 
