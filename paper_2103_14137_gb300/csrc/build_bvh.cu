@@ -49,6 +49,8 @@ __global__ void k_prepare_tris(const float* __restrict__ verts, int64_t nv, cons
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned int mn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu};
     unsigned int mx[3] = {0u, 0u, 0u};
+    unsigned int bmn[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu};
+    unsigned int bmx[3] = {0u, 0u, 0u};
     if (t < nt) {
         int ia = tris[3 * t], ib = tris[3 * t + 1], ic = tris[3 * t + 2];
         float3 lo = make_float3(0.f, 0.f, 0.f), hi = lo, p = lo;
@@ -66,6 +68,8 @@ __global__ void k_prepare_tris(const float* __restrict__ verts, int64_t nv, cons
             mn[0] = mx[0] = float_to_ordered(p.x);
             mn[1] = mx[1] = float_to_ordered(p.y);
             mn[2] = mx[2] = float_to_ordered(p.z);
+            bmn[0] = float_to_ordered(lo.x); bmn[1] = float_to_ordered(lo.y); bmn[2] = float_to_ordered(lo.z);
+            bmx[0] = float_to_ordered(hi.x); bmx[1] = float_to_ordered(hi.y); bmx[2] = float_to_ordered(hi.z);
         }
         tri_lo[t] = make_float4(lo.x, lo.y, lo.z, 0.f);
         tri_hi[t] = make_float4(hi.x, hi.y, hi.z, 0.f);
@@ -74,9 +78,13 @@ __global__ void k_prepare_tris(const float* __restrict__ verts, int64_t nv, cons
     for (int k = 0; k < 3; ++k) {
         unsigned int a = __reduce_min_sync(0xffffffffu, mn[k]);
         unsigned int b = __reduce_max_sync(0xffffffffu, mx[k]);
+        unsigned int c = __reduce_min_sync(0xffffffffu, bmn[k]);
+        unsigned int d = __reduce_max_sync(0xffffffffu, bmx[k]);
         if ((threadIdx.x & 31) == 0) {
             if (a != 0xffffffffu) atomicMin(&bounds[k], a);
             if (b != 0u) atomicMax(&bounds[3 + k], b);
+            if (c != 0xffffffffu) atomicMin(&bounds[6 + k], c);
+            if (d != 0u) atomicMax(&bounds[9 + k], d);
         }
     }
 }
@@ -358,6 +366,115 @@ __global__ void k_pack_nodes(int n, const int2* __restrict__ children, const int
     nodes[i] = nd;
 }
 
+// Clearance of each patch: a lower bound on the distance from its sample
+// point s_j to the nearest triangle that could occlude a segment ending at
+// s_j.  Excluded triangles never occlude.  A triangle lying exactly in the
+// patch's plane cannot meet a segment that arrives from the free side except
+// at s_j itself (tau = 1, outside the open segment), so it is ignored unless
+// it comes within `margin` of s_j in the plane (then the clearance is 0).  The
+// plane test is exact: it applies when the patch normal is an exact axis
+// vector and all three vertices share s_j's coordinate on that axis.  Other
+// triangles count with the distance to their bounding box (a lower bound).
+// The traversal uses the clearance to stop box tests that far short of s_j.
+__device__ __forceinline__ float box_dist2(float px, float py, float pz, float lx, float ly, float lz, float hx,
+                                           float hy, float hz) {
+    const float dx = fmaxf(fmaxf(lx - px, px - hx), 0.f);
+    const float dy = fmaxf(fmaxf(ly - py, py - hy), 0.f);
+    const float dz = fmaxf(fmaxf(lz - pz, pz - hz), 0.f);
+    return dx * dx + dy * dy + dz * dz;
+}
+
+__device__ __forceinline__ float seg2_dist2(float px, float py, float ax, float ay, float bx, float by) {
+    const float ux = bx - ax, uy = by - ay;
+    const float L = ux * ux + uy * uy;
+    float t = L > 0.f ? ((px - ax) * ux + (py - ay) * uy) / L : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    const float dx = ax + t * ux - px, dy = ay + t * uy - py;
+    return dx * dx + dy * dy;
+}
+
+// 2-D distance^2 from p to triangle (a, b, c) (0 inside).
+__device__ float tri2_dist2(float px, float py, float ax, float ay, float bx, float by, float cx, float cy) {
+    const float e0 = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+    const float e1 = (cx - bx) * (py - by) - (cy - by) * (px - bx);
+    const float e2 = (ax - cx) * (py - cy) - (ay - cy) * (px - cx);
+    if ((e0 >= 0.f && e1 >= 0.f && e2 >= 0.f) || (e0 <= 0.f && e1 <= 0.f && e2 <= 0.f)) return 0.f;
+    return fminf(seg2_dist2(px, py, ax, ay, bx, by), fminf(seg2_dist2(px, py, bx, by, cx, cy),
+                                                           seg2_dist2(px, py, cx, cy, ax, ay)));
+}
+
+__device__ __forceinline__ float tri_box_dist2(float px, float py, float pz, float4 a, float4 b, float4 c) {
+    return box_dist2(px, py, pz, fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y),
+                     fminf(fminf(a.z, b.z), c.z), fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y),
+                     fmaxf(fmaxf(a.z, b.z), c.z));
+}
+
+// One thread per patch: depth-first nearest search, nearer child first,
+// pruning boxes that are no closer than the best distance so far.
+constexpr int kClearStack = 128;
+
+__global__ void k_clearance(const Node* __restrict__ nodes, const float4* __restrict__ tri, int nt,
+                            const float4* __restrict__ ps, float4* __restrict__ pn, const int2* __restrict__ pe,
+                            int np, float margin) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    const float4 s4 = ps[j];
+    float4 n4 = pn[j];
+    const int2 ex = pe[j];
+    int ax = -1;
+    if (fabsf(n4.x) == 1.f && n4.y == 0.f && n4.z == 0.f) ax = 0;
+    if (fabsf(n4.y) == 1.f && n4.x == 0.f && n4.z == 0.f) ax = 1;
+    if (fabsf(n4.z) == 1.f && n4.x == 0.f && n4.y == 0.f) ax = 2;
+    const float sk = ax == 0 ? s4.x : (ax == 1 ? s4.y : s4.z);
+    const float su = ax == 0 ? s4.y : s4.x, sv = ax == 2 ? s4.y : s4.z;   // in-plane coordinates
+    const float margin2 = margin * margin;
+    float best = 3.0e38f;
+    int stack[kClearStack];
+    int top = 0;
+    if (nt > 1) stack[top++] = 0;
+    else if (nt == 1) stack[top++] = ~0;
+    int guard = 0;
+    while (top > 0 && best > 0.f) {
+        if (++guard > 4 * nt + 64) { best = 0.f; break; }   // cannot happen on a valid tree; 0 = no trimming
+        const int ref = stack[--top];
+        if (ref < 0) {
+            const int k = ~ref;
+            const float4 a = tri[3 * k], b = tri[3 * k + 1], c = tri[3 * k + 2];
+            const int id = __float_as_int(a.w);
+            if (id == ex.x || id == ex.y) continue;
+            const float d2 = tri_box_dist2(s4.x, s4.y, s4.z, a, b, c);
+            if (d2 >= best) continue;
+            bool coplanar = false;
+            if (ax >= 0) {
+                const float ak = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+                const float bk = ax == 0 ? b.x : (ax == 1 ? b.y : b.z);
+                const float ck = ax == 0 ? c.x : (ax == 1 ? c.y : c.z);
+                coplanar = ak == sk && bk == sk && ck == sk;
+            }
+            if (coplanar) {
+                const float au = ax == 0 ? a.y : a.x, av = ax == 2 ? a.y : a.z;
+                const float bu = ax == 0 ? b.y : b.x, bv = ax == 2 ? b.y : b.z;
+                const float cu = ax == 0 ? c.y : c.x, cv = ax == 2 ? c.y : c.z;
+                if (tri2_dist2(su, sv, au, av, bu, bv, cu, cv) <= margin2) best = 0.f;
+            } else {
+                best = d2;
+            }
+            continue;
+        }
+        const Node nd = nodes[ref];
+        const float dL = box_dist2(s4.x, s4.y, s4.z, nd.x.x, nd.y.x, nd.z.x, nd.x.z, nd.y.z, nd.z.z);
+        const float dR = box_dist2(s4.x, s4.y, s4.z, nd.x.y, nd.y.y, nd.z.y, nd.x.w, nd.y.w, nd.z.w);
+        const bool lfirst = dL <= dR;
+        const int far_ref = lfirst ? nd.r.y : nd.r.x, near_ref = lfirst ? nd.r.x : nd.r.y;
+        const float far_d = lfirst ? dR : dL, near_d = lfirst ? dL : dR;
+        if (top + 2 > kClearStack) { best = 0.f; break; }
+        if (far_d < best) stack[top++] = far_ref;
+        if (near_d < best) stack[top++] = near_ref;
+    }
+    n4.w = sqrtf(best);
+    pn[j] = n4;
+}
+
 struct Carver {
     char* base;
     size_t off = 0;
@@ -425,7 +542,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     2 * align256(sizeof(float4) * (size_t)n) +               // leaf lo/hi
                     2 * align256(sizeof(float4) * (size_t)ni) +              // node lo/hi
                     2 * align256(sizeof(int) * (size_t)ni) +                 // height, flags
-                    align256(sizeof(unsigned int) * 6) + align256(sizeof(int) * 2) + 256;
+                    align256(sizeof(unsigned int) * 12) + align256(sizeof(int) * 2) + 256;
     void* tblock = nullptr;
     if (cudaMallocAsync(&tblock, tbytes, stream) != cudaSuccess) {
         cudaGetLastError();
@@ -451,11 +568,12 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     float4* node_hi = tc.take<float4>(ni);
     int* height = tc.take<int>(ni);
     int* flags = tc.take<int>(ni);
-    unsigned int* bounds = tc.take<unsigned int>(6);
+    unsigned int* bounds = tc.take<unsigned int>(12);   // reference points lo/hi, triangle boxes lo/hi
     int* errdepth = tc.take<int>(2);   // [0] = error bits, [1] = depth
 
     cudaError_t e = cudaSuccess;
-    unsigned int init_bounds[6] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
+    unsigned int init_bounds[12] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u,
+                                    0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u};
     e = cudaMemcpyAsync(bounds, init_bounds, sizeof(init_bounds), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(errdepth, 0, 2 * sizeof(int), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sc->status, 0, sizeof(int), stream);
@@ -490,6 +608,32 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
             k_pack_nodes<<<(ni + B - 1) / B, B, 0, stream>>>(n, children, parent_int, leaf_lo, leaf_hi, node_lo,
                                                              node_hi, sc->nodes);
         }
+        e = cudaGetLastError();
+    }
+    // scene diameter (host) for the clearance margin and the traversal's cut tolerance
+    unsigned int host_bounds[12];
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_bounds, bounds, sizeof(host_bounds), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    float diam = 0.f;
+    if (e == cudaSuccess && n > 0) {
+        double d2 = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            const unsigned int lo_u = host_bounds[6 + k], hi_u = host_bounds[9 + k];
+            float lo_f, hi_f;
+            unsigned int a = (lo_u & 0x80000000u) ? (lo_u & 0x7fffffffu) : ~lo_u;
+            unsigned int b = (hi_u & 0x80000000u) ? (hi_u & 0x7fffffffu) : ~hi_u;
+            std::memcpy(&lo_f, &a, 4);
+            std::memcpy(&hi_f, &b, 4);
+            const double ext = (double)hi_f - (double)lo_f;
+            if (std::isfinite(ext)) d2 += ext * ext;
+        }
+        diam = (float)std::sqrt(d2);
+    }
+    sc->diameter = diam;
+    if (e == cudaSuccess && np > 0) {
+        // a patch closer than 2^-14 of the scene diameter to a coplanar triangle gets no clearance
+        k_clearance<<<(int)((np + B - 1) / B), B, 0, stream>>>(sc->nodes, sc->tri, n, sc->patch_s, sc->patch_n,
+                                                               sc->patch_excl, (int)np, diam * 6.103515625e-05f);
         e = cudaGetLastError();
     }
     int host_ed[2] = {0, 0};

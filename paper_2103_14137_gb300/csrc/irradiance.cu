@@ -32,6 +32,15 @@
 namespace uvc {
 namespace {
 
+// Resident blocks per SM the traversal kernels are compiled for (register cap
+// 65536 / (256 * this)); tuning constants, measured on the ward workload.
+#ifndef UVC_IRR_MIN_BLOCKS
+#define UVC_IRR_MIN_BLOCKS 3
+#endif
+#ifndef UVC_STREAMED_MIN_BLOCKS
+#define UVC_STREAMED_MIN_BLOCKS 4
+#endif
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr float kFourPi = 12.566370614359172f;
 // 1 + 2^-20: widening of the far slab distance; covers the relative rounding
@@ -45,6 +54,7 @@ struct SceneView {
     const float4* __restrict__ pn;
     const int2* __restrict__ pe;
     int nt, np, root, stack_cap, visit_cap;
+    float cut_eps;   // absolute slack (metres) subtracted from a patch's clearance
     int* status;
 };
 
@@ -60,6 +70,7 @@ SceneView view_of(const uvc_scene* sc) {
     v.root = sc->root;
     v.stack_cap = sc->depth + 1;
     v.visit_cap = (int)sc->nt + 64;
+    v.cut_eps = 1e-5f * sc->diameter;
     v.status = sc->status;
     return v;
 }
@@ -69,6 +80,7 @@ struct Ray {
     float dx, dy, dz;   // segment vector: end = start + d
     float ix, iy, iz;   // 1/d with zero components replaced by +-1e-30
     float sx, sy, sz;   // shear constants of the watertight test
+    float tend;         // box tests stop at this segment parameter (<= 1), see clearance
     int kx, ky, kz;     // axis permutation of the watertight test
     int ex0, ex1;       // triangles that never occlude this segment
 };
@@ -154,8 +166,10 @@ constexpr int kNumCounters = 6;
 //
 // Node test: both children's slab intervals at once with packed FP32x2
 // (t = (b - o) * (1/d), one rounding per operation), then per child
-// t_near = max(0, per-axis minima), t_far = min(1, per-axis maxima), and the
+// t_near = max(0, per-axis minima), t_far = min(tend, per-axis maxima), and the
 // child is entered when t_near <= t_far * (1 + 2^-20) (conservative).
+// tend < 1 skips the part of the segment next to the patch point that lies
+// within the patch's clearance: no triangle there can occlude it (k_clearance).
 template <bool COUNT>
 __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t alive, int* stack, int lane,
                                   uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
@@ -193,9 +207,9 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
         const float2 t0z = __fmul2_rn(__fadd2_rn(make_float2(bz.x, bz.y), noz), iz);
         const float2 t1z = __fmul2_rn(__fadd2_rn(make_float2(bz.z, bz.w), noz), iz);
         const float tnL = max3f(fminf(t0x.x, t1x.x), fminf(t0y.x, t1y.x), fmaxf(fminf(t0z.x, t1z.x), 0.f));
-        const float tfL = min3f(fmaxf(t0x.x, t1x.x), fmaxf(t0y.x, t1y.x), fminf(fmaxf(t0z.x, t1z.x), 1.f));
+        const float tfL = min3f(fmaxf(t0x.x, t1x.x), fmaxf(t0y.x, t1y.x), fminf(fmaxf(t0z.x, t1z.x), r.tend));
         const float tnR = max3f(fminf(t0x.y, t1x.y), fminf(t0y.y, t1y.y), fmaxf(fminf(t0z.y, t1z.y), 0.f));
-        const float tfR = min3f(fmaxf(t0x.y, t1x.y), fmaxf(t0y.y, t1y.y), fminf(fmaxf(t0z.y, t1z.y), 1.f));
+        const float tfR = min3f(fmaxf(t0x.y, t1x.y), fmaxf(t0y.y, t1y.y), fminf(fmaxf(t0z.y, t1z.y), r.tend));
         const bool me = (alive >> lane) & 1u;
         if (COUNT) c_box += 2 * __popc(alive);
         uint32_t ml = __ballot_sync(kFull, me && tnL <= tfL * kFarScale);
@@ -256,7 +270,7 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
 
 // The patch of one lane: sample point, normal, excluded triangles.
 struct PatchLane {
-    float4 s, n;
+    float4 s, n;   // n.w = clearance (metres)
     int2 ex;
     bool valid;
 };
@@ -326,29 +340,35 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
         }
         const float nv = __fadd_rn(acc, err);
         const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+        const float d = sqrtf(d2);
         const bool facing = P.valid && nv > 0.f && d2 > 0.f;
         Ray r;
         r.ox = ox; r.oy = oy; r.oz = oz;
         r.dx = -hx; r.dy = -hy; r.dz = -hz;
         r.ex0 = P.ex.x; r.ex1 = P.ex.y;
         setup_ray(r);
+        // the last `cut` metres before the patch point need no box tests; a
+        // segment shorter than the cut meets no triangle at all
+        const float cut = __fmaf_rn(0.99f, P.n.w, -S.cut_eps);
+        r.tend = cut > 0.f ? 1.f - cut * __frcp_rn(d) : 1.f;
+        const bool settled = facing && r.tend <= 0.f;
         bool cached_hit = false;
-        if (facing && cache >= 0) {
+        if (facing && !settled && cache >= 0) {
             const float4* t = S.tri + 3 * (size_t)cache;
             cached_hit = seg_tri(r, __ldg(t), __ldg(t + 1), __ldg(t + 2));
         }
         const uint32_t facing_mask = __ballot_sync(kFull, facing);
         const uint32_t cached_mask = __ballot_sync(kFull, cached_hit);
+        const uint32_t settled_mask = __ballot_sync(kFull, settled);
         uint32_t failed;
         int hit_tri = -1;
-        const uint32_t occl =
-            cached_mask | warp_occluded<COUNT>(S, r, facing_mask & ~cached_mask, stack, lane, failed, ctr, hit_tri);
+        const uint32_t occl = cached_mask | warp_occluded<COUNT>(S, r, facing_mask & ~cached_mask & ~settled_mask,
+                                                                 stack, lane, failed, ctr, hit_tri);
         if (hit_tri >= 0) cache = hit_tri;
         const uint32_t visible = facing_mask & ~occl & ~failed;
         if (vis && lane == 0) vis[((size_t)m * nc + i) * nwords + jb] = visible;
         if ((failed >> lane) & 1u) bad = true;
         if ((visible >> lane) & 1u) {
-            const float d = sqrtf(d2);
             E = __fadd_rn(E, __fmul_rn(L.pw[m], __fdiv_rn(nv, __fmul_rn(__fmul_rn(kFourPi, d2), d))));
         }
     }
@@ -360,7 +380,7 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
 constexpr int kCandPerTask = 8;
 
 template <bool COUNT>
-__global__ void __launch_bounds__(kThreads, 4) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
+__global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
                                                          LampDev L, float* __restrict__ A, int64_t lda,
                                                          uint32_t* __restrict__ vis, unsigned long long* ctr) {
     extern __shared__ int smem[];
@@ -386,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_irradiance(SceneView S, const f
 // Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
 // E values of up to 32 candidates are staged in shared memory, multiplied by
 // the dwell times and added to the chunk's partial sums partial[s][v][j].
-__global__ void __launch_bounds__(kThreads, 4) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
+__global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,
                                                        float* __restrict__ partial, int nsplit, int chunk) {
     extern __shared__ int smem[];

@@ -35,6 +35,7 @@ struct uvc_scene {
     int64_t nt = 0, np = 0;
     int32_t depth = 0;     // edges from the root to the deepest leaf
     int32_t root = 0;      // root reference (0, or ~0 for a single triangle)
+    float diameter = 0.f;  // diagonal of the triangles' bounding box
     // device buffers, carved out of one allocation
     void* block = nullptr;
     float4* tri = nullptr;        // [nt][3]: (v0, id bits), (v1, 0), (v2, 0) in sorted order
@@ -42,7 +43,7 @@ struct uvc_scene {
     uint64_t* keys = nullptr;     // [nt] sorted Morton keys
     int32_t* order = nullptr;     // [nt] triangle index per sorted position
     float4* patch_s = nullptr;    // [np] (centroid, area)
-    float4* patch_n = nullptr;    // [np] (normal, 0)
+    float4* patch_n = nullptr;    // [np] (normal, clearance): see k_clearance
     int2* patch_excl = nullptr;   // [np]
     float* area_total = nullptr;  // [1]
     int* status = nullptr;        // [1] device status word (0 = ok)

@@ -1,0 +1,71 @@
+"""The large floor (30x30x3 m, ~2M triangles, ~1M patches, K=8) at full size:
+the hierarchy over all triangles, irradiance entries of a candidate subset
+checked against brute force on sampled pairs, and the streamed fluence
+checked for the properties that hold at any size (consistency with the
+materialised path on the same candidates, linearity in t, non-negativity)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2103_14137_gb300 as uvc
+from synth import dwell_vectors, large_floor
+from tests._compare import compare_irradiance
+from tests.gpu_util import T, build, lamp_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def large():
+    s = large_floor()
+    sc = build(s)
+    yield s, sc
+    sc.free()
+
+
+def test_large_sampled_pairs_against_oracle(large):
+    s, sc = large
+    sub = np.arange(0, s.nc, s.nc // 24)[:24]           # 24 candidates spread over the floor
+    cand = T(s.cand[sub])
+    A, vis = uvc.irradiance_matrix(sc, cand, lamp_of(s.lamp), with_vis=True)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    rng = np.random.default_rng(11)
+    # pairs near each candidate (same room) and random ones
+    pi = rng.integers(0, len(sub), 160)
+    d2 = None
+    pj = rng.integers(0, s.np_, 160)
+    near = []
+    for k in range(len(sub)):
+        dd = np.sum((s.centroid - s.cand[sub[k]]) ** 2, axis=1)
+        near.extend([(k, j) for j in np.argsort(dd)[:2000][rng.integers(0, 2000, 6)]])
+    pairs = np.concatenate([np.stack([pi, pj], 1), np.array(near)])
+    Ag = A[torch.from_numpy(pairs[:, 0]).cuda(), torch.from_numpy(pairs[:, 1]).cuda()].cpu().numpy()
+    v = vis.cpu().numpy().view(np.uint32)
+    words = v[:, pairs[:, 0], pairs[:, 1] // 32]
+    visg = ((words >> (pairs[:, 1] % 32).astype(np.uint32)) & 1).astype(bool).T
+    opairs = np.stack([sub[pairs[:, 0]], pairs[:, 1]], 1)
+    E, ovis, flag = oracle.irradiance_scene(s, pairs=opairs)
+    st = compare_irradiance(Ag, visg, E, ovis, flag)
+    assert st["visible_frac"] > 0.02
+
+
+def test_large_streamed_properties(large):
+    s, sc = large
+    sub = np.arange(0, 96)
+    cand = T(s.cand[sub])
+    lamp = lamp_of(s.lamp)
+    t1 = dwell_vectors(64, len(sub), seed=5)
+    t2 = dwell_vectors(64, len(sub), seed=6)
+    mu1 = uvc.fluence_streamed(sc, cand, lamp, T(t1))
+    mu2 = uvc.fluence_streamed(sc, cand, lamp, T(t2))
+    mu12 = uvc.fluence_streamed(sc, cand, lamp, T(t1 + t2))
+    A, _ = uvc.irradiance_matrix(sc, cand, lamp)
+    mu_m = uvc.fluence(sc, A, T(t1))
+    torch.cuda.synchronize()
+    a, b, c, m = (x.cpu().numpy().astype(np.float64) for x in (mu1, mu2, mu12, mu_m))
+    assert np.all(np.isfinite(a)) and np.all(a >= 0)
+    scale = np.maximum(np.abs(a), 1e-30)
+    assert np.max(np.abs(a - m) / scale) <= 1e-5            # streamed == materialised
+    assert np.max(np.abs(c - (a + b)) / np.maximum(c, 1e-30)) <= 1e-5   # linear in t
