@@ -40,7 +40,7 @@ NVEC = 16
 L2_BYTES = 129 * 2 ** 20
 # ALU work per segment operation (FP32 arithmetic, min/max and compare
 # instructions of the kernels, per lane): see the design doc for the count.
-OPS_BOX_TEST = 26
+OPS_BOX_TEST = 18
 OPS_TRI_TEST = 40
 OPS_SEGMENT_SETUP = 60
 

@@ -366,6 +366,66 @@ __global__ void k_pack_nodes(int n, const int2* __restrict__ children, const int
     nodes[i] = nd;
 }
 
+// Depth of every internal node (edges from the root), by walking up.
+__global__ void k_node_depth(int n, const int* __restrict__ parent_int, int* __restrict__ depth) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    int d = 0;
+    int p = parent_int[i];
+    while (p >= 0 && d < n) {
+        ++d;
+        p = parent_int[p];
+    }
+    depth[i] = d;
+}
+
+// Collapse to the four-wide tree: every internal node at even depth gets a
+// four-wide node holding its children (leaf children) or grandchildren.
+__global__ void k_collapse4(int n, const Node* __restrict__ nodes, const int* __restrict__ depth,
+                            Node4* __restrict__ nodes4) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1 || (depth[i] & 1)) return;
+    const Node nd = nodes[i];
+    float lo[4][3], hi[4][3];
+    int ref[4];
+    const float far = 1e30f;
+    for (int c = 0; c < 2; ++c) {
+        const int r = c ? nd.r.y : nd.r.x;
+        const float clo[3] = {c ? nd.x.y : nd.x.x, c ? nd.y.y : nd.y.x, c ? nd.z.y : nd.z.x};
+        const float chi[3] = {c ? nd.x.w : nd.x.z, c ? nd.y.w : nd.y.z, c ? nd.z.w : nd.z.z};
+        if (r < 0) {
+            ref[2 * c] = r;
+            ref[2 * c + 1] = kEmptyChild;
+            for (int k = 0; k < 3; ++k) {
+                lo[2 * c][k] = clo[k];
+                hi[2 * c][k] = chi[k];
+                lo[2 * c + 1][k] = far;
+                hi[2 * c + 1][k] = far;
+            }
+        } else {
+            const Node g = nodes[r];
+            ref[2 * c] = g.r.x;
+            ref[2 * c + 1] = g.r.y;
+            lo[2 * c][0] = g.x.x; lo[2 * c][1] = g.y.x; lo[2 * c][2] = g.z.x;
+            hi[2 * c][0] = g.x.z; hi[2 * c][1] = g.y.z; hi[2 * c][2] = g.z.z;
+            lo[2 * c + 1][0] = g.x.y; lo[2 * c + 1][1] = g.y.y; lo[2 * c + 1][2] = g.z.y;
+            hi[2 * c + 1][0] = g.x.w; hi[2 * c + 1][1] = g.y.w; hi[2 * c + 1][2] = g.z.w;
+        }
+    }
+    Node4 o;
+    for (int h = 0; h < 2; ++h)
+        for (int k = 0; k < 3; ++k)
+            o.q[3 * h + k] = make_float4(lo[2 * h][k], lo[2 * h + 1][k], hi[2 * h][k], hi[2 * h + 1][k]);
+    o.r = make_int4(ref[0], ref[1], ref[2], ref[3]);
+    int leafmask = 0, innermask = 0;
+    for (int c = 0; c < 4; ++c) {
+        if (ref[c] < 0) leafmask |= 1 << c;
+        else if (ref[c] != kEmptyChild) innermask |= 1 << c;
+    }
+    o.m = make_int4(leafmask, innermask, 0, 0);
+    nodes4[i] = o;
+}
+
 // Clearance of each patch: a lower bound on the distance from its sample
 // point s_j to the nearest triangle that could occlude a segment ending at
 // s_j.  Excluded triangles never occlude.  A triangle lying exactly in the
@@ -512,6 +572,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
 
     // persistent buffers
     size_t bytes = align256(sizeof(float4) * 3 * (size_t)n) + align256(sizeof(Node) * (size_t)ni) +
+                   align256(sizeof(Node4) * (size_t)ni) +
                    align256(sizeof(uint64_t) * (size_t)n) + align256(sizeof(int32_t) * (size_t)n) +
                    2 * align256(sizeof(float4) * (size_t)np) + align256(sizeof(int2) * (size_t)np) +
                    align256(sizeof(float)) + align256(sizeof(int)) + 256;
@@ -523,6 +584,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     Carver pc(sc->block);
     sc->tri = pc.take<float4>(3 * (size_t)n);
     sc->nodes = pc.take<Node>(ni);
+    sc->nodes4 = pc.take<Node4>(ni);
     sc->keys = pc.take<uint64_t>(n);
     sc->order = pc.take<int32_t>(n);
     sc->patch_s = pc.take<float4>(np);
@@ -541,7 +603,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     align256(sizeof(int) * (size_t)n) +                      // parent_leaf
                     2 * align256(sizeof(float4) * (size_t)n) +               // leaf lo/hi
                     2 * align256(sizeof(float4) * (size_t)ni) +              // node lo/hi
-                    2 * align256(sizeof(int) * (size_t)ni) +                 // height, flags
+                    3 * align256(sizeof(int) * (size_t)ni) +                 // height, flags, depth
                     align256(sizeof(unsigned int) * 12) + align256(sizeof(int) * 2) + 256;
     void* tblock = nullptr;
     if (cudaMallocAsync(&tblock, tbytes, stream) != cudaSuccess) {
@@ -568,6 +630,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     float4* node_hi = tc.take<float4>(ni);
     int* height = tc.take<int>(ni);
     int* flags = tc.take<int>(ni);
+    int* ndepth = tc.take<int>(ni);
     unsigned int* bounds = tc.take<unsigned int>(12);   // reference points lo/hi, triangle boxes lo/hi
     int* errdepth = tc.take<int>(2);   // [0] = error bits, [1] = depth
 
@@ -607,6 +670,8 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                                                        node_lo, node_hi, height, flags, errdepth + 1);
             k_pack_nodes<<<(ni + B - 1) / B, B, 0, stream>>>(n, children, parent_int, leaf_lo, leaf_hi, node_lo,
                                                              node_hi, sc->nodes);
+            k_node_depth<<<(ni + B - 1) / B, B, 0, stream>>>(n, parent_int, ndepth);
+            k_collapse4<<<(ni + B - 1) / B, B, 0, stream>>>(n, sc->nodes, ndepth, sc->nodes4);
         }
         e = cudaGetLastError();
     }
@@ -652,6 +717,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
         return UVC_E_INVAL;
     }
     sc->depth = host_ed[1];
+    sc->depth4 = (sc->depth + 1) / 2;
     sc->root = n == 1 ? ~0 : 0;
     *out = sc;
     return UVC_OK;

@@ -38,7 +38,7 @@ namespace {
 #define UVC_IRR_MIN_BLOCKS 3
 #endif
 #ifndef UVC_STREAMED_MIN_BLOCKS
-#define UVC_STREAMED_MIN_BLOCKS 4
+#define UVC_STREAMED_MIN_BLOCKS 3
 #endif
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -49,7 +49,7 @@ constexpr float kFarScale = 1.0f + 9.5367431640625e-07f;
 
 struct SceneView {
     const float4* __restrict__ tri;
-    const Node* __restrict__ nodes;
+    const Node4* __restrict__ nodes4;
     const float4* __restrict__ ps;
     const float4* __restrict__ pn;
     const int2* __restrict__ pe;
@@ -61,14 +61,14 @@ struct SceneView {
 SceneView view_of(const uvc_scene* sc) {
     SceneView v;
     v.tri = sc->tri;
-    v.nodes = sc->nodes;
+    v.nodes4 = sc->nodes4;
     v.ps = sc->patch_s;
     v.pn = sc->patch_n;
     v.pe = sc->patch_excl;
     v.nt = (int)sc->nt;
     v.np = (int)sc->np;
     v.root = sc->root;
-    v.stack_cap = sc->depth + 1;
+    v.stack_cap = 3 * (sc->depth4 + 1) + 1;   // at most 3 pushes per four-wide level
     v.visit_cap = (int)sc->nt + 64;
     v.cut_eps = 1e-5f * sc->diameter;
     v.status = sc->status;
@@ -157,19 +157,125 @@ __device__ __forceinline__ uint32_t test_leaf(const SceneView& S, int k, const R
 
 // Traversal counters of the instrumented variant (one launch, outside timing):
 // [0] warp node visits, [1] warp leaf tests, [2] warp traversals,
-// [3] lane box tests (alive lanes x 2 per node), [4] lane triangle tests,
+// [3] lane box tests (alive lanes x 4 per node), [4] lane triangle tests,
 // [5] facing segments.
 constexpr int kNumCounters = 6;
 
-// Packet traversal: returns the lanes (of `alive`) whose segment is occluded;
-// lanes whose search hit the visit cap are returned in `failed`.
-//
-// Node test: both children's slab intervals at once with packed FP32x2
-// (t = (b - o) * (1/d), one rounding per operation), then per child
-// t_near = max(0, per-axis minima), t_far = min(tend, per-axis maxima), and the
-// child is entered when t_near <= t_far * (1 + 2^-20) (conservative).
-// tend < 1 skips the part of the segment next to the patch point that lies
-// within the patch's clearance: no triangle there can occlude it (k_clearance).
+// Both boxes of a child pair (packed FP32x2).  Each lane loads, per axis, the
+// pair of planes its segment meets first (near) and last (far): the near
+// planes are the lower bounds when the direction component is positive, the
+// upper bounds when it is negative (the sign of 1/d is that of d, zero
+// components included), so no per-axis minimum or maximum is needed:
+// t = (b - o) * (1/d), t_near = max(0, near values), t_far = min(tend, far
+// values), and a child is entered when t_near <= t_far * (1 + 2^-20)
+// (conservative).  tend < 1 skips the part of the segment next to the patch
+// point that lies within the patch's clearance: no triangle there can
+// occlude it (k_clearance).
+__device__ __forceinline__ void pair_hits(const Ray& r, float2 nox, float2 noy, float2 noz, float2 ix, float2 iy,
+                                          float2 iz, float2 nx, float2 fx, float2 ny, float2 fy, float2 nz,
+                                          float2 fz, bool& h0, bool& h1) {
+    const float2 tnx = __fmul2_rn(__fadd2_rn(nx, nox), ix), tfx = __fmul2_rn(__fadd2_rn(fx, nox), ix);
+    const float2 tny = __fmul2_rn(__fadd2_rn(ny, noy), iy), tfy = __fmul2_rn(__fadd2_rn(fy, noy), iy);
+    const float2 tnz = __fmul2_rn(__fadd2_rn(nz, noz), iz), tfz = __fmul2_rn(__fadd2_rn(fz, noz), iz);
+    const float tn0 = max3f(tnx.x, tny.x, fmaxf(tnz.x, 0.f));
+    const float tf0 = min3f(tfx.x, tfy.x, fminf(tfz.x, r.tend));
+    const float tn1 = max3f(tnx.y, tny.y, fmaxf(tnz.y, 0.f));
+    const float tf1 = min3f(tfx.y, tfy.y, fminf(tfz.y, r.tend));
+    h0 = tn0 <= tf0 * kFarScale;
+    h1 = tn1 <= tf1 * kFarScale;
+}
+
+__device__ __forceinline__ float2 ldg2(const char* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+
+__device__ __forceinline__ int pick4(int4 v, int c) { return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w)); }
+
+// Packet traversal of the four-wide tree from `node` with the lanes `alive`:
+// returns the lanes found occluded; `failed` gets lanes whose search hit the
+// visit cap; `hit_tri` receives the occluding leaf of each occluded lane.
+// Children are entered in slot order (with the occluder cache in front, the
+// order of children hardly changes the work).
+template <bool COUNT>
+__device__ __forceinline__ uint32_t traverse4(const SceneView& S, const Ray& r, uint32_t alive, int* stack, int lane,
+                                           uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
+    const float2 nox = make_float2(-r.ox, -r.ox), noy = make_float2(-r.oy, -r.oy), noz = make_float2(-r.oz, -r.oz);
+    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
+    // byte offset of the near pair inside an axis record (lo pair at 0, hi pair at 8)
+    const int onx = (int)(__float_as_uint(r.dx) >> 31) * 8, ony = (int)(__float_as_uint(r.dy) >> 31) * 8,
+              onz = (int)(__float_as_uint(r.dz) >> 31) * 8;
+    uint32_t occl = 0;
+    int top = 0, node = 0, visits = 0;
+    unsigned long long c_leaf = 0, c_box = 0, c_tri = 0;
+    while (true) {
+        if (++visits > S.visit_cap) {
+            failed = alive;
+            if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
+            break;
+        }
+        const Node4* nd = S.nodes4 + node;
+        const char* b = reinterpret_cast<const char*>(nd);
+        const char *bnx = b + onx, *bfx = b + (8 - onx), *bny = b + 16 + ony, *bfy = b + 16 + (8 - ony);
+        const char *bnz = b + 32 + onz, *bfz = b + 32 + (8 - onz);
+        const int4 rr = __ldg(&nd->r);
+        const int4 mm = __ldg(&nd->m);
+        bool h0, h1, h2, h3;
+        pair_hits(r, nox, noy, noz, ix, iy, iz, ldg2(bnx), ldg2(bfx), ldg2(bny), ldg2(bfy), ldg2(bnz), ldg2(bfz), h0, h1);
+        pair_hits(r, nox, noy, noz, ix, iy, iz, ldg2(bnx + 48), ldg2(bfx + 48), ldg2(bny + 48), ldg2(bfy + 48),
+                  ldg2(bnz + 48), ldg2(bfz + 48), h2, h3);
+        if (COUNT) c_box += 4 * __popc(alive);
+        // which children any searching lane enters (one warp OR-reduction)
+        const unsigned nib = ((alive >> lane) & 1u) ? (unsigned)h0 | ((unsigned)h1 << 1) | ((unsigned)h2 << 2) |
+                                                          ((unsigned)h3 << 3)
+                                                    : 0u;
+        const unsigned hit = __reduce_or_sync(kFull, nib);
+        unsigned leaves = hit & (unsigned)mm.x;
+        while (leaves) {                   // leaf children: test their triangle
+            const int c = __ffs(leaves) - 1;
+            leaves &= leaves - 1;
+            const uint32_t m = __ballot_sync(kFull, (nib >> c) & 1u) & alive;
+            if (!m) continue;
+            const int leaf = ~pick4(rr, c);
+            if (COUNT) { ++c_leaf; c_tri += __popc(m); }
+            const uint32_t h = test_leaf(S, leaf, r, m, lane);
+            if ((h >> lane) & 1u) hit_tri = leaf;
+            occl |= h;
+            alive &= ~h;
+        }
+        if (!alive) break;
+        unsigned inner = hit & (unsigned)mm.y;
+        if ((leaves = hit & (unsigned)mm.x) != 0 && inner) {
+            // lanes that just became occluded may have been the only ones wanting a child
+            const unsigned nib2 = ((alive >> lane) & 1u) ? nib : 0u;
+            inner &= __reduce_or_sync(kFull, nib2);
+        }
+        if (inner) {
+            const int first = __ffs(inner) - 1;
+            if (top + 3 > S.stack_cap) {
+                failed = alive;
+                if (lane == 0) atomicCAS(S.status, 0, UVC_E_STACK);
+                break;
+            }
+            // push the others, highest slot first (branch-free)
+            const unsigned rest = inner & (inner - 1);
+            stack[top] = rr.w; top += (rest >> 3) & 1u;
+            stack[top] = rr.z; top += (rest >> 2) & 1u;
+            stack[top] = rr.y; top += (rest >> 1) & 1u;
+            node = pick4(rr, first);
+        } else {
+            if (top == 0) break;
+            node = stack[--top];
+        }
+    }
+    if (COUNT && lane == 0) {
+        atomicAdd(&ctr[0], (unsigned long long)visits);
+        atomicAdd(&ctr[1], c_leaf);
+        atomicAdd(&ctr[2], 1ull);
+        atomicAdd(&ctr[3], c_box);
+        atomicAdd(&ctr[4], c_tri);
+    }
+    return occl;
+}
+
+// Packet occlusion query for the lanes `alive`.
 template <bool COUNT>
 __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t alive, int* stack, int lane,
                                   uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
@@ -186,86 +292,7 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
         if ((h >> lane) & 1u) hit_tri = ~S.root;
         return h;
     }
-    const float2 nox = make_float2(-r.ox, -r.ox), noy = make_float2(-r.oy, -r.oy), noz = make_float2(-r.oz, -r.oz);
-    const float2 ix = make_float2(r.ix, r.ix), iy = make_float2(r.iy, r.iy), iz = make_float2(r.iz, r.iz);
-    uint32_t occl = 0;
-    int top = 0, node = 0, visits = 0;
-    unsigned long long c_leaf = 0, c_box = 0, c_tri = 0;
-    while (true) {
-        if (++visits > S.visit_cap) {
-            failed = alive;
-            if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
-            break;
-        }
-        const Node* nd = S.nodes + node;
-        const float4 bx = __ldg(&nd->x), by = __ldg(&nd->y), bz = __ldg(&nd->z);
-        const int4 rr = __ldg(&nd->r);
-        const float2 t0x = __fmul2_rn(__fadd2_rn(make_float2(bx.x, bx.y), nox), ix);
-        const float2 t1x = __fmul2_rn(__fadd2_rn(make_float2(bx.z, bx.w), nox), ix);
-        const float2 t0y = __fmul2_rn(__fadd2_rn(make_float2(by.x, by.y), noy), iy);
-        const float2 t1y = __fmul2_rn(__fadd2_rn(make_float2(by.z, by.w), noy), iy);
-        const float2 t0z = __fmul2_rn(__fadd2_rn(make_float2(bz.x, bz.y), noz), iz);
-        const float2 t1z = __fmul2_rn(__fadd2_rn(make_float2(bz.z, bz.w), noz), iz);
-        const float tnL = max3f(fminf(t0x.x, t1x.x), fminf(t0y.x, t1y.x), fmaxf(fminf(t0z.x, t1z.x), 0.f));
-        const float tfL = min3f(fmaxf(t0x.x, t1x.x), fmaxf(t0y.x, t1y.x), fminf(fmaxf(t0z.x, t1z.x), r.tend));
-        const float tnR = max3f(fminf(t0x.y, t1x.y), fminf(t0y.y, t1y.y), fmaxf(fminf(t0z.y, t1z.y), 0.f));
-        const float tfR = min3f(fmaxf(t0x.y, t1x.y), fmaxf(t0y.y, t1y.y), fminf(fmaxf(t0z.y, t1z.y), r.tend));
-        const bool me = (alive >> lane) & 1u;
-        if (COUNT) c_box += 2 * __popc(alive);
-        uint32_t ml = __ballot_sync(kFull, me && tnL <= tfL * kFarScale);
-        uint32_t mr = __ballot_sync(kFull, me && tnR <= tfR * kFarScale);
-        // leaf children: test their triangle now (one copy of the test code)
-        const bool leafL = rr.x < 0, leafR = rr.y < 0;
-        uint32_t pend = (leafL && ml ? 1u : 0u) | (leafR && mr ? 2u : 0u);
-        while (pend) {
-            const int c = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const uint32_t m = (c ? mr : ml) & alive;
-            if (COUNT) { ++c_leaf; c_tri += __popc(m); }
-            const int leaf = ~(c ? rr.y : rr.x);
-            const uint32_t h = test_leaf(S, leaf, r, m, lane);
-            if ((h >> lane) & 1u) hit_tri = leaf;
-            occl |= h;
-            alive &= ~h;
-        }
-        if (leafL) ml = 0;
-        if (leafR) mr = 0;
-        ml &= alive;
-        mr &= alive;
-        if (!alive) break;
-        if (ml && mr) {
-            // near child first, judged on one lane that enters both
-            const int src = __ffs(ml & mr) - 1;
-            const float a = __shfl_sync(kFull, tnL, src), b = __shfl_sync(kFull, tnR, src);
-            const int first = a <= b ? rr.x : rr.y;
-            const int second = a <= b ? rr.y : rr.x;
-            if (top >= S.stack_cap) {
-                failed = alive;
-                if (lane == 0) atomicCAS(S.status, 0, UVC_E_STACK);
-                break;
-            }
-            if (lane == 0) stack[top] = second;
-            ++top;
-            node = first;
-        } else if (ml) {
-            node = rr.x;
-        } else if (mr) {
-            node = rr.y;
-        } else {
-            if (top == 0) break;
-            --top;
-            __syncwarp();
-            node = stack[top];
-        }
-    }
-    if (COUNT && lane == 0) {
-        atomicAdd(&ctr[0], (unsigned long long)visits);
-        atomicAdd(&ctr[1], c_leaf);
-        atomicAdd(&ctr[2], 1ull);
-        atomicAdd(&ctr[3], c_box);
-        atomicAdd(&ctr[4], c_tri);
-    }
-    return occl;
+    return traverse4<COUNT>(S, r, alive, stack, lane, failed, ctr, hit_tri);
 }
 
 // The patch of one lane: sample point, normal, excluded triangles.

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/uvc.h"
+#include "uvc.h"
 
 namespace uvc {
 
@@ -19,6 +19,22 @@ namespace uvc {
 struct __align__(16) Node {
     float4 x, y, z;
     int4 r;
+};
+
+// Four-wide node used by the traversal: the binary tree collapsed two levels
+// at a time (a node at even depth keeps its grandchildren; a leaf child stays a
+// leaf).  Children are tested in pairs (0,1) and (2,3) with packed FP32x2:
+//   q[0..2] = x, y, z of (c0.lo, c1.lo, c0.hi, c1.hi)
+//   q[3..5] = x, y, z of (c2.lo, c3.lo, c2.hi, c3.hi)
+//   r = child refs: >= 0 four-wide node (indexed like the binary node it came
+//       from), < 0 leaf ~k, kEmptyChild for an unused slot (its box is a point
+//       far outside the scene, so no segment enters it)
+//   m = (bit c set: child c is a leaf, bit c set: child c is a four-wide node, 0, 0)
+constexpr int kEmptyChild = 0x7fffffff;
+struct __align__(16) Node4 {
+    float4 q[6];
+    int4 r;
+    int4 m;
 };
 
 // Lamp as seen by the kernels: source offsets and source powers w_m * P.
@@ -40,6 +56,8 @@ struct uvc_scene {
     void* block = nullptr;
     float4* tri = nullptr;        // [nt][3]: (v0, id bits), (v1, 0), (v2, 0) in sorted order
     uvc::Node* nodes = nullptr;   // [nt-1]
+    uvc::Node4* nodes4 = nullptr; // [nt-1], used at even-depth binary indices only
+    int32_t depth4 = 0;           // depth of the four-wide tree
     uint64_t* keys = nullptr;     // [nt] sorted Morton keys
     int32_t* order = nullptr;     // [nt] triangle index per sorted position
     float4* patch_s = nullptr;    // [np] (centroid, area)
