@@ -185,7 +185,9 @@ def run_ours(args):
 
     def step(irr_events=None):
         sc = uvc.build_scene(d["verts"], d["tris"], d["centroid"], d["normal"], d["area"], d["excl"])
-        n = 2 + (28 if s.nt > 0 else 0) + (3 if s.nt > 1 else 0)
+        # build: pack_patches, area_total; prepare, morton, 3 x 8 sort passes, gather;
+        # karras, refit, pack_nodes, node_depth, collapse4; clearance
+        n = 2 + (27 if s.nt > 0 else 0) + (5 if s.nt > 1 else 0) + (1 if s.np_ > 0 else 0)
         if irr_events:
             irr_events[0].record(stream)
         if streamed:
