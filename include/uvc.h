@@ -88,7 +88,8 @@ typedef struct uvc_scene uvc_scene; /* opaque; owns its device buffers */
 /*
  * uvc_build_scene - upload the environment and build its bounding-volume
  * hierarchy (a linear BVH: Morton codes, radix sort, binary radix tree,
- * bottom-up box refit).  The paper's environment boundary E is the triangle
+ * bottom-up box refit; then a surface-area restructuring pass, see
+ * uvc_build_scene_ex).  The paper's environment boundary E is the triangle
  * mesh of Sec. III-B; the hierarchy replaces the paper's rasterised visibility
  * cube (Sec. IV-C, Fig. 2) as the means of answering "does another surface
  * lie closer to the source along the ray" (the visibility rule of Eq. (7)).
@@ -105,6 +106,22 @@ typedef struct uvc_scene uvc_scene; /* opaque; owns its device buffers */
  */
 int uvc_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     const uvc_patches* patches, int64_t np, uvc_stream_t stream, uvc_scene** out);
+
+/*
+ * uvc_build_scene_ex - uvc_build_scene with build options (bit flags):
+ *   UVC_BUILD_LBVH_ONLY  keep the plain linear BVH (Morton order + radix tree +
+ *                        refit).  Without it, the hierarchy is additionally
+ *                        restructured for lower surface-area cost (treelets of
+ *                        up to 7 leaves re-wired optimally, bottom-up, three
+ *                        passes): the same triangles under the same root, a
+ *                        different topology, the same query results, fewer
+ *                        nodes visited per query.
+ * uvc_build_scene(...) equals uvc_build_scene_ex(..., 0, ...).  Unknown flags:
+ * UVC_E_INVAL.
+ */
+#define UVC_BUILD_LBVH_ONLY 1u
+int uvc_build_scene_ex(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
+                       int64_t np, uint32_t flags, uvc_stream_t stream, uvc_scene** out);
 
 /* uvc_free_scene - release a scene's device buffers (synchronises the device
  * work that may still use them).  NULL is accepted. */

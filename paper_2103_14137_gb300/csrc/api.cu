@@ -51,7 +51,16 @@ extern "C" {
 
 int uvc_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
                     int64_t np, uvc_stream_t stream, uvc_scene** out) {
-    return uvc::build_scene(verts, nv, tris, nt, patches, np, (cudaStream_t)stream, out);
+    return uvc::build_scene(verts, nv, tris, nt, patches, np, 0u, (cudaStream_t)stream, out);
+}
+
+int uvc_build_scene_ex(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
+                       int64_t np, uint32_t flags, uvc_stream_t stream, uvc_scene** out) {
+    if (flags & ~(uint32_t)UVC_BUILD_LBVH_ONLY) {
+        if (out) *out = nullptr;
+        return UVC_E_INVAL;
+    }
+    return uvc::build_scene(verts, nv, tris, nt, patches, np, flags, (cudaStream_t)stream, out);
 }
 
 int uvc_free_scene(uvc_scene* scene) {

@@ -366,8 +366,10 @@ __global__ void k_pack_nodes(int n, const int2* __restrict__ children, const int
     nodes[i] = nd;
 }
 
-// Depth of every internal node (edges from the root), by walking up.
-__global__ void k_node_depth(int n, const int* __restrict__ parent_int, int* __restrict__ depth) {
+// Depth of every internal node (edges from the root), by walking up; the
+// tree depth (deepest leaf) goes to *tree_depth.
+__global__ void k_node_depth(int n, const int* __restrict__ parent_int, const int2* __restrict__ children,
+                             int* __restrict__ depth, int* tree_depth) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     int d = 0;
@@ -377,6 +379,172 @@ __global__ void k_node_depth(int n, const int* __restrict__ parent_int, int* __r
         p = parent_int[p];
     }
     depth[i] = d;
+    const int2 c = children[i];
+    if (c.x < 0 || c.y < 0) atomicMax(tree_depth, d + 1);
+}
+
+// ---------------------------------------------------------------------------
+// Treelet restructuring (optional quality pass over the LBVH)
+// ---------------------------------------------------------------------------
+// The matrix asks 1e9+ segment queries of one hierarchy, so the hierarchy's
+// quality matters far more than its build time.  After the refit, every
+// internal node is visited bottom-up (second child to finish, as in the refit)
+// and the treelet below it - the node's children, repeatedly replacing the
+// internal treelet leaf of largest surface area by its two children, up to 7
+// treelet leaves - is given the topology of least surface-area cost, found by
+// dynamic programming over all subsets of the treelet leaves (Karras & Aila,
+// "Fast Parallel Construction of High-Quality Bounding Volume Hierarchies",
+// HPG 2013).  Cost of a subtree: C_i * area + children's costs; of a leaf:
+// C_t * area.  The set of triangles under every treelet root is unchanged, so
+// its box is too; only nodes inside the treelet are rewired.
+constexpr int kTreelet = 7;
+constexpr int kRestructurePasses = 3;
+constexpr float kCostNode = 1.2f, kCostTri = 1.0f;
+
+__device__ __forceinline__ float half_area(float4 lo, float4 hi) {
+    const float dx = fmaxf(hi.x - lo.x, 0.f), dy = fmaxf(hi.y - lo.y, 0.f), dz = fmaxf(hi.z - lo.z, 0.f);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+struct TreeView {
+    int2* children;
+    int* parent_int;
+    int* parent_leaf;
+    const float4* leaf_lo;
+    const float4* leaf_hi;
+    float4* node_lo;
+    float4* node_hi;
+    float* cost;
+};
+
+__device__ __forceinline__ void ref_box(const TreeView& T, int ref, float4& lo, float4& hi) {
+    if (ref < 0) { lo = T.leaf_lo[~ref]; hi = T.leaf_hi[~ref]; }
+    else { lo = __ldcg(&T.node_lo[ref]); hi = __ldcg(&T.node_hi[ref]); }
+}
+
+__device__ __forceinline__ float ref_cost(const TreeView& T, int ref) {
+    if (ref < 0) return kCostTri * half_area(T.leaf_lo[~ref], T.leaf_hi[~ref]);
+    return __ldcg(&T.cost[ref]);
+}
+
+__device__ void restructure_treelet(const TreeView& T, int root) {
+    int tl[kTreelet];          // treelet leaves (refs)
+    int ti[kTreelet - 1];      // treelet internal nodes (reused)
+    const int2 rc = __ldcg(&T.children[root]);
+    tl[0] = rc.x;
+    tl[1] = rc.y;
+    int nl = 2, nin = 1;
+    ti[0] = root;
+    while (nl < kTreelet) {
+        int best = -1;
+        float best_a = -1.f;
+        for (int q = 0; q < nl; ++q) {
+            if (tl[q] < 0) continue;
+            float4 lo, hi;
+            ref_box(T, tl[q], lo, hi);
+            const float a = half_area(lo, hi);
+            if (a > best_a) { best_a = a; best = q; }
+        }
+        if (best < 0) break;
+        const int q = tl[best];
+        const int2 c = __ldcg(&T.children[q]);
+        ti[nin++] = q;
+        tl[best] = c.x;
+        tl[nl++] = c.y;
+    }
+    const float4 rlo = __ldcg(&T.node_lo[root]), rhi = __ldcg(&T.node_hi[root]);
+    // current cost of the root's subtree (children are final)
+    const float cur = kCostNode * half_area(rlo, rhi) + ref_cost(T, rc.x) + ref_cost(T, rc.y);
+    if (nl <= 2) {
+        __stcg(&T.cost[root], cur);
+        return;
+    }
+    const int nsub = 1 << nl;
+    float4 llo[kTreelet], lhi[kTreelet];
+    float copt[1 << kTreelet];
+    unsigned char part[1 << kTreelet];
+    for (int q = 0; q < nl; ++q) {
+        ref_box(T, tl[q], llo[q], lhi[q]);
+        copt[1 << q] = ref_cost(T, tl[q]);
+    }
+    auto set_box = [&](int S, float4& lo, float4& hi) {
+        lo = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+        hi = make_float4(-3.0e38f, -3.0e38f, -3.0e38f, 0.f);
+        for (int q = 0; q < nl; ++q)
+            if (S & (1 << q)) {
+                lo = make_float4(fminf(lo.x, llo[q].x), fminf(lo.y, llo[q].y), fminf(lo.z, llo[q].z), 0.f);
+                hi = make_float4(fmaxf(hi.x, lhi[q].x), fmaxf(hi.y, lhi[q].y), fmaxf(hi.z, lhi[q].z), 0.f);
+            }
+    };
+    for (int S = 1; S < nsub; ++S) {
+        const int low = S & -S;
+        if (S == low) continue;
+        float best = 3.0e38f;
+        int bp = low;
+        // partitions (P, S\P) with P holding S's lowest leaf
+        for (int P = (S - 1) & S; P != 0; P = (P - 1) & S) {
+            if (!(P & low)) continue;
+            const float c = copt[P] + copt[S ^ P];
+            if (c < best) { best = c; bp = P; }
+        }
+        float4 lo, hi;
+        set_box(S, lo, hi);
+        copt[S] = kCostNode * half_area(lo, hi) + best;
+        part[S] = (unsigned char)bp;
+    }
+    const int full = nsub - 1;
+    if (!(copt[full] < cur * 0.999f)) {
+        __stcg(&T.cost[root], cur);
+        return;
+    }
+    // rewire: the root keeps its index and parent; other internal nodes are reused
+    int st_set[kTreelet], st_node[kTreelet];
+    int top = 0, next = 1;
+    st_set[top] = full;
+    st_node[top] = root;
+    ++top;
+    while (top > 0) {
+        --top;
+        const int S = st_set[top], node = st_node[top];
+        const int P = part[S], Q = S ^ P;
+        int ref[2];
+        const int sets[2] = {P, Q};
+        for (int h = 0; h < 2; ++h) {
+            const int X = sets[h];
+            if ((X & (X - 1)) == 0) {
+                ref[h] = tl[__ffs(X) - 1];
+            } else {
+                const int m = ti[next++];
+                ref[h] = m;
+                st_set[top] = X;
+                st_node[top] = m;
+                ++top;
+            }
+            if (ref[h] < 0) T.parent_leaf[~ref[h]] = node;
+            else T.parent_int[ref[h]] = node;
+        }
+        float4 lo, hi;
+        set_box(S, lo, hi);
+        __stcg(&T.children[node], make_int2(ref[0], ref[1]));
+        __stcg(&T.node_lo[node], lo);
+        __stcg(&T.node_hi[node], hi);
+        __stcg(&T.cost[node], copt[S]);
+    }
+}
+
+__global__ void k_restructure(int n, TreeView T, const int* __restrict__ leaf_parent0, int* flags) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int p = leaf_parent0[k];
+    while (p >= 0) {
+        __threadfence();
+        if (atomicAdd(&flags[p], 1) == 0) return;   // the sibling subtree finishes p
+        __threadfence();
+        restructure_treelet(T, p);
+        __threadfence();
+        if (p == 0) return;
+        p = T.parent_int[p];
+    }
 }
 
 // Collapse to the four-wide tree: every internal node at even depth gets a
@@ -553,7 +721,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
-                int64_t np, cudaStream_t stream, uvc_scene** out) {
+                int64_t np, uint32_t flags_in, cudaStream_t stream, uvc_scene** out) {
     if (!out) return UVC_E_INVAL;
     *out = nullptr;
     const int64_t lim = int64_t(1) << 31;
@@ -604,6 +772,8 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     2 * align256(sizeof(float4) * (size_t)n) +               // leaf lo/hi
                     2 * align256(sizeof(float4) * (size_t)ni) +              // node lo/hi
                     3 * align256(sizeof(int) * (size_t)ni) +                 // height, flags, depth
+                    align256(sizeof(float) * (size_t)ni) +                   // subtree cost
+                    align256(sizeof(int) * (size_t)n) +                      // leaf parents at pass start
                     align256(sizeof(unsigned int) * 12) + align256(sizeof(int) * 2) + 256;
     void* tblock = nullptr;
     if (cudaMallocAsync(&tblock, tbytes, stream) != cudaSuccess) {
@@ -631,6 +801,8 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     int* height = tc.take<int>(ni);
     int* flags = tc.take<int>(ni);
     int* ndepth = tc.take<int>(ni);
+    float* cost = tc.take<float>(ni);
+    int* leaf_parent0 = tc.take<int>(n);
     unsigned int* bounds = tc.take<unsigned int>(12);   // reference points lo/hi, triangle boxes lo/hi
     int* errdepth = tc.take<int>(2);   // [0] = error bits, [1] = depth
 
@@ -668,9 +840,19 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
             k_karras<<<(ni + B - 1) / B, B, 0, stream>>>(sc->keys, n, children, parent_int, parent_leaf);
             k_refit<<<(n + B - 1) / B, B, 0, stream>>>(n, children, parent_int, parent_leaf, leaf_lo, leaf_hi,
                                                        node_lo, node_hi, height, flags, errdepth + 1);
+            if (!(flags_in & UVC_BUILD_LBVH_ONLY) && n > 2) {
+                TreeView T{children, parent_int, parent_leaf, leaf_lo, leaf_hi, node_lo, node_hi, cost};
+                for (int pass = 0; pass < kRestructurePasses; ++pass) {
+                    cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)ni, stream);
+                    cudaMemcpyAsync(leaf_parent0, parent_leaf, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice,
+                                    stream);
+                    k_restructure<<<(n + 127) / 128, 128, 0, stream>>>(n, T, leaf_parent0, flags);
+                }
+            }
+            cudaMemsetAsync(errdepth + 1, 0, sizeof(int), stream);
             k_pack_nodes<<<(ni + B - 1) / B, B, 0, stream>>>(n, children, parent_int, leaf_lo, leaf_hi, node_lo,
                                                              node_hi, sc->nodes);
-            k_node_depth<<<(ni + B - 1) / B, B, 0, stream>>>(n, parent_int, ndepth);
+            k_node_depth<<<(ni + B - 1) / B, B, 0, stream>>>(n, parent_int, children, ndepth, errdepth + 1);
             k_collapse4<<<(ni + B - 1) / B, B, 0, stream>>>(n, sc->nodes, ndepth, sc->nodes4);
         }
         e = cudaGetLastError();

@@ -78,7 +78,7 @@ int status_from_cuda(cudaError_t e);
 
 // BVH build (build_bvh.cu)
 int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const uvc_patches* patches,
-                int64_t np, cudaStream_t stream, uvc_scene** out);
+                int64_t np, uint32_t flags, cudaStream_t stream, uvc_scene** out);
 
 // irradiance (irradiance.cu)
 int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,

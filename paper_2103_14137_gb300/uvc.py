@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libuvc.so")
 MAX_SOURCES = 32
 
 UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT, UVC_E_SCRATCH = range(7)
+UVC_BUILD_LBVH_ONLY = 1
 
 
 class UvcError(RuntimeError):
@@ -50,6 +51,7 @@ def library():
     P, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
     sig = {
         "uvc_build_scene": [P, i64, P, i64, ctypes.POINTER(_Patches), i64, P, ctypes.POINTER(P)],
+        "uvc_build_scene_ex": [P, i64, P, i64, ctypes.POINTER(_Patches), i64, ctypes.c_uint32, P, ctypes.POINTER(P)],
         "uvc_free_scene": [P],
         "uvc_irradiance_matrix": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence": [P, P, i64, i64, P, i32, P, P],
@@ -164,15 +166,20 @@ class Scene:
             pass
 
 
-def build_scene(verts, tris, centroid, normal, area, excl, stream=None) -> Scene:
+def build_scene(verts, tris, centroid, normal, area, excl, stream=None, lbvh_only=False) -> Scene:
+    """uvc_build_scene (lbvh_only=False) or uvc_build_scene_ex(UVC_BUILD_LBVH_ONLY)."""
     nv, nt, np_ = verts.shape[0], tris.shape[0], centroid.shape[0]
     p = _Patches(_dev(centroid, torch.float32, "centroid", (np_, 3)), _dev(normal, torch.float32, "normal", (np_, 3)),
                  _dev(area, torch.float32, "area", (np_,)), _dev(excl, torch.int32, "excl", (np_, 2)))
     out = ctypes.c_void_p()
-    rc = library().uvc_build_scene(_dev(verts, torch.float32, "verts", (nv, 3)), nv,
-                                   _dev(tris, torch.int32, "tris", (nt, 3)), nt, ctypes.byref(p), np_,
-                                   _stream(stream), ctypes.byref(out))
-    _check(rc, "uvc_build_scene")
+    args = (_dev(verts, torch.float32, "verts", (nv, 3)), nv, _dev(tris, torch.int32, "tris", (nt, 3)), nt,
+            ctypes.byref(p), np_)
+    if lbvh_only:
+        rc = library().uvc_build_scene_ex(*args, UVC_BUILD_LBVH_ONLY, _stream(stream), ctypes.byref(out))
+        _check(rc, "uvc_build_scene_ex")
+    else:
+        rc = library().uvc_build_scene(*args, _stream(stream), ctypes.byref(out))
+        _check(rc, "uvc_build_scene")
     return Scene(out)
 
 

@@ -11,15 +11,16 @@ def T(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def build(scene_or_arrays):
+def build(scene_or_arrays, lbvh_only=False):
     s = scene_or_arrays
-    return uvc.build_scene(T(s.verts), T(s.tris), T(s.centroid), T(s.normal), T(s.area), T(s.excl))
+    return uvc.build_scene(T(s.verts), T(s.tris), T(s.centroid), T(s.normal), T(s.area), T(s.excl),
+                           lbvh_only=lbvh_only)
 
 
-def build_arrays(verts, tris, cen, nrm, area, excl):
+def build_arrays(verts, tris, cen, nrm, area, excl, lbvh_only=False):
     return uvc.build_scene(T(np.asarray(verts, np.float32)), T(np.asarray(tris, np.int32)),
                            T(np.asarray(cen, np.float32)), T(np.asarray(nrm, np.float32)),
-                           T(np.asarray(area, np.float32)), T(np.asarray(excl, np.int32)))
+                           T(np.asarray(area, np.float32)), T(np.asarray(excl, np.int32)), lbvh_only=lbvh_only)
 
 
 def lamp_of(L):

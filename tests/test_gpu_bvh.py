@@ -1,5 +1,7 @@
 """GPU hierarchy against the oracle's definitions, bit for bit: Morton keys,
-stable order, radix tree children, child boxes."""
+stable order, radix tree children, child boxes (plain LBVH build); and the
+surface-area restructured hierarchy: a valid tree over the same triangles with
+exact boxes and a lower surface-area cost, giving bit-identical matrices."""
 import numpy as np
 import pytest
 
@@ -29,14 +31,14 @@ def _check(verts, tris, sc):
 
 def test_tiny_bvh_bit_exact():
     s = tiny_room()
-    sc = build(s)
+    sc = build(s, lbvh_only=True)
     _check(s.verts, s.tris, sc)
     sc.free()
 
 
 def test_ward_bvh_bit_exact():
     s = ward_room()
-    sc = build(s)
+    sc = build(s, lbvh_only=True)
     _check(s.verts, s.tris, sc)
     assert 10 < sc.depth < 96
     sc.free()
@@ -50,6 +52,78 @@ def test_sizes_across_sort_tiles_and_duplicates(n):
     verts = np.repeat(base, 3, axis=0) + np.tile(np.array([[0, 0, 0], [0.01, 0, 0], [0, 0.01, 0]], np.float32), (n, 1))
     tris = np.arange(3 * n, dtype=np.int32).reshape(-1, 3)
     cen = np.zeros((1, 3), np.float32)
-    sc = build_arrays(verts, tris, cen, [[0, 0, 1]], [1.0], [[-1, -1]])
+    sc = build_arrays(verts, tris, cen, [[0, 0, 1]], [1.0], [[-1, -1]], lbvh_only=True)
     _check(verts, tris, sc)
     sc.free()
+
+
+def _tree_sah(children, boxes, verts, tris, order):
+    """Surface-area cost with the restructuring's constants (C_i = 1.2, C_t = 1)."""
+    def ha(lo, hi):
+        d = np.maximum(hi - lo, 0)
+        return d[..., 0] * d[..., 1] + d[..., 1] * d[..., 2] + d[..., 2] * d[..., 0]
+    lo_l, hi_l, lo_r, hi_r = boxes[:, 0:3], boxes[:, 3:6], boxes[:, 6:9], boxes[:, 9:12]
+    node_area = ha(np.minimum(lo_l, lo_r), np.maximum(hi_l, hi_r))
+    leaf_cost = (ha(lo_l, hi_l) * (children[:, 0] < 0)).sum() + (ha(lo_r, hi_r) * (children[:, 1] < 0)).sum()
+    return 1.2 * node_area.sum() + leaf_cost
+
+
+def _check_tree(verts, tris, g):
+    n = tris.shape[0]
+    ch = g["children"]
+    assert sorted(g["order"].tolist()) == list(range(n))
+    seen_leaf = np.zeros(n, int)
+    seen_node = np.zeros(n - 1, int)
+    for a in ch.ravel():
+        (seen_leaf if a < 0 else seen_node)[~a if a < 0 else a] += 1
+    assert np.all(seen_leaf == 1) and seen_node[0] == 0 and np.all(seen_node[1:] == 1)
+    v = verts[tris[g["order"]]]
+    tlo, thi = v.min(axis=1), v.max(axis=1)
+    b = g["boxes"]
+    # exact boxes: each child box is the min/max over its subtree's triangles
+    memo = {}
+
+    def box(ref):
+        if ref < 0:
+            return tlo[~ref], thi[~ref]
+        if ref not in memo:
+            l0, l1 = box(ch[ref, 0])
+            r0, r1 = box(ch[ref, 1])
+            memo[ref] = (np.minimum(l0, r0), np.maximum(l1, r1))
+        return memo[ref]
+    import sys
+    sys.setrecursionlimit(100000)
+    for k in range(n - 1):
+        l0, l1 = box(ch[k, 0])
+        r0, r1 = box(ch[k, 1])
+        assert np.array_equal(b[k, 0:3], l0) and np.array_equal(b[k, 3:6], l1)
+        assert np.array_equal(b[k, 6:9], r0) and np.array_equal(b[k, 9:12], r1)
+
+
+def test_restructured_tree_valid_and_cheaper():
+    import paper_2103_14137_gb300 as uvc
+    s = ward_room()
+    sc0 = build(s, lbvh_only=True)
+    sc1 = build(s)
+    g0, g1 = uvc.scene_export_bvh(sc0), uvc.scene_export_bvh(sc1)
+    _check_tree(s.verts, s.tris, g1)
+    c0 = _tree_sah(g0["children"], g0["boxes"], s.verts, s.tris, g0["order"])
+    c1 = _tree_sah(g1["children"], g1["boxes"], s.verts, s.tris, g1["order"])
+    assert c1 < 0.95 * c0, (c0, c1)
+    sc0.free()
+    sc1.free()
+
+
+def test_restructured_tree_gives_identical_matrix():
+    import paper_2103_14137_gb300 as uvc
+    from tests.gpu_util import T, lamp_of
+    s = ward_room(n_cand=64)
+    sc0 = build(s, lbvh_only=True)
+    sc1 = build(s)
+    A0, v0 = uvc.irradiance_matrix(sc0, T(s.cand), lamp_of(s.lamp), with_vis=True)
+    A1, v1 = uvc.irradiance_matrix(sc1, T(s.cand), lamp_of(s.lamp), with_vis=True)
+    import torch
+    torch.cuda.synchronize()
+    assert torch.equal(A0, A1) and torch.equal(v0, v1)
+    sc0.free()
+    sc1.free()
