@@ -112,8 +112,8 @@ int uvc_build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t
  *   UVC_BUILD_LBVH_ONLY  keep the plain linear BVH (Morton order + radix tree +
  *                        refit).  Without it, the hierarchy is additionally
  *                        restructured for lower surface-area cost (treelets of
- *                        up to 7 leaves re-wired optimally, bottom-up, three
- *                        passes): the same triangles under the same root, a
+ *                        up to 7 leaves re-wired optimally, bottom-up, one
+ *                        pass): the same triangles under the same root, a
  *                        different topology, the same query results, fewer
  *                        nodes visited per query.
  * uvc_build_scene(...) equals uvc_build_scene_ex(..., 0, ...).  Unknown flags:

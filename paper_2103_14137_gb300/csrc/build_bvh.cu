@@ -396,9 +396,10 @@ __global__ void k_node_depth(int n, const int* __restrict__ parent_int, const in
 // "Fast Parallel Construction of High-Quality Bounding Volume Hierarchies",
 // HPG 2013).  Cost of a subtree: C_i * area + children's costs; of a leaf:
 // C_t * area.  The set of triangles under every treelet root is unchanged, so
-// its box is too; only nodes inside the treelet are rewired.
+// its box is too; only nodes inside the treelet are rewired.  One pass: on the
+// ward, passes 2 and 3 cost 2.1 ms each and save under 1 % of the traversal.
 constexpr int kTreelet = 7;
-constexpr int kRestructurePasses = 3;
+constexpr int kRestructurePasses = 1;
 constexpr float kCostNode = 1.2f, kCostTri = 1.0f;
 
 __device__ __forceinline__ float half_area(float4 lo, float4 hi) {
@@ -703,6 +704,112 @@ __global__ void k_clearance(const Node* __restrict__ nodes, const float4* __rest
     pn[j] = n4;
 }
 
+// Clearance, warp-packet version over the four-wide tree: a warp takes 32
+// consecutive (spatially close) patches and walks the tree once for all of
+// them; each lane keeps its own best distance, a child is entered while any
+// lane could still find something closer in it, nearest children first (as
+// seen from the first lane).  Same definition as k_clearance.
+__global__ void __launch_bounds__(kThreads) k_clearance4(const Node4* __restrict__ nodes4,
+                                                         const float4* __restrict__ tri, int nt,
+                                                         const float4* __restrict__ ps, float4* __restrict__ pn,
+                                                         const int2* __restrict__ pe, int np, float margin,
+                                                         int stack_cap) {
+    extern __shared__ int cl_stack[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int* stack = cl_stack + warp * stack_cap;
+    const int j = (blockIdx.x * kWarpsPerBlock + warp) * 32 + lane;
+    const bool valid = j < np;
+    const float4 s4 = valid ? ps[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 n4 = valid ? pn[j] : make_float4(0.f, 0.f, 1.f, 0.f);
+    const int2 ex = valid ? pe[j] : make_int2(-1, -1);
+    int ax = -1;
+    if (fabsf(n4.x) == 1.f && n4.y == 0.f && n4.z == 0.f) ax = 0;
+    if (fabsf(n4.y) == 1.f && n4.x == 0.f && n4.z == 0.f) ax = 1;
+    if (fabsf(n4.z) == 1.f && n4.x == 0.f && n4.y == 0.f) ax = 2;
+    const float sk = ax == 0 ? s4.x : (ax == 1 ? s4.y : s4.z);
+    const float su = ax == 0 ? s4.y : s4.x, sv = ax == 2 ? s4.y : s4.z;
+    const float margin2 = margin * margin;
+    float best = valid ? 3.0e38f : 0.f;
+    const uint32_t live = __ballot_sync(0xffffffffu, valid);
+    if (!live) return;
+    const int src = __ffs(live) - 1;
+    int top = 0, node = 0, visits = 0;
+    while (true) {
+        if (++visits > 4 * nt + 64) { best = 0.f; break; }   // cannot happen on a valid tree
+        const Node4* nd = nodes4 + node;
+        const float4 q0 = nd->q[0], q1 = nd->q[1], q2 = nd->q[2], q3 = nd->q[3], q4 = nd->q[4], q5 = nd->q[5];
+        const int4 rr = nd->r, mm = nd->m;
+        float d[4];
+        d[0] = box_dist2(s4.x, s4.y, s4.z, q0.x, q1.x, q2.x, q0.z, q1.z, q2.z);
+        d[1] = box_dist2(s4.x, s4.y, s4.z, q0.y, q1.y, q2.y, q0.w, q1.w, q2.w);
+        d[2] = box_dist2(s4.x, s4.y, s4.z, q3.x, q4.x, q5.x, q3.z, q4.z, q5.z);
+        d[3] = box_dist2(s4.x, s4.y, s4.z, q3.y, q4.y, q5.y, q3.w, q4.w, q5.w);
+        if (ax >= 0) {
+            // a box flat in the patch's own plane holds only coplanar triangles:
+            // it matters only if it comes within the margin (in-plane distance)
+            const float lo4[4] = {ax == 0 ? q0.x : (ax == 1 ? q1.x : q2.x), ax == 0 ? q0.y : (ax == 1 ? q1.y : q2.y),
+                                  ax == 0 ? q3.x : (ax == 1 ? q4.x : q5.x), ax == 0 ? q3.y : (ax == 1 ? q4.y : q5.y)};
+            const float hi4[4] = {ax == 0 ? q0.z : (ax == 1 ? q1.z : q2.z), ax == 0 ? q0.w : (ax == 1 ? q1.w : q2.w),
+                                  ax == 0 ? q3.z : (ax == 1 ? q4.z : q5.z), ax == 0 ? q3.w : (ax == 1 ? q4.w : q5.w)};
+            for (int c = 0; c < 4; ++c)
+                if (lo4[c] == sk && hi4[c] == sk && d[c] > margin2) d[c] = 3.0e38f;
+        }
+        const unsigned nib = (unsigned)(d[0] < best) | ((unsigned)(d[1] < best) << 1) |
+                             ((unsigned)(d[2] < best) << 2) | ((unsigned)(d[3] < best) << 3);
+        const unsigned hit = __reduce_or_sync(0xffffffffu, nib);
+        unsigned leaves = hit & (unsigned)mm.x;
+        while (leaves) {
+            const int c = __ffs(leaves) - 1;
+            leaves &= leaves - 1;
+            if (!((nib >> c) & 1u)) continue;
+            const int ref = c == 0 ? rr.x : (c == 1 ? rr.y : (c == 2 ? rr.z : rr.w));
+            const int k = ~ref;
+            const float4 a = tri[3 * k], b = tri[3 * k + 1], cc = tri[3 * k + 2];
+            const int id = __float_as_int(a.w);
+            if (id == ex.x || id == ex.y || d[c] >= best) continue;
+            bool coplanar = false;
+            if (ax >= 0) {
+                const float ak = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+                const float bk = ax == 0 ? b.x : (ax == 1 ? b.y : b.z);
+                const float ck = ax == 0 ? cc.x : (ax == 1 ? cc.y : cc.z);
+                coplanar = ak == sk && bk == sk && ck == sk;
+            }
+            if (coplanar) {
+                const float au = ax == 0 ? a.y : a.x, av = ax == 2 ? a.y : a.z;
+                const float bu = ax == 0 ? b.y : b.x, bv = ax == 2 ? b.y : b.z;
+                const float cu = ax == 0 ? cc.y : cc.x, cv = ax == 2 ? cc.y : cc.z;
+                if (tri2_dist2(su, sv, au, av, bu, bv, cu, cv) <= margin2) best = 0.f;
+            } else {
+                best = d[c];
+            }
+        }
+        // internal children still wanted (after the leaf updates), nearest first
+        const unsigned nib2 = (unsigned)(d[0] < best) | ((unsigned)(d[1] < best) << 1) |
+                              ((unsigned)(d[2] < best) << 2) | ((unsigned)(d[3] < best) << 3);
+        unsigned inner = __reduce_or_sync(0xffffffffu, nib2) & (unsigned)mm.y;
+        if (inner) {
+            float key[4];
+            for (int c = 0; c < 4; ++c) key[c] = __shfl_sync(0xffffffffu, d[c], src);
+            if (top + 4 > stack_cap) { best = 0.f; break; }
+            // push farthest first so that the nearest is popped next
+            while (inner) {
+                int far_c = -1;
+                float far_k = -1.f;
+                for (int c = 0; c < 4; ++c)
+                    if (((inner >> c) & 1u) && key[c] > far_k) { far_k = key[c]; far_c = c; }
+                inner &= ~(1u << far_c);
+                stack[top++] = far_c == 0 ? rr.x : (far_c == 1 ? rr.y : (far_c == 2 ? rr.z : rr.w));
+            }
+        }
+        if (top == 0) break;
+        node = stack[--top];
+    }
+    if (valid) {
+        n4.w = sqrtf(best);
+        pn[j] = n4;
+    }
+}
+
 struct Carver {
     char* base;
     size_t off = 0;
@@ -857,12 +964,27 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
         }
         e = cudaGetLastError();
     }
-    // scene diameter (host) for the clearance margin and the traversal's cut tolerance
+    // one synchronisation: validation result, tree depth and the scene diameter
+    // (clearance margin, traversal cut tolerance) come back to the host
     unsigned int host_bounds[12];
+    int host_ed[2] = {0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(host_bounds, bounds, sizeof(host_bounds), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_ed, errdepth, sizeof(host_ed), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    auto fail = [&](int code) {
+        cudaGetLastError();
+        cudaStreamSynchronize(stream);
+        cudaFreeAsync(tblock, stream);
+        cudaFree(sc->block);
+        delete sc;
+        return code;
+    };
+    if (e != cudaSuccess) return fail(UVC_E_CUDA);
+    if (host_ed[0] != 0) return fail(UVC_E_INVAL);
+    sc->depth = host_ed[1];
+    sc->depth4 = (sc->depth + 1) / 2;
     float diam = 0.f;
-    if (e == cudaSuccess && n > 0) {
+    if (n > 0) {
         double d2 = 0.0;
         for (int k = 0; k < 3; ++k) {
             const unsigned int lo_u = host_bounds[6 + k], hi_u = host_bounds[9 + k];
@@ -877,29 +999,23 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
         diam = (float)std::sqrt(d2);
     }
     sc->diameter = diam;
-    if (e == cudaSuccess && np > 0) {
+    if (np > 0) {
         // a patch closer than 2^-14 of the scene diameter to a coplanar triangle gets no clearance
-        k_clearance<<<(int)((np + B - 1) / B), B, 0, stream>>>(sc->nodes, sc->tri, n, sc->patch_s, sc->patch_n,
-                                                               sc->patch_excl, (int)np, diam * 6.103515625e-05f);
+        if (n > 1) {
+            const int cap = 3 * (sc->depth4 + 1) + 8;
+            const int blocks = (int)((np + kThreads - 1) / kThreads);
+            k_clearance4<<<blocks, kThreads, sizeof(int) * kWarpsPerBlock * cap, stream>>>(
+                sc->nodes4, sc->tri, n, sc->patch_s, sc->patch_n, sc->patch_excl, (int)np, diam * 6.103515625e-05f,
+                cap);
+        } else {
+            k_clearance<<<(int)((np + B - 1) / B), B, 0, stream>>>(sc->nodes, sc->tri, n, sc->patch_s,
+                                                                   sc->patch_n, sc->patch_excl, (int)np,
+                                                                   diam * 6.103515625e-05f);
+        }
         e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(UVC_E_CUDA);
     }
-    int host_ed[2] = {0, 0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_ed, errdepth, sizeof(host_ed), cudaMemcpyDeviceToHost, stream);
     cudaFreeAsync(tblock, stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(sc->block);
-        delete sc;
-        return UVC_E_CUDA;
-    }
-    if (host_ed[0] != 0) {
-        cudaFree(sc->block);
-        delete sc;
-        return UVC_E_INVAL;
-    }
-    sc->depth = host_ed[1];
-    sc->depth4 = (sc->depth + 1) / 2;
     sc->root = n == 1 ? ~0 : 0;
     *out = sc;
     return UVC_OK;
