@@ -63,16 +63,44 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+# ---------------------------------------------------------------------------
+# multi-rank bookkeeping (weak scaling over independent rooms; no data-path
+# collective: only a barrier and a max-reduction of the step time)
+# ---------------------------------------------------------------------------
+
+def rank_seeds(name: str, rank: int):
+    """Room and dwell-vector seeds of a rank: rank 0 runs the reference room of
+    the workload; rank r an independent room of the same size (seed + 1000 r)."""
+    base = {"tiny": 0, "ward": 1, "large": 3}[name]
+    return base + 1000 * rank, 2 + 1000 * rank
+
+
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest per-rank value (the job's time is its slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(pairs_per_rank: int, world: int, ms_step: float) -> float:
+    """Whole-job throughput in Gpairs/s: every rank's pairs over the slowest step."""
+    return world * pairs_per_rank / (ms_step * 1e-3) / 1e9
+
+
 def make_workload(name: str, rank: int):
     from synth import dwell_vectors, large_floor, tiny_room, ward_room
+    room_seed, t_seed = rank_seeds(name, rank)
     if name == "tiny":
-        s = tiny_room(seed=0 + 1000 * rank)
+        s = tiny_room(seed=room_seed)
     elif name == "large":
-        s = large_floor(seed=3 + 1000 * rank)
+        s = large_floor(seed=room_seed)
     else:
-        s = ward_room(seed=1 + 1000 * rank)
+        s = ward_room(seed=room_seed)
     nvec = 64 if name == "large" else NVEC
-    t = dwell_vectors(nvec, s.nc, seed=2 + 1000 * rank)
+    t = dwell_vectors(nvec, s.nc, seed=t_seed)
     return s, t
 
 
@@ -239,12 +267,9 @@ def run_ours(args):
     irr_ms = [ie[0].elapsed_time(ie[1]) for _, _, ie in step_ms]
     mean_ms = sum(per_step) / len(per_step)
     cov = ca.cpu().numpy().tolist()
-    t_max = torch.tensor([mean_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step = float(t_max.item())
+    ms_step = max_over_ranks(mean_ms, dist if world > 1 else None, dev)
     pairs = s.nc * s.np_
-    value = world * pairs / (ms_step * 1e-3) / 1e9
+    value = job_value(pairs, world, ms_step)
 
     # instrumented run (outside timing) for the dominant kernel's algorithmic work
     sc = scenes[-1]
@@ -339,12 +364,8 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
     torch.cuda.synchronize()
     for sc in scs:
         sc.free()
-    ms = a.elapsed_time(b) / n
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    return {"value": round(world * s.nc * s.np_ / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+    ms = max_over_ranks(a.elapsed_time(b) / n, dist, dev)
+    return {"value": round(job_value(s.nc * s.np_, world, ms), 4), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
             "steps": n}
 
