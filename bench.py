@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["ward", "tiny", "large"], default="ward")
+    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched"], default="ward")
+    p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
+    p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -370,7 +372,7 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
             "steps": n}
 
 
-_KERNEL_FILES = ("irradiance.cu", "uvc_internal.cuh")
+_KERNEL_FILES = ("irradiance.cu", "traverse.cuh", "uvc_internal.cuh")
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_irradiance_ward.txt")
 
 
@@ -451,10 +453,148 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# batched rooms x designs (one persistent launch per wave, CUDA graph)
+# ---------------------------------------------------------------------------
+
+def run_batched(args):
+    """Rooms of uneven size x 12 lamp designs: all matrices A plus the fluence
+    (16 dwell vectors) and coverage of every (room, design) job.  The batched
+    pipeline replays, per wave of rooms, one captured CUDA graph holding the
+    persistent batch launch and every job's fluence and coverage; the plain
+    pipeline makes the same calls job by job.  Scenes, candidates and dwell
+    vectors are resident before timing; A lives in a fixed pool reused by the
+    waves.  Metric: rooms per second (and the pair rate)."""
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    from synth import dwell_vectors
+    from synth.batched import batch, designs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    t_gen = time.perf_counter()
+    data = batch(args.rooms, base_seed=100 + 1000 * rank)
+    t_gen = time.perf_counter() - t_gen
+    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for _, L, _ in data[0][1]]   # the 12 designs' lamps
+    Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rooms = []
+    for room, jobs in data:
+        sc = uvc.build_scene(Td(room.verts), Td(room.tris), Td(room.centroid), Td(room.normal), Td(room.area),
+                             Td(room.excl))
+        js = [(Td(cand), d, Td(dwell_vectors(NVEC, cand.shape[0], seed=d))) for cand, _, d in jobs]
+        rooms.append((sc, js))
+    # waves of whole rooms under the A pool
+    pool_floats = int(args.pool_gb * 2 ** 30 / 4)
+    waves, cur, used = [], [], 0
+    for r, (sc, js) in enumerate(rooms):
+        need = sum(c.shape[0] * sc.np for c, _, _ in js)
+        if cur and used + need > pool_floats:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(r)
+        used += need
+    waves.append(cur)
+    biggest = max(sum(sum(c.shape[0] * rooms[r][0].np for c, _, _ in rooms[r][1]) for r in w) for w in waves)
+    pool = torch.empty(biggest, dtype=torch.float32, device=dev)
+
+    def wave_views(w):
+        views, off = [], 0
+        for r in w:
+            sc, js = rooms[r]
+            for cand, d, t in js:
+                n = cand.shape[0] * sc.np
+                views.append((sc, cand, d, t, pool[off:off + n].view(cand.shape[0], sc.np)))
+                off += n
+        return views
+
+    def post(sc, A, t, mus):
+        mu = uvc.fluence(sc, A, t, mu=mus)
+        uvc.coverage(sc, mu, MU_MIN)
+
+    # batched: one batch, one graph per wave (captured before timing)
+    graphs, batches, keep = [], [], []
+    tuned = None
+    for w in waves:
+        views = wave_views(w)
+        b = uvc.Batch([(sc, cand, d, A, None) for sc, cand, d, t, A in views], lamps)
+        if tuned is None:
+            tuned = b.autotune(0.02)
+        else:
+            b.set_config(*tuned)
+        mus = [torch.empty((NVEC, sc.np), device=dev) for sc, _, _, _, _ in views]
+        b.launch()
+        for (sc, cand, d, t, A), mu in zip(views, mus):
+            post(sc, A, t, mu)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            b.launch()
+            for (sc, cand, d, t, A), mu in zip(views, mus):
+                post(sc, A, t, mu)
+        graphs.append(g)
+        batches.append(b)
+        keep.append((views, mus))
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    a, bb = ev(), ev()
+    a.record()
+    for g in graphs:
+        g.replay()
+    bb.record()
+    torch.cuda.synchronize()
+    ms_batched = a.elapsed_time(bb)
+    clk = clocks.stop()
+    # plain: the same work, job by job
+    for w in waves[:1]:                        # warm the plain path
+        for sc, cand, d, t, A in wave_views(w)[:2]:
+            uvc.irradiance_matrix(sc, cand, lamps[d], A=A)
+            post(sc, A, t, None)
+    torch.cuda.synchronize()
+    a, bb = ev(), ev()
+    a.record()
+    for w in waves:
+        for sc, cand, d, t, A in wave_views(w):
+            uvc.irradiance_matrix(sc, cand, lamps[d], A=A)
+            post(sc, A, t, None)
+    bb.record()
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(bb)
+    pairs = sum(c.shape[0] * sc.np for sc, js in rooms for c, _, _ in js)
+    n = args.rooms
+    out = {
+        "metric": METRIC, "value": round(n / (ms_batched * 1e-3), 4), "unit": "rooms/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": round(ms_batched, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batched: {n} seeded rooms of uneven size (10k-200k triangles, 5k-300k patches, "
+                               "500-5,000 candidates, log-uniform) x 12 designs (lamp-bottom heights 0.3/0.5/0.8/1.1 m "
+                               "x line lamps 0.6/1.2/1.8 m, K = 4/8/12); all A plus fluence (16 vectors) and coverage",
+                   "rooms": n, "jobs": n * 12, "pairs": pairs, "waves": len(waves), "pool_gib": args.pool_gb,
+                   "tuned": {"cand_per_task": tuned[0], "blocks_per_sm": tuned[1]}},
+        "batched": {"rooms_per_s": round(n / (ms_batched * 1e-3), 4), "ms": round(ms_batched, 1),
+                    "gpairs_per_s": round(pairs / (ms_batched * 1e-3) / 1e9, 4)},
+        "plain": {"rooms_per_s": round(n / (ms_plain * 1e-3), 4), "ms": round(ms_plain, 1),
+                  "gpairs_per_s": round(pairs / (ms_plain * 1e-3) / 1e9, 4)},
+        "batched_over_plain": round(ms_plain / ms_batched, 4),
+        "clocks": clk, "generation_s": round(t_gen, 1),
+    }
+    for b in batches:
+        b.free()
+    for sc, _ in rooms:
+        sc.free()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

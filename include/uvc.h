@@ -32,6 +32,7 @@
 #ifndef UVC_H
 #define UVC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -232,6 +233,56 @@ int uvc_fluence_streamed_noalloc(const uvc_scene* scene, const float* cand, int6
  */
 int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu_min, float* cov_area,
                  float* cov_count, uvc_stream_t stream);
+
+/*
+ * Batched irradiance matrices: many jobs - (scene, candidates, lamp) triples,
+ * e.g. rooms of uneven size crossed with lamp designs (the robot-design
+ * comparison of Sec. V-C) - computed by one persistent launch whose warps walk
+ * the tasks of all jobs round-robin, so the launch ends evenly whatever the
+ * job sizes.  Each job writes its own A (and optional visibility words)
+ * exactly as uvc_irradiance_matrix would (bit-identical results).
+ *
+ *   uvc_job.scene, cand, nc, A, lda, vis  as in uvc_irradiance_matrix
+ *   uvc_job.lamp                          index into the `lamps` array
+ *
+ * uvc_batch_create copies the job table to `workspace` (caller-owned device
+ * memory of uvc_batch_workspace_bytes(njobs, nlamps) bytes, 256-byte
+ * aligned; it must outlive the batch) and synchronises `stream`.  The caller
+ * keeps the scenes and buffers alive while the batch is used.
+ * uvc_batch_launch enqueues the whole batch on `stream`; it reads no host
+ * data and allocates nothing, so it may be captured in a CUDA graph.
+ * uvc_batch_autotune times the tunable launch parameters on a sample of the
+ * batch's tasks (sample_fraction of them; the sampled A entries are written,
+ * correctly), keeps the fastest for the batch, caches it per size bucket for
+ * later batches of this process, and synchronises `stream`.
+ * uvc_batch_set_config sets them by hand (cand_per_task in {2, 4, 8, 16};
+ * blocks_per_sm 0 = as many as fit).  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+typedef struct {
+    const uvc_scene* scene;
+    const float* cand;
+    int64_t nc;
+    int32_t lamp;
+    float* A;
+    int64_t lda;
+    uint32_t* vis;
+} uvc_job;
+
+typedef struct {
+    int32_t cand_per_task;   /* candidates a warp handles for its 32 patches */
+    int32_t blocks_per_sm;   /* resident blocks per SM, 0 = occupancy limit */
+} uvc_batch_config;
+
+typedef struct uvc_batch uvc_batch; /* opaque host-side handle */
+
+size_t uvc_batch_workspace_bytes(int32_t njobs, int32_t nlamps);
+int uvc_batch_create(const uvc_job* jobs, int32_t njobs, const uvc_lamp* lamps, int32_t nlamps, void* workspace,
+                     size_t workspace_bytes, uvc_stream_t stream, uvc_batch** out);
+int uvc_batch_launch(uvc_batch* batch, uvc_stream_t stream);
+int uvc_batch_set_config(uvc_batch* batch, const uvc_batch_config* config, uvc_stream_t stream);
+int uvc_batch_autotune(uvc_batch* batch, double sample_fraction, uvc_batch_config* chosen, uvc_stream_t stream);
+int uvc_batch_info(const uvc_batch* batch, int64_t* total_pairs, int32_t* stack_cap, uvc_batch_config* config);
+int uvc_batch_free(uvc_batch* batch);
 
 /* uvc_status_string - static text for a status code (never NULL). */
 const char* uvc_status_string(int status);

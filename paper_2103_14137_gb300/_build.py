@@ -8,7 +8,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libuvc.so")
-SOURCES = ["build_bvh.cu", "irradiance.cu", "fluence.cu", "api.cu"]
+SOURCES = ["build_bvh.cu", "irradiance.cu", "batch.cu", "fluence.cu", "api.cu"]
+HEADERS = ["uvc_internal.cuh", "traverse.cuh"]
 INCLUDE = os.path.join(HERE, "..", "include")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -23,8 +24,7 @@ def _nvcc():
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "uvc_internal.cuh"),
-                                                       os.path.join(HERE, "..", "include", "uvc.h")]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(HERE, "..", "include", "uvc.h")]
     if not force and os.path.exists(OUT) and all(os.path.getmtime(OUT) >= os.path.getmtime(d) for d in deps):
         return OUT
     bdir = os.path.join(HERE, "_build")

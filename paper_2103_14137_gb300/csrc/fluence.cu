@@ -196,8 +196,10 @@ int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const 
     if (np == 0) return UVC_OK;
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)nvec * np, stream));
     static_assert(kWarpsPerBlock * kNV * 33 <= kWarpsPerBlock * kStages * kRows * (32 + kNV), "red fits");
-    cudaError_t e = cudaFuncSetAttribute(k_fluence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFluenceSmem);
-    if (e != cudaSuccess) return status_from_cuda(e);
+    // once per process (and so not during a stream capture that follows a first call)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_fluence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFluenceSmem);
+    if (attr != cudaSuccess) return status_from_cuda(attr);
     const int grid = (np + 31) / 32;
     for (int v0 = 0; v0 < nvec; v0 += kNV)
         k_fluence<<<grid, kThreads, kFluenceSmem, stream>>>(A, (int)nc, lda, t, nvec, v0, mu, np);

@@ -37,6 +37,15 @@ class _Patches(ctypes.Structure):
                 ("area", ctypes.c_void_p), ("excl", ctypes.c_void_p)]
 
 
+class _Job(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("cand", ctypes.c_void_p), ("nc", ctypes.c_int64),
+                ("lamp", ctypes.c_int32), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("vis", ctypes.c_void_p)]
+
+
+class _BatchConfig(ctypes.Structure):
+    _fields_ = [("cand_per_task", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -63,10 +72,21 @@ def library():
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "uvc_scene_export_bvh": [P, P, P, P, P],
     }
+    sig.update({
+        "uvc_batch_create": [ctypes.POINTER(_Job), i32, ctypes.POINTER(_Lamp), i32, P, ctypes.c_size_t, P,
+                             ctypes.POINTER(P)],
+        "uvc_batch_launch": [P, P],
+        "uvc_batch_set_config": [P, ctypes.POINTER(_BatchConfig), P],
+        "uvc_batch_autotune": [P, ctypes.c_double, ctypes.POINTER(_BatchConfig), P],
+        "uvc_batch_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(_BatchConfig)],
+        "uvc_batch_free": [P],
+    })
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.uvc_batch_workspace_bytes.argtypes = [i32, i32]
+    lib.uvc_batch_workspace_bytes.restype = ctypes.c_size_t
     lib.uvc_status_string.argtypes = [ctypes.c_int]
     lib.uvc_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -286,6 +306,73 @@ def scene_export_bvh(scene: Scene) -> dict:
     _check(library().uvc_scene_export_bvh(scene.handle, ptr(keys), ptr(order), ptr(children), ptr(boxes)),
            "uvc_scene_export_bvh")
     return dict(keys=keys, order=order, children=children, boxes=boxes)
+
+
+class Batch:
+    """Many irradiance matrices in one persistent launch (uvc_batch_*).
+
+    jobs: list of (scene, cand (nc,3) CUDA tensor, lamp index, A (nc, lda) CUDA
+    tensor, vis CUDA int32 tensor or None); lamps: list of Lamp.  The caller
+    keeps scenes and tensors alive while the batch is used (the batch keeps
+    references to the tensors it was given).  launch() may be captured in a
+    CUDA graph."""
+
+    def __init__(self, jobs, lamps, stream=None):
+        lib = library()
+        cj = (_Job * len(jobs))()
+        self._keep = []
+        for q, (scene, cand, lamp, A, vis) in enumerate(jobs):
+            nc = cand.shape[0]
+            cj[q].scene = scene.handle
+            cj[q].cand = _dev(cand, torch.float32, "cand", (nc, 3))
+            cj[q].nc = nc
+            cj[q].lamp = int(lamp)
+            cj[q].A = _dev(A, torch.float32, "A")
+            cj[q].lda = A.shape[1]
+            if A.dim() != 2 or A.shape[0] != nc:
+                raise ValueError("A must be (nc, lda)")
+            cj[q].vis = None if vis is None else _dev(vis, torch.int32, "vis")
+            self._keep.append((scene, cand, A, vis))
+        cl = (_Lamp * len(lamps))(*[L._c() for L in lamps])
+        nbytes = lib.uvc_batch_workspace_bytes(len(jobs), len(lamps))
+        dev = jobs[0][1].device
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        off = (-self.workspace.data_ptr()) % 256
+        out = ctypes.c_void_p()
+        _check(lib.uvc_batch_create(cj, len(jobs), cl, len(lamps), ctypes.c_void_p(self.workspace.data_ptr() + off),
+                                    nbytes, _stream(stream), ctypes.byref(out)), "uvc_batch_create")
+        self._h = out
+
+    def launch(self, stream=None):
+        _check(library().uvc_batch_launch(self._h, _stream(stream)), "uvc_batch_launch")
+
+    def set_config(self, cand_per_task: int, blocks_per_sm: int = 0, stream=None):
+        c = _BatchConfig(cand_per_task, blocks_per_sm)
+        _check(library().uvc_batch_set_config(self._h, ctypes.byref(c), _stream(stream)), "uvc_batch_set_config")
+
+    def autotune(self, sample_fraction: float = 0.05, stream=None):
+        c = _BatchConfig()
+        _check(library().uvc_batch_autotune(self._h, float(sample_fraction), ctypes.byref(c), _stream(stream)),
+               "uvc_batch_autotune")
+        return c.cand_per_task, c.blocks_per_sm
+
+    def info(self):
+        tp, cap, c = ctypes.c_int64(), ctypes.c_int32(), _BatchConfig()
+        _check(library().uvc_batch_info(self._h, ctypes.byref(tp), ctypes.byref(cap), ctypes.byref(c)),
+               "uvc_batch_info")
+        return dict(total_pairs=tp.value, stack_cap=cap.value, cand_per_task=c.cand_per_task,
+                    blocks_per_sm=c.blocks_per_sm)
+
+    def free(self):
+        if getattr(self, "_h", None) is not None:
+            library().uvc_batch_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 def vis_to_bool(vis: torch.Tensor, np_: int) -> np.ndarray:
