@@ -284,6 +284,82 @@ int uvc_batch_autotune(uvc_batch* batch, double sample_fraction, uvc_batch_confi
 int uvc_batch_info(const uvc_batch* batch, int64_t* total_pairs, int32_t* stack_cap, uvc_batch_config* config);
 int uvc_batch_free(uvc_batch* batch);
 
+/*
+ * Learned candidate proposal.  The paper samples vantage configurations on a
+ * uniform grid and leaves a better choice to future work (Sec. VI); the
+ * relaxed LP of Sec. IV-D (Eq. (9)) then keeps only the few configurations
+ * with non-zero dwell time.  The proposal scores every candidate with a small
+ * perceptron before the irradiance matrix is computed, so the matrix is
+ * evaluated for the best-scoring candidates only.  It has no counterpart in
+ * the paper's own pipeline.
+ *
+ * uvc_candidate_features - the scorer's input, per candidate c (row i):
+ *   feat[i][b], b = 0..63   fraction of the patch area whose centroid lies at
+ *                           squared distance d^2 = |s_j - c|^2 in bin b; the bin
+ *                           edges are E_b = fl32((0.1 * 250^(b/64))^2) m^2 for
+ *                           b = 1..63 (E_0 = 0, E_64 = infinity), bin b holding
+ *                           E_b <= d^2 < E_{b+1}
+ *   feat[i][64]             distance from c to the nearest triangle (metres;
+ *                           3e38 for a scene without triangles)
+ *   feat[i][65]             the height (z) of c
+ *   cand  float[nc][3] device;  feat  float[nc][66] device (caller-owned).
+ * FP32 arithmetic with fixed-order sums (deterministic).  Errors: UVC_E_INVAL
+ * (NULL scene, nc out of range, NULL buffer with nc > 0), UVC_E_CUDA.
+ */
+int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, uvc_stream_t stream);
+
+/*
+ * uvc_select_top - the k best-scoring of n candidates (higher score first,
+ * equal scores to the lower index, NaN lowest), written in ascending index
+ * order: out_idx[r] (int32, may be NULL) and out_cand[r][3] = cand[idx][3]
+ * (may be NULL if out_idx is given).  All arrays on the device.
+ * n in [0, 16384], k in [0, n].  One block; enqueued on `stream`, capturable.
+ * Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
+                   uvc_stream_t stream);
+
+/*
+ * The scorer: logit(x) = w3 . relu(relu(x W1 + b1) W2 + b2) + b3, with x the
+ * candidate features (in_dim of them, zero-padded to a multiple of 16),
+ * hidden width `hidden`.  W1, W2 and the activations are stored in BF16, the
+ * products run on the tensor cores with FP32 accumulation; biases, w3, the
+ * head and all gradients are FP32.  Training minimises the weighted binary
+ * cross-entropy sum_i w_i (softplus(s_i) - y_i s_i) of the logits s_i against
+ * labels y_i in [0, 1] (1 = the LP of Eq. (9) gave the candidate a non-zero
+ * dwell time) with Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected).
+ *
+ * Parameter layout (float[uvc_mlp_param_count]): W1 [in_pad][hidden] (rows
+ * in_dim..in_pad-1 unused, keep them 0), b1 [hidden], W2 [hidden][hidden],
+ * b2 [hidden], w3 [hidden], b3 [1].  Gradients use the same layout.
+ *
+ * uvc_mlp_create     in_dim in [1, 4096], hidden a multiple of 8 in [8, 4096],
+ *                    max_batch in [1, 2^24]; He-normal initial weights from a
+ *                    seeded generator, zero biases; one device allocation,
+ *                    freed by uvc_mlp_free.  Synchronises the device.
+ * uvc_mlp_params     copies the FP32 parameters to (set = 0) or from (set = 1)
+ *                    host memory; n must equal the parameter count.  Synchronous.
+ * uvc_mlp_forward    logit float[B] device <- x float[B][in_dim] device, B <=
+ *                    max_batch; enqueued on `stream`.
+ * uvc_mlp_train_step one forward, backward and Adam update on (x, y, w), each
+ *                    device arrays of B rows; *loss (device float, may be NULL)
+ *                    receives the batch loss.  lr > 0.  Enqueued on `stream`;
+ *                    one model is not used from two streams at once.
+ * uvc_mlp_grads      the gradients of the last training step (host copy).
+ * Errors: UVC_E_INVAL for NULL handles or out-of-range sizes, UVC_E_NOMEM,
+ * UVC_E_CUDA.
+ */
+typedef struct uvc_mlp uvc_mlp; /* opaque handle */
+
+int uvc_mlp_create(int32_t in_dim, int32_t hidden, int32_t max_batch, uint64_t seed, uvc_mlp** out);
+int uvc_mlp_free(uvc_mlp* model);
+int64_t uvc_mlp_param_count(const uvc_mlp* model);
+int uvc_mlp_params(uvc_mlp* model, float* host, int64_t n, int32_t set);
+int uvc_mlp_forward(uvc_mlp* model, const float* x, int32_t B, float* logit, uvc_stream_t stream);
+int uvc_mlp_train_step(uvc_mlp* model, const float* x, const float* y, const float* w, int32_t B, float lr,
+                       float* loss, uvc_stream_t stream);
+int uvc_mlp_grads(const uvc_mlp* model, float* host, int64_t n);
+
 /* uvc_status_string - static text for a status code (never NULL). */
 const char* uvc_status_string(int status);
 

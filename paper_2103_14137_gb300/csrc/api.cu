@@ -135,6 +135,19 @@ int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu
     return uvc::coverage(scene, mu, nvec, mu_min, cov_area, cov_count, (cudaStream_t)stream);
 }
 
+int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc)) return UVC_E_INVAL;
+    if (nc > 0 && (!cand || !feat)) return UVC_E_INVAL;
+    return uvc::candidate_features(scene, cand, nc, feat, (cudaStream_t)stream);
+}
+
+int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
+                   uvc_stream_t stream) {
+    if (n < 0 || n > 16384 || k < 0 || k > n) return UVC_E_INVAL;
+    if (k > 0 && (!score || (!out_cand && !out_idx) || (out_cand && !cand))) return UVC_E_INVAL;
+    return uvc::select_top(score, n, k, cand, out_cand, out_idx, (cudaStream_t)stream);
+}
+
 const char* uvc_status_string(int status) {
     switch (status) {
         case UVC_OK: return "ok";

@@ -97,4 +97,9 @@ int coverage(const uvc_scene* sc, const float* mu, int32_t nvec, float mu_min, f
              float* cov_count, cudaStream_t stream);
 void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream_t stream);
 
+// learned-proposal features (features.cu)
+int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, cudaStream_t stream);
+int select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
+               cudaStream_t stream);
+
 }  // namespace uvc

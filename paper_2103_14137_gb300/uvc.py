@@ -80,6 +80,14 @@ def library():
         "uvc_batch_autotune": [P, ctypes.c_double, ctypes.POINTER(_BatchConfig), P],
         "uvc_batch_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(_BatchConfig)],
         "uvc_batch_free": [P],
+        "uvc_candidate_features": [P, P, i64, P, P],
+        "uvc_select_top": [P, i64, i64, P, P, P, P],
+        "uvc_mlp_create": [i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(P)],
+        "uvc_mlp_free": [P],
+        "uvc_mlp_params": [P, P, i64, i32],
+        "uvc_mlp_forward": [P, P, i32, P, P],
+        "uvc_mlp_train_step": [P, P, P, P, i32, ctypes.c_float, P, P],
+        "uvc_mlp_grads": [P, P, i64],
     })
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -87,6 +95,8 @@ def library():
         fn.restype = ctypes.c_int
     lib.uvc_batch_workspace_bytes.argtypes = [i32, i32]
     lib.uvc_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.uvc_mlp_param_count.argtypes = [P]
+    lib.uvc_mlp_param_count.restype = i64
     lib.uvc_status_string.argtypes = [ctypes.c_int]
     lib.uvc_status_string.restype = ctypes.c_char_p
     _lib = lib
@@ -288,6 +298,113 @@ def coverage(scene: Scene, mu, mu_min: float, stream=None):
                                 _dev(cc, torch.float32, "cov_count"), _stream(stream))
     _check(rc, "uvc_coverage")
     return ca, cc
+
+
+FEATURES = 66
+
+
+def candidate_features(scene: Scene, cand, feat=None, stream=None):
+    """(nc, 66) float32 scorer inputs: 64-bin area histogram of squared
+    distances to the patch centroids, nearest-triangle distance, height."""
+    nc = cand.shape[0]
+    if feat is None:
+        feat = torch.empty((nc, FEATURES), dtype=torch.float32, device=cand.device)
+    rc = library().uvc_candidate_features(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                          _dev(feat, torch.float32, "feat", (nc, FEATURES)), _stream(stream))
+    _check(rc, "uvc_candidate_features")
+    return feat
+
+
+def select_top(score, k: int, cand=None, out_cand=None, out_idx=None, stream=None):
+    """The k best-scoring candidates in ascending index order: (idx int32 (k,),
+    cand (k, 3) or None).  Ties go to the lower index."""
+    n = score.shape[0]
+    dev = score.device
+    if out_idx is None:
+        out_idx = torch.empty(k, dtype=torch.int32, device=dev)
+    if cand is not None and out_cand is None:
+        out_cand = torch.empty((k, 3), dtype=torch.float32, device=dev)
+    rc = library().uvc_select_top(_dev(score, torch.float32, "score", (n,)), n, int(k),
+                                  _dev(cand, torch.float32, "cand", (n, 3)) if cand is not None else None,
+                                  _dev(out_cand, torch.float32, "out_cand", (k, 3)) if out_cand is not None else None,
+                                  _dev(out_idx, torch.int32, "out_idx", (k,)), _stream(stream))
+    _check(rc, "uvc_select_top")
+    return out_idx, out_cand
+
+
+class Mlp:
+    """The candidate scorer (uvc_mlp_*): BF16 tensor-core perceptron
+    in_dim -> hidden -> hidden -> 1 with FP32 master weights and Adam."""
+
+    def __init__(self, in_dim: int, hidden: int = 256, max_batch: int = 65536, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(library().uvc_mlp_create(int(in_dim), int(hidden), int(max_batch), int(seed), ctypes.byref(h)),
+               "uvc_mlp_create")
+        self.handle, self.in_dim, self.hidden, self.max_batch = h, int(in_dim), int(hidden), int(max_batch)
+        self.in_pad = (self.in_dim + 15) // 16 * 16
+        self.nparam = int(library().uvc_mlp_param_count(h))
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            library().uvc_mlp_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        _check(library().uvc_mlp_params(self.handle, out.ctypes.data_as(ctypes.c_void_p), self.nparam, 0),
+               "uvc_mlp_params")
+        return out
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, np.float32)
+        if a.size != self.nparam:
+            raise ValueError(f"expected {self.nparam} parameters, got {a.size}")
+        _check(library().uvc_mlp_params(self.handle, a.ctypes.data_as(ctypes.c_void_p), self.nparam, 1),
+               "uvc_mlp_params")
+
+    def split(self, flat) -> dict:
+        """Views of a flat parameter (or gradient) array by name."""
+        P, H = self.in_pad, self.hidden
+        sizes = [("W1", (P, H)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", (1,))]
+        out, o = {}, 0
+        for name, shp in sizes:
+            n = int(np.prod(shp))
+            out[name] = flat[o:o + n].reshape(shp)
+            o += n
+        return out
+
+    def forward(self, x, logit=None, stream=None):
+        B = x.shape[0]
+        if logit is None:
+            logit = torch.empty(B, dtype=torch.float32, device=x.device)
+        _check(library().uvc_mlp_forward(self.handle, _dev(x, torch.float32, "x", (B, self.in_dim)), B,
+                                         _dev(logit, torch.float32, "logit", (B,)), _stream(stream)),
+               "uvc_mlp_forward")
+        return logit
+
+    def train_step(self, x, y, w, lr: float, loss=None, stream=None):
+        """One Adam step on the weighted BCE loss; returns the device loss (1,)."""
+        B = x.shape[0]
+        if loss is None:
+            loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _check(library().uvc_mlp_train_step(self.handle, _dev(x, torch.float32, "x", (B, self.in_dim)),
+                                            _dev(y, torch.float32, "y", (B,)), _dev(w, torch.float32, "w", (B,)),
+                                            B, float(lr), _dev(loss, torch.float32, "loss", (1,)),
+                                            _stream(stream)),
+               "uvc_mlp_train_step")
+        return loss
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        _check(library().uvc_mlp_grads(self.handle, out.ctypes.data_as(ctypes.c_void_p), self.nparam),
+               "uvc_mlp_grads")
+        return out
 
 
 def scene_status(scene: Scene, stream=None) -> int:

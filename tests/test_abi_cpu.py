@@ -57,6 +57,16 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.uvc_coverage(None, None, 1, 1.0, None, None, None) == 1
     assert lib.uvc_scene_status(None, None) == 1
     assert lib.uvc_free_scene(None) == 0
+    assert lib.uvc_candidate_features(None, None, 0, None, None) == 1
+    assert lib.uvc_select_top(None, 20000, 1, None, None, None, None) == 1      # n above 16384
+    assert lib.uvc_select_top(None, 10, 11, None, None, None, None) == 1        # k > n
+    assert lib.uvc_mlp_create(0, 256, 16, 0, ctypes.byref(out)) == 1           # in_dim < 1
+    assert lib.uvc_mlp_create(66, 250, 16, 0, ctypes.byref(out)) == 1          # hidden not a multiple of 8
+    assert lib.uvc_mlp_create(66, 256, 0, 0, ctypes.byref(out)) == 1           # max_batch < 1
+    assert lib.uvc_mlp_forward(None, None, 1, None, None) == 1
+    assert lib.uvc_mlp_train_step(None, None, None, None, 1, ctypes.c_float(1e-3), None, None) == 1
+    assert lib.uvc_mlp_param_count(None) == -1
+    assert lib.uvc_mlp_free(None) == 0
 
 
 def test_lamp_struct_layout():

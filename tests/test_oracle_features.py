@@ -1,0 +1,38 @@
+"""Pins of the feature oracle: bin edges by their definition, a histogram of
+hand-placed patches, and the point-triangle distance against closed forms and
+dense sampling of the triangle."""
+import numpy as np
+
+from oracle import features as F
+
+
+def test_bin_edges():
+    E = F.bin_edges_sq()
+    assert E.shape == (63,) and np.all(np.diff(E) > 0)
+    assert np.isclose(np.sqrt(E[0]), 0.1 * 250 ** (1 / 64)) and np.isclose(np.sqrt(E[31]), 0.1 * 250 ** 0.5)
+
+
+def test_histogram_hand_placed():
+    c = np.array([[0.0, 0.0, 0.0]])
+    # distances 0.05 (bin 0), 1.0, 30 (last bin); areas 1, 2, 3
+    s = np.array([[0.05, 0, 0], [0, 1.0, 0], [0, 0, 30.0]], np.float32)
+    f, amb = F.features(np.zeros((3, 3)), np.zeros((0, 3), np.int64), s, [1, 2, 3], c)
+    b1 = int(np.floor(64 * np.log(1.0 / 0.1) / np.log(250)))    # d = 1 m lies in bin floor(64 log10 / log250)
+    assert f[0, 0] == 1 / 6 and f[0, 63] == 3 / 6 and f[0, b1] == 2 / 6
+    assert np.isclose(f[0, :64].sum(), 1.0)
+
+
+def test_point_triangle_distance():
+    a, b, c = np.array([[0.0, 0, 0]]), np.array([[2.0, 0, 0]]), np.array([[0.0, 2, 0]])
+    d = lambda p: F._point_triangle_distance(np.array(p, float), a, b, c)[0]  # noqa: E731
+    assert np.isclose(d([0.5, 0.5, 3.0]), 3.0)                     # above the interior
+    assert np.isclose(d([-1.0, -1.0, 0.0]), np.sqrt(2))            # nearest to vertex a
+    assert np.isclose(d([1.0, -2.0, 0.0]), 2.0)                    # nearest to edge ab
+    assert np.isclose(d([2.0, 2.0, 0.0]), np.sqrt(2))              # nearest to edge bc (x+y=2)
+    rng = np.random.default_rng(0)
+    uv = rng.uniform(size=(20000, 2))
+    uv = np.where(uv.sum(1, keepdims=True) > 1, 1 - uv, uv)
+    pts = a + uv[:, :1] * (b - a) + uv[:, 1:] * (c - a)
+    for p in rng.uniform(-3, 3, size=(10, 3)):
+        assert d(p) <= np.linalg.norm(pts - p, axis=1).min() + 1e-12
+        assert d(p) >= np.linalg.norm(pts - p, axis=1).min() - 0.03
