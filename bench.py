@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched"], default="ward")
+    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned"], default="ward")
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
@@ -589,12 +589,215 @@ def run_batched(args):
     print(json.dumps(out), flush=True)
 
 
+def run_learned(args):
+    """Batched + learned proposal against the plain method, in rooms/s.
+
+    Per (room, design) job the learned pipeline computes the irradiance of all
+    candidates on a probe of 1% of the patches (one batched launch), the
+    scorer features, one scorer pass over all jobs, keeps the best source of
+    every sketch patch plus the best-scoring candidates (20% in all), checks
+    the other probe half for lit area lost, and computes the exact matrix of
+    the kept candidates (a second batched launch) with its fluence (16 dwell
+    vectors) and coverage; all of it replays as one CUDA graph per wave.  Jobs
+    whose check fails are then recomputed on all candidates (inside the timed
+    region).  The plain pipeline computes every job's full matrix, fluence and
+    coverage job by job.  Scenes, probe scenes, candidates and dwell vectors
+    are resident before timing.  The judged quality (lost coverage, added
+    dwell against the plain LP) comes from the scorer's report."""
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    from paper_2103_14137_gb300 import proposal as prop
+    from synth import dwell_vectors
+    from synth.batched import batch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    t_gen = time.perf_counter()
+    data = batch(args.rooms, base_seed=100 + 1000 * rank)
+    t_gen = time.perf_counter() - t_gen
+    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for _, L, _ in data[0][1]]
+    Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rooms, total_nc = [], 0
+    for room, jobs in data:
+        sc = uvc.build_scene(Td(room.verts), Td(room.tris), Td(room.centroid), Td(room.normal), Td(room.area),
+                             Td(room.excl))
+        probe, half = prop.probe_columns(room.np_, seed=room.info["seed"] * 977)
+        psc = uvc.build_scene(Td(room.verts), Td(room.tris), Td(room.centroid[probe]), Td(room.normal[probe]),
+                              Td(room.area[probe]), Td(room.excl[probe]))
+        js = []
+        for cand, _, d in jobs:
+            nc = cand.shape[0]
+            k = prop.keep_count(nc)
+            js.append({"cand": Td(cand), "d": d, "nc": nc, "k": k, "t_full": Td(dwell_vectors(NVEC, nc, seed=d)),
+                       "t_kept": Td(dwell_vectors(NVEC, k, seed=d)),
+                       "kept": torch.zeros((k, 3), dtype=torch.float32, device=dev),
+                       "idx": torch.zeros(k, dtype=torch.int32, device=dev)})
+            total_nc += nc
+        rooms.append({"sc": sc, "psc": psc, "area_p": Td(room.area[probe].astype(np.float32)), "half": half,
+                      "P": int(probe.size), "np": room.np_, "jobs": js})
+    scorer = prop.Scorer.load(max_batch=max(1, total_nc))
+    # waves of whole rooms under the pool (reduced matrices + probe matrices)
+    pool_floats = int(args.pool_gb * 2 ** 30 / 4)
+    waves, cur, used = [], [], 0
+    for r, R in enumerate(rooms):
+        need = sum(j["k"] * R["np"] + j["nc"] * R["P"] for j in R["jobs"])
+        if cur and used + need > pool_floats:
+            waves.append(cur)
+            cur, used = [], 0
+        cur.append(r)
+        used += need
+    waves.append(cur)
+    biggest_job = max(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
+    pool = torch.empty(max(sum(j["k"] * rooms[r]["np"] + j["nc"] * rooms[r]["P"] for r in w
+                               for j in rooms[r]["jobs"]) for w in waves), dtype=torch.float32, device=dev)
+    full_tmp = torch.empty(biggest_job, dtype=torch.float32, device=dev)
+    flags = torch.zeros(sum(len(R["jobs"]) for R in rooms), dtype=torch.float32, device=dev)
+    maxhalf = max(R["P"] - R["half"] for R in rooms)
+    work = uvc.probe_features_work(max(R["half"] for R in rooms), dev)
+    lost_scratch = torch.empty(max(1, maxhalf), dtype=torch.float32, device=dev)
+    feat = torch.empty((max(1, total_nc), prop.IN_DIM), dtype=torch.float32, device=dev)
+    score = torch.empty(max(1, total_nc), dtype=torch.float32, device=dev)
+    mus_flat = torch.empty(NVEC * max(R["np"] for R in rooms), dtype=torch.float32, device=dev)
+    mus = lambda n: mus_flat[:NVEC * n].view(NVEC, n)  # noqa: E731
+
+    def wave_layout(w):
+        """Views of the pool (probe then reduced matrices) and feature rows."""
+        off, row, lay = 0, 0, []
+        for r in w:
+            R = rooms[r]
+            for j in R["jobs"]:
+                Ap = pool[off:off + j["nc"] * R["P"]].view(j["nc"], R["P"])
+                off += j["nc"] * R["P"]
+                lay.append((R, j, Ap, row))
+                row += j["nc"]
+        for q, (R, j, Ap, row0) in enumerate(lay):
+            Ar = pool[off:off + j["k"] * R["np"]].view(j["k"], R["np"])
+            off += j["k"] * R["np"]
+            lay[q] = (R, j, Ap, Ar, row0)
+        return lay, row
+
+    job_ids = {}
+    for R in rooms:
+        for j in R["jobs"]:
+            job_ids[id(j)] = len(job_ids)
+
+    def learned_wave(lay, nrows, bprobe, bred):
+        bprobe.launch()
+        for R, j, Ap, Ar, row0 in lay:
+            prop.features(R["sc"], j["cand"], Ap[:, :R["half"]], R["area_p"][:R["half"]],
+                          feat=feat[row0:row0 + j["nc"]], work=work)
+        scorer.scores(feat[:nrows], out=score[:nrows])
+        for R, j, Ap, Ar, row0 in lay:
+            sj = score[row0:row0 + j["nc"]]
+            uvc.mark_best(Ap[:, :R["half"]], sj)
+            uvc.select_top(sj, j["k"], cand=j["cand"], out_cand=j["kept"], out_idx=j["idx"])
+            q = job_ids[id(j)]
+            uvc.probe_lost(Ap[:, R["half"]:], j["idx"], R["area_p"][R["half"]:], out=flags[q:q + 1],
+                           lost=lost_scratch[:R["P"] - R["half"]])
+        bred.launch()
+        for R, j, Ap, Ar, row0 in lay:
+            mu = uvc.fluence(R["sc"], Ar, j["t_kept"], mu=mus(R["np"]))
+            uvc.coverage(R["sc"], mu, MU_MIN)
+
+    graphs, batches, tuned = [], [], None
+    for w in waves:
+        lay, nrows = wave_layout(w)
+        bprobe = uvc.Batch([(R["psc"], j["cand"], j["d"], Ap, None) for R, j, Ap, Ar, _ in lay], lamps)
+        bred = uvc.Batch([(R["sc"], j["kept"], j["d"], Ar, None) for R, j, Ap, Ar, _ in lay], lamps)
+        if tuned is None:
+            tuned = bprobe.autotune(0.05)
+        bprobe.set_config(*tuned)
+        bred.set_config(*tuned)
+        learned_wave(lay, nrows, bprobe, bred)          # eager pass: fills the kept buffers
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            learned_wave(lay, nrows, bprobe, bred)
+        graphs.append(g)
+        batches += [bprobe, bred]
+
+    def plain_job(R, j):
+        A = full_tmp[:j["nc"] * R["np"]].view(j["nc"], R["np"])
+        uvc.irradiance_matrix(R["sc"], j["cand"], lamps[j["d"]], A=A)
+        mu = uvc.fluence(R["sc"], A, j["t_full"], mu=mus(R["np"]))
+        uvc.coverage(R["sc"], mu, MU_MIN)
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for g in graphs:                                    # warm replay
+        g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    a, b = ev(), ev()
+    a.record()
+    for g in graphs:
+        g.replay()
+    fl = (flags > prop.LOST_MAX).cpu().numpy()          # the check, read back on the host
+    fallback = [(R, j) for R in rooms for j in R["jobs"] if fl[job_ids[id(j)]]]
+    for R, j in fallback:
+        plain_job(R, j)
+    b.record()
+    torch.cuda.synchronize()
+    ms_learned = a.elapsed_time(b)
+    clk = clocks.stop()
+    # plain: every job's full matrix, job by job
+    plain_job(rooms[0], rooms[0]["jobs"][0])
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for R in rooms:
+        for j in R["jobs"]:
+            plain_job(R, j)
+    b.record()
+    torch.cuda.synchronize()
+    ms_plain = a.elapsed_time(b)
+    n = args.rooms
+    pairs_plain = sum(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
+    pairs_learned = sum(j["k"] * R["np"] + j["nc"] * R["P"] for R in rooms for j in R["jobs"]) + \
+        sum(j["nc"] * R["np"] for R, j in fallback)
+    rep_path = os.path.join(ROOT, "paper_2103_14137_gb300", "data", "scorer_report.json")
+    quality = None
+    if os.path.exists(rep_path):
+        with open(rep_path) as f:
+            rep = json.load(f)
+        quality = {k: rep.get(k) for k in ("eval_jobs", "lost_coverage_mean", "lost_coverage_max",
+                                           "added_dwell_mean", "added_dwell_max", "fallback_rate",
+                                           "support_recall_mean")}
+        quality["source"] = "paper_2103_14137_gb300/data/scorer_report.json (train_scorer judge)"
+    out = {
+        "metric": METRIC, "value": round(n / (ms_learned * 1e-3), 4), "unit": "rooms/s", "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": round(ms_learned, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (scorer bf16)", "data": "synthetic",
+        "config": {"workload": f"learned: {n} seeded rooms of uneven size x 12 designs; batched + learned "
+                               f"proposal (keep {prop.KEEP:.0%}, probe {prop.PROBE:.0%}) vs plain full matrices; "
+                               "fluence (16 vectors) and coverage of every job",
+                   "rooms": n, "jobs": len(job_ids), "waves": len(waves), "tuned": list(tuned)},
+        "learned": {"rooms_per_s": round(n / (ms_learned * 1e-3), 4), "ms": round(ms_learned, 1),
+                    "pairs": pairs_learned, "fallback_jobs": len(fallback)},
+        "plain": {"rooms_per_s": round(n / (ms_plain * 1e-3), 4), "ms": round(ms_plain, 1), "pairs": pairs_plain},
+        "learned_over_plain": round(ms_plain / ms_learned, 4), "quality": quality,
+        "clocks": clk, "generation_s": round(t_gen, 1),
+    }
+    for bb in batches:
+        bb.free()
+    scorer.close()
+    for R in rooms:
+        R["sc"].free()
+        R["psc"].free()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

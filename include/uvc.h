@@ -302,11 +302,36 @@ int uvc_batch_free(uvc_batch* batch);
  *   feat[i][64]             distance from c to the nearest triangle (metres;
  *                           3e38 for a scene without triangles)
  *   feat[i][65]             the height (z) of c
- *   cand  float[nc][3] device;  feat  float[nc][66] device (caller-owned).
+ *   cand  float[nc][3] device;  feat  float rows of ldf >= 66 floats, device
+ *   (caller-owned; columns 66..ldf-1 untouched).
  * FP32 arithmetic with fixed-order sums (deterministic).  Errors: UVC_E_INVAL
  * (NULL scene, nc out of range, NULL buffer with nc > 0), UVC_E_CUDA.
  */
-int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, uvc_stream_t stream);
+int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, int64_t ldf,
+                           uvc_stream_t stream);
+
+/*
+ * uvc_probe_features - a visibility sketch of each candidate from the
+ * irradiance of all candidates on a small probe sample of the patches (a
+ * matrix from uvc_irradiance_matrix on a scene holding only the probe
+ * patches).  With E*_j = max_i A[i][j] the best irradiance patch j gets from
+ * any candidate, L the lit probe patches (E*_j > 0) and
+ * Ebar = sum_L a_j E*_j / sum_L a_j:
+ *   hardness  h_j = floor(log2(fl32(E*_j / Ebar))) + 4, clamped to [0, 7]
+ *   efficiency bin of fl32(A[i][j] / E*_j): [0, .5) [.5, .7) [.7, .8) [.8, .9)
+ *             [.9, .95) [.95, 1] -> 0..5
+ *   feat[i][6 h + e] = sum of a_j over L in that (h, e) cell / sum_L a_j
+ * In LP terms (Eq. (9)), a candidate that is the most efficient source for
+ * hard-to-light patches is the one the optimum spends time at.
+ *   A     float[nc][lda] device, lda >= np;  area  float[np] device
+ *   work  device scratch of uvc_probe_features_work_bytes(np) bytes (4-aligned)
+ *   feat  float rows of ldf >= 48 floats, device (columns 48.. untouched)
+ * FP32 with compensated, fixed-order sums; the bins are decided in FP32.
+ * Enqueued on `stream`, capturable.  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+size_t uvc_probe_features_work_bytes(int64_t np);
+int uvc_probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const float* area, void* work,
+                       float* feat, int64_t ldf, uvc_stream_t stream);
 
 /*
  * uvc_select_top - the k best-scoring of n candidates (higher score first,
@@ -318,6 +343,33 @@ int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc
  */
 int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
                    uvc_stream_t stream);
+
+/*
+ * uvc_mark_best - for every probe patch j that some candidate lights, set
+ * score[i*] = value where i* = argmax_i A[i][j] (the lowest index among equal
+ * maxima), so that a following uvc_select_top keeps the best source of every
+ * probe patch whatever the scorer says (value = +inf; if more candidates are
+ * marked than kept, the lower indices win).
+ *   A  float[nc][lda] device, lda >= np;  score  float[nc] device, updated
+ * Enqueued on `stream`, capturable.  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value,
+                  uvc_stream_t stream);
+
+/*
+ * uvc_probe_lost - the fallback check of the proposal: of a probe sample of
+ * patches (columns of A), the area fraction that some candidate lights
+ * (A[i][j] > 0 for some row i < nc) but none of the selected rows idx[0..k)
+ * does:  *out = sum_j a_j [lit by all, dark for the selection] / sum_j a_j.
+ *   A     float[nc][lda] device (irradiance of all candidates on the probe)
+ *   idx   int32[k] device, rows of A (e.g. from uvc_select_top); rows outside
+ *         [0, nc) are ignored
+ *   area  float[np] device;  lost  float[np] device scratch;  out  float[1] device
+ * Compensated FP32 sums in a fixed order.  Enqueued on `stream`, capturable.
+ * Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+int uvc_probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
+                   const float* area, float* lost, float* out, uvc_stream_t stream);
 
 /*
  * The scorer: logit(x) = w3 . relu(relu(x W1 + b1) W2 + b2) + b3, with x the

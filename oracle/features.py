@@ -83,3 +83,46 @@ def features(verts, tris, centroid, area, cand):
         out[i, NBINS] = _point_triangle_distance(c, A, B, C).min() if t.shape[0] else np.inf
         out[i, NBINS + 1] = c[2]
     return out, amb
+
+
+EFF_EDGES = np.array([0.5, 0.7, 0.8, 0.9, 0.95], np.float32)
+HARD_BINS, EFF_BINS = 8, 6
+
+
+def probe_features(A, area):
+    """(nc, 48) visibility sketch and the per-patch hardness ambiguity mask.
+
+    From the irradiance of all candidates on a probe sample of patches:
+    E*_j = max_i A[i][j] (the best any candidate gives patch j), the lit set
+    L = {j : E*_j > 0}, Ebar = sum_L a_j E*_j / sum_L a_j; patch j's hardness
+    h_j = floor(log2(E*_j / Ebar)) + 4 clamped to [0, 7]; candidate i's
+    efficiency on it A[i][j] / E*_j, binned at 0.5, 0.7, 0.8, 0.9, 0.95.
+    feat[i][6 h + e] = the lit area in that cell / sum_L a_j.  The ratios that
+    pick a bin are taken in FP32 (the kernel's precision), so the efficiency
+    bin is exact; Ebar is a sum, so a ratio within 1e-5 of a power of two is
+    flagged ambiguous (its hardness bin may differ by one)."""
+    A32 = np.asarray(A, np.float32)
+    a = np.asarray(area, np.float32).astype(np.float64)
+    nc, m = A32.shape
+    out = np.zeros((nc, HARD_BINS * EFF_BINS))
+    amb = np.zeros(m, bool)
+    if nc == 0 or m == 0:
+        return out, amb
+    emax = A32.max(0)
+    lit = emax > 0
+    if not lit.any():
+        return out, amb
+    S1 = a[lit].sum()
+    ebar = np.float32((a[lit] * emax[lit].astype(np.float64)).sum() / S1)
+    r = emax[lit] / ebar                                   # float32 division
+    _, ex = np.frexp(r)
+    h = np.clip(ex - 1 + 4, 0, HARD_BINS - 1)
+    l2 = np.log2(r.astype(np.float64))
+    amb[np.flatnonzero(lit)] = np.abs(l2 - np.round(l2)) <= 1e-5 / np.log(2)
+    eff = A32[:, lit] / emax[lit][None, :]                 # float32 division
+    eb = np.searchsorted(EFF_EDGES, eff, side="right")     # number of edges <= e
+    cell = h[None, :] * EFF_BINS + eb
+    w = a[lit] / S1
+    for i in range(nc):
+        out[i] = np.bincount(cell[i], weights=w, minlength=HARD_BINS * EFF_BINS)
+    return out, amb

@@ -6,7 +6,7 @@ patches (Eq. (4), (7)), the fluence A^T t (Eq. (5)) and the covered-area
 fraction, as hand-written CUDA for sm_103a behind the C ABI of include/uvc.h.
 """
 from ._build import build  # noqa: F401
-from .uvc import (FEATURES, Batch, Lamp, Mlp, Scene, UvcError, build_scene, candidate_features,  # noqa: F401
+from .uvc import (FEATURES, PROBE_FEATURES, Batch, Lamp, Mlp, Scene, UvcError, build_scene, candidate_features,  # noqa: F401
                   coverage, fluence, fluence_streamed, fluence_streamed_noalloc, irradiance_counters,
-                  irradiance_matrix, library, line_lamp, point_lamp, scene_export_bvh, scene_status, select_top,
+                  irradiance_matrix, library, line_lamp, mark_best, point_lamp, probe_features, probe_features_work, probe_lost, scene_export_bvh, scene_status, select_top,
                   status_string, vis_to_bool)

@@ -135,10 +135,24 @@ int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu
     return uvc::coverage(scene, mu, nvec, mu_min, cov_area, cov_count, (cudaStream_t)stream);
 }
 
-int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, uvc_stream_t stream) {
-    if (!scene || !uvc::count_ok(nc)) return UVC_E_INVAL;
+int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, int64_t ldf,
+                           uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX || ldf < 66) return UVC_E_INVAL;
     if (nc > 0 && (!cand || !feat)) return UVC_E_INVAL;
-    return uvc::candidate_features(scene, cand, nc, feat, (cudaStream_t)stream);
+    return uvc::candidate_features(scene, cand, nc, feat, ldf, (cudaStream_t)stream);
+}
+
+size_t uvc_probe_features_work_bytes(int64_t np) {
+    return np < 0 ? 0 : (size_t)(np + 4) * sizeof(float) + (size_t)np + 16;
+}
+
+int uvc_probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const float* area, void* work,
+                       float* feat, int64_t ldf, uvc_stream_t stream) {
+    if (!uvc::count_ok(nc) || !uvc::count_ok(np) || nc > INT32_MAX || np > INT32_MAX || lda < np || ldf < 48)
+        return UVC_E_INVAL;
+    if (nc > 0 && (!feat || !work || (np > 0 && (!A || !area)))) return UVC_E_INVAL;
+    if (reinterpret_cast<uintptr_t>(work) % 4) return UVC_E_INVAL;
+    return uvc::probe_features(A, nc, lda, np, area, static_cast<float*>(work), feat, ldf, (cudaStream_t)stream);
 }
 
 int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
@@ -146,6 +160,22 @@ int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, 
     if (n < 0 || n > 16384 || k < 0 || k > n) return UVC_E_INVAL;
     if (k > 0 && (!score || (!out_cand && !out_idx) || (out_cand && !cand))) return UVC_E_INVAL;
     return uvc::select_top(score, n, k, cand, out_cand, out_idx, (cudaStream_t)stream);
+}
+
+int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value,
+                  uvc_stream_t stream) {
+    if (!uvc::count_ok(nc) || !uvc::count_ok(np) || nc > INT32_MAX || np > INT32_MAX || lda < np) return UVC_E_INVAL;
+    if (nc > 0 && np > 0 && (!A || !score)) return UVC_E_INVAL;
+    return uvc::mark_best(A, nc, lda, np, score, value, (cudaStream_t)stream);
+}
+
+int uvc_probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
+                   const float* area, float* lost, float* out, uvc_stream_t stream) {
+    if (!uvc::count_ok(nc) || !uvc::count_ok(np) || np > INT32_MAX || nc > INT32_MAX || k < 0 || k > nc ||
+        lda < np || !out)
+        return UVC_E_INVAL;
+    if (np > 0 && (!area || !lost || (nc > 0 && !A) || (k > 0 && !idx))) return UVC_E_INVAL;
+    return uvc::probe_lost(A, nc, lda, np, idx, k, area, lost, out, (cudaStream_t)stream);
 }
 
 const char* uvc_status_string(int status) {

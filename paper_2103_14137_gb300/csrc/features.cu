@@ -12,7 +12,6 @@ namespace uvc {
 namespace {
 
 constexpr int kBins = 64;
-constexpr int kFeat = kBins + 2;
 constexpr int kHistThreads = 256;
 
 struct Edges {
@@ -24,7 +23,7 @@ struct Edges {
 __global__ void __launch_bounds__(kHistThreads) k_feat_hist(const float4* __restrict__ ps, int np,
                                                              const float* __restrict__ area_total,
                                                              const float* __restrict__ cand, Edges E,
-                                                             float* __restrict__ feat) {
+                                                             float* __restrict__ feat, int64_t ldf) {
     extern __shared__ float slot[];   // [kBins][kHistThreads]
     __shared__ float edge[kBins - 1];
     const int i = blockIdx.x;
@@ -49,7 +48,7 @@ __global__ void __launch_bounds__(kHistThreads) k_feat_hist(const float4* __rest
     for (int b = t; b < kBins; b += blockDim.x) {
         float sum = 0.f;
         for (int q = 0; q < kHistThreads; ++q) sum += slot[b * kHistThreads + q];
-        feat[(size_t)i * kFeat + b] = tot > 0.f ? sum / tot : 0.f;
+        feat[i * ldf + b] = tot > 0.f ? sum / tot : 0.f;
     }
 }
 
@@ -101,7 +100,7 @@ __device__ __forceinline__ float box_d2(float3 p, float lx, float ly, float lz, 
 
 // One thread per candidate: nearest-triangle search over the binary tree.
 __global__ void k_feat_clear(const Node* __restrict__ nodes, const float4* __restrict__ tri, int nt,
-                             const float* __restrict__ cand, int nc, float* __restrict__ feat) {
+                             const float* __restrict__ cand, int nc, float* __restrict__ feat, int64_t ldf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     const float3 p = make_float3(cand[3 * (size_t)i], cand[3 * (size_t)i + 1], cand[3 * (size_t)i + 2]);
@@ -128,8 +127,8 @@ __global__ void k_feat_clear(const Node* __restrict__ nodes, const float4* __res
         if ((lfirst ? dR : dL) < best) stack[top++] = lfirst ? nd.r.y : nd.r.x;
         if ((lfirst ? dL : dR) < best) stack[top++] = lfirst ? nd.r.x : nd.r.y;
     }
-    feat[(size_t)i * kFeat + kBins] = nt > 0 ? sqrtf(best) : 3.0e38f;
-    feat[(size_t)i * kFeat + kBins + 1] = p.z;
+    feat[i * ldf + kBins] = nt > 0 ? sqrtf(best) : 3.0e38f;
+    feat[i * ldf + kBins + 1] = p.z;
 }
 
 constexpr int kSelectMax = 16384;
@@ -204,7 +203,192 @@ __global__ void __launch_bounds__(kSelectThreads) k_select_top(const float* __re
         }
 }
 
+// Per probe patch j: its area if some candidate lights it (A[i][j] > 0) but
+// none of the selected ones does, else 0.
+__global__ void k_probe_lost(const float* __restrict__ A, int nc, int64_t lda, int np,
+                             const int32_t* __restrict__ idx, int k, const float* __restrict__ area,
+                             float* __restrict__ lost) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    bool full = false, red = false;
+    for (int i = 0; i < nc && !full; ++i) full = A[(int64_t)i * lda + j] > 0.f;
+    for (int r = 0; r < k && full && !red; ++r) {
+        const int i = idx[r];
+        if (i >= 0 && i < nc) red = A[(int64_t)i * lda + j] > 0.f;   // rows out of range are ignored
+    }
+    lost[j] = (full && !red) ? area[j] : 0.f;
+}
+
+// out = sum(lost) / sum(area), compensated sums in a fixed order (one block).
+__global__ void k_probe_total(const float* __restrict__ lost, const float* __restrict__ area, int np,
+                              float* __restrict__ out) {
+    __shared__ float sl[256], sa[256];
+    float l = 0.f, cl = 0.f, a = 0.f, ca = 0.f;
+    for (int j = threadIdx.x; j < np; j += 256) {
+        const float yl = lost[j] - cl, tl = l + yl;
+        cl = (tl - l) - yl;
+        l = tl;
+        const float ya = area[j] - ca, ta = a + ya;
+        ca = (ta - a) - ya;
+        a = ta;
+    }
+    sl[threadIdx.x] = l;
+    sa[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float L = 0.f, cL = 0.f, S = 0.f, cS = 0.f;
+        for (int q = 0; q < 256; ++q) {
+            const float yl = sl[q] - cL, tl = L + yl;
+            cL = (tl - L) - yl;
+            L = tl;
+            const float ya = sa[q] - cS, ta = S + ya;
+            cS = (ta - S) - ya;
+            S = ta;
+        }
+        *out = S > 0.f ? L / S : 0.f;
+    }
+}
+
+constexpr int kHardBins = 8, kEffBins = 6, kProbeFeat = kHardBins * kEffBins;
+constexpr int kProbeWarps = 4;
+
+// E*_j = max_i A[i][j] (thread per probe patch, coalesced rows).
+__global__ void k_col_max(const float* __restrict__ A, int nc, int64_t lda, int np, float* __restrict__ emax) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    float m = 0.f;
+    for (int i = 0; i < nc; ++i) m = fmaxf(m, A[(int64_t)i * lda + j]);
+    emax[j] = m;
+}
+
+// Lit-area-weighted mean of E* (compensated sums, fixed order, one block),
+// then each lit patch's hardness bin floor(log2(E*_j / mean)) + 4 clamped to
+// [0, 7] (-1 for an unlit patch); stats = (sum a E*, sum a) over lit patches.
+__global__ void k_probe_bins(const float* __restrict__ emax, const float* __restrict__ area, int np,
+                             float* __restrict__ stats, signed char* __restrict__ hb) {
+    __shared__ float s0[256], s1[256];
+    __shared__ float mean_sh;
+    float a0 = 0.f, c0 = 0.f, a1 = 0.f, c1 = 0.f;
+    for (int j = threadIdx.x; j < np; j += 256) {
+        const float e = emax[j];
+        if (!(e > 0.f)) continue;
+        const float y0 = area[j] * e - c0, t0 = a0 + y0;
+        c0 = (t0 - a0) - y0;
+        a0 = t0;
+        const float y1 = area[j] - c1, t1 = a1 + y1;
+        c1 = (t1 - a1) - y1;
+        a1 = t1;
+    }
+    s0[threadIdx.x] = a0;
+    s1[threadIdx.x] = a1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float A0 = 0.f, C0 = 0.f, A1 = 0.f, C1 = 0.f;
+        for (int q = 0; q < 256; ++q) {
+            const float y0 = s0[q] - C0, t0 = A0 + y0;
+            C0 = (t0 - A0) - y0;
+            A0 = t0;
+            const float y1 = s1[q] - C1, t1 = A1 + y1;
+            C1 = (t1 - A1) - y1;
+            A1 = t1;
+        }
+        stats[0] = A0;
+        stats[1] = A1;
+        mean_sh = A1 > 0.f ? A0 / A1 : 0.f;
+    }
+    __syncthreads();
+    const float mean = mean_sh;
+    for (int j = threadIdx.x; j < np; j += 256) {
+        const float e = emax[j];
+        if (!(e > 0.f) || !(mean > 0.f)) {
+            hb[j] = -1;
+            continue;
+        }
+        int ex;
+        frexpf(e / mean, &ex);   // e / mean = f 2^ex, f in [0.5, 1): floor(log2) = ex - 1
+        hb[j] = (signed char)min(kHardBins - 1, max(0, ex - 1 + 4));
+    }
+}
+
+// One warp per candidate: area of the lit probe patches by (hardness bin,
+// efficiency bin of A[i][j] / E*_j), over the lit area.  Per-lane slots in
+// shared memory, lanes added in a fixed order.
+__global__ void __launch_bounds__(kProbeWarps * 32) k_probe_feat(const float* __restrict__ A, int nc, int64_t lda,
+                                                                  int np, const float* __restrict__ emax,
+                                                                  const signed char* __restrict__ hb,
+                                                                  const float* __restrict__ area,
+                                                                  const float* __restrict__ stats,
+                                                                  float* __restrict__ feat, int64_t ldf) {
+    __shared__ float slot[kProbeWarps][kProbeFeat][32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = blockIdx.x * kProbeWarps + w;
+    if (i >= nc) return;
+    for (int b = 0; b < kProbeFeat; ++b) slot[w][b][lane] = 0.f;
+    const float* row = A + (int64_t)i * lda;
+    for (int j = lane; j < np; j += 32) {
+        const int h = hb[j];
+        if (h < 0) continue;
+        const float e = row[j] / emax[j];
+        const int eb = e < 0.5f ? 0 : e < 0.7f ? 1 : e < 0.8f ? 2 : e < 0.9f ? 3 : e < 0.95f ? 4 : 5;
+        slot[w][h * kEffBins + eb][lane] += area[j];
+    }
+    __syncwarp();
+    const float lit = stats[1];
+    for (int b = lane; b < kProbeFeat; b += 32) {
+        float sum = 0.f;
+        for (int q = 0; q < 32; ++q) sum += slot[w][b][q];
+        feat[(int64_t)i * ldf + b] = lit > 0.f ? sum / lit : 0.f;
+    }
+}
+
+// For each lit probe patch j, score[argmax_i A[i][j]] = value (the lowest
+// index among equal maxima).  Several patches may write the same candidate
+// with the same value.
+__global__ void k_mark_best(const float* __restrict__ A, int nc, int64_t lda, int np, float* __restrict__ score,
+                            float value) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= np) return;
+    float m = 0.f;
+    int best = -1;
+    for (int i = 0; i < nc; ++i) {
+        const float v = A[(int64_t)i * lda + j];
+        if (v > m) {
+            m = v;
+            best = i;
+        }
+    }
+    if (best >= 0) score[best] = value;
+}
+
 }  // namespace
+
+int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, cudaStream_t stream) {
+    if (np > 0 && nc > 0)
+        k_mark_best<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, score, value);
+    return status_from_cuda(cudaGetLastError());
+}
+
+int probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const float* area, float* work,
+                   float* feat, int64_t ldf, cudaStream_t stream) {
+    if (nc == 0) return UVC_OK;
+    float* emax = work;
+    float* stats = work + np;
+    signed char* hb = reinterpret_cast<signed char*>(work + np + 4);
+    if (np > 0) k_col_max<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, emax);
+    k_probe_bins<<<1, 256, 0, stream>>>(emax, area, (int)np, stats, hb);
+    k_probe_feat<<<(int)((nc + kProbeWarps - 1) / kProbeWarps), kProbeWarps * 32, 0, stream>>>(
+        A, (int)nc, lda, (int)np, emax, hb, area, stats, feat, ldf);
+    return status_from_cuda(cudaGetLastError());
+}
+
+int probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
+               const float* area, float* lost, float* out, cudaStream_t stream) {
+    if (np > 0) {
+        k_probe_lost<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, idx, (int)k, area, lost);
+    }
+    k_probe_total<<<1, 256, 0, stream>>>(lost, area, (int)np, out);
+    return status_from_cuda(cudaGetLastError());
+}
 
 int select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
                cudaStream_t stream) {
@@ -221,7 +405,8 @@ int select_top(const float* score, int64_t n, int64_t k, const float* cand, floa
     return status_from_cuda(cudaGetLastError());
 }
 
-int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, cudaStream_t stream) {
+int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, int64_t ldf,
+                       cudaStream_t stream) {
     if (nc == 0) return UVC_OK;
     Edges E;
     for (int b = 1; b < kBins; ++b) {
@@ -232,8 +417,9 @@ int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float
                                                          (int)(sizeof(float) * kBins * kHistThreads));
     if (attr != cudaSuccess) return status_from_cuda(attr);
     k_feat_hist<<<(int)nc, kHistThreads, sizeof(float) * kBins * kHistThreads, stream>>>(
-        sc->patch_s, (int)sc->np, sc->area_total, cand, E, feat);
-    k_feat_clear<<<(int)((nc + 127) / 128), 128, 0, stream>>>(sc->nodes, sc->tri, (int)sc->nt, cand, (int)nc, feat);
+        sc->patch_s, (int)sc->np, sc->area_total, cand, E, feat, ldf);
+    k_feat_clear<<<(int)((nc + 127) / 128), 128, 0, stream>>>(sc->nodes, sc->tri, (int)sc->nt, cand, (int)nc, feat,
+                                                              ldf);
     return status_from_cuda(cudaGetLastError());
 }
 

@@ -98,7 +98,13 @@ int coverage(const uvc_scene* sc, const float* mu, int32_t nvec, float mu_min, f
 void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream_t stream);
 
 // learned-proposal features (features.cu)
-int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, cudaStream_t stream);
+int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, int64_t ldf,
+                       cudaStream_t stream);
+int probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const float* area, float* work,
+                   float* feat, int64_t ldf, cudaStream_t stream);
+int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, cudaStream_t stream);
+int probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
+               const float* area, float* lost, float* out, cudaStream_t stream);
 int select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,
                cudaStream_t stream);
 

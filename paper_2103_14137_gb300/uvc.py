@@ -80,8 +80,11 @@ def library():
         "uvc_batch_autotune": [P, ctypes.c_double, ctypes.POINTER(_BatchConfig), P],
         "uvc_batch_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(_BatchConfig)],
         "uvc_batch_free": [P],
-        "uvc_candidate_features": [P, P, i64, P, P],
+        "uvc_candidate_features": [P, P, i64, P, i64, P],
+        "uvc_probe_features": [P, i64, i64, i64, P, P, P, i64, P],
         "uvc_select_top": [P, i64, i64, P, P, P, P],
+        "uvc_probe_lost": [P, i64, i64, i64, P, i64, P, P, P, P],
+        "uvc_mark_best": [P, i64, i64, i64, P, ctypes.c_float, P],
         "uvc_mlp_create": [i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(P)],
         "uvc_mlp_free": [P],
         "uvc_mlp_params": [P, P, i64, i32],
@@ -95,6 +98,8 @@ def library():
         fn.restype = ctypes.c_int
     lib.uvc_batch_workspace_bytes.argtypes = [i32, i32]
     lib.uvc_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.uvc_probe_features_work_bytes.argtypes = [i64]
+    lib.uvc_probe_features_work_bytes.restype = ctypes.c_size_t
     lib.uvc_mlp_param_count.argtypes = [P]
     lib.uvc_mlp_param_count.restype = i64
     lib.uvc_status_string.argtypes = [ctypes.c_int]
@@ -301,17 +306,54 @@ def coverage(scene: Scene, mu, mu_min: float, stream=None):
 
 
 FEATURES = 66
+PROBE_FEATURES = 48
+
+
+def _rows(feat, nc, min_cols, name):
+    if not isinstance(feat, torch.Tensor) or not feat.is_cuda or feat.dtype != torch.float32:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    if feat.dim() != 2 or feat.shape[0] != nc or feat.shape[1] < min_cols or feat.stride(1) != 1 \
+            or (nc > 1 and feat.stride(0) < min_cols):
+        raise ValueError(f"{name} must be ({nc}, >= {min_cols}) with unit column stride")
+    return ctypes.c_void_p(feat.data_ptr() if feat.numel() else 0), max(feat.stride(0), min_cols)
 
 
 def candidate_features(scene: Scene, cand, feat=None, stream=None):
     """(nc, 66) float32 scorer inputs: 64-bin area histogram of squared
-    distances to the patch centroids, nearest-triangle distance, height."""
+    distances to the patch centroids, nearest-triangle distance, height.
+    `feat` may be a column slice of a wider row-major buffer."""
     nc = cand.shape[0]
     if feat is None:
         feat = torch.empty((nc, FEATURES), dtype=torch.float32, device=cand.device)
-    rc = library().uvc_candidate_features(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
-                                          _dev(feat, torch.float32, "feat", (nc, FEATURES)), _stream(stream))
+    fp, ld = _rows(feat, nc, FEATURES, "feat")
+    rc = library().uvc_candidate_features(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc, fp, ld,
+                                          _stream(stream))
     _check(rc, "uvc_candidate_features")
+    return feat
+
+
+def probe_features_work(np_: int, device="cuda"):
+    n = int(library().uvc_probe_features_work_bytes(int(np_)))
+    return torch.empty((n + 3) // 4, dtype=torch.float32, device=device)
+
+
+def probe_features(A, area, feat=None, work=None, lda=None, stream=None):
+    """(nc, 48) visibility sketch from the probe irradiance A (nc, np): area of
+    the lit probe patches by hardness and efficiency bin (uvc_probe_features).
+    A may be a column slice (unit column stride) of a wider matrix."""
+    nc, np_ = A.shape
+    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
+        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
+    lda = max(A.stride(0), np_) if lda is None else lda
+    if feat is None:
+        feat = torch.empty((nc, PROBE_FEATURES), dtype=torch.float32, device=A.device)
+    if work is None:
+        work = probe_features_work(np_, A.device)
+    fp, ld = _rows(feat, nc, PROBE_FEATURES, "feat")
+    rc = library().uvc_probe_features(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, lda, np_,
+                                      _dev(area, torch.float32, "area", (np_,)),
+                                      ctypes.c_void_p(work.data_ptr()), fp, ld, _stream(stream))
+    _check(rc, "uvc_probe_features")
     return feat
 
 
@@ -330,6 +372,37 @@ def select_top(score, k: int, cand=None, out_cand=None, out_idx=None, stream=Non
                                   _dev(out_idx, torch.int32, "out_idx", (k,)), _stream(stream))
     _check(rc, "uvc_select_top")
     return out_idx, out_cand
+
+
+def mark_best(A, score, value=float("inf"), stream=None):
+    """score[argmax_i A[i, j]] = value for every lit column j of A (nc, np)."""
+    nc, np_ = A.shape
+    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
+        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
+    rc = library().uvc_mark_best(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, max(A.stride(0), np_), np_,
+                                 _dev(score, torch.float32, "score", (nc,)), float(value), _stream(stream))
+    _check(rc, "uvc_mark_best")
+    return score
+
+
+def probe_lost(A, idx, area, out=None, lost=None, stream=None):
+    """Area fraction of the probe patches lit by some row of A (nc, np) but by
+    none of the rows idx; (1,) float32 on the device."""
+    nc, np_ = A.shape
+    k = idx.shape[0]
+    if out is None:
+        out = torch.empty(1, dtype=torch.float32, device=A.device)
+    if lost is None:
+        lost = torch.empty(np_, dtype=torch.float32, device=A.device)
+    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
+        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
+    lda = max(A.stride(0), np_)
+    rc = library().uvc_probe_lost(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, lda, np_,
+                                  _dev(idx, torch.int32, "idx", (k,)), k,
+                                  _dev(area, torch.float32, "area", (np_,)), _dev(lost, torch.float32, "lost", (np_,)),
+                                  _dev(out, torch.float32, "out", (1,)), _stream(stream))
+    _check(rc, "uvc_probe_lost")
+    return out
 
 
 class Mlp:

@@ -57,7 +57,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.uvc_coverage(None, None, 1, 1.0, None, None, None) == 1
     assert lib.uvc_scene_status(None, None) == 1
     assert lib.uvc_free_scene(None) == 0
-    assert lib.uvc_candidate_features(None, None, 0, None, None) == 1
+    assert lib.uvc_candidate_features(None, None, 0, None, 66, None) == 1
+    assert lib.uvc_probe_features(None, 1, 10, 10, None, None, None, 47, None) == 1      # ldf < 48
     assert lib.uvc_select_top(None, 20000, 1, None, None, None, None) == 1      # n above 16384
     assert lib.uvc_select_top(None, 10, 11, None, None, None, None) == 1        # k > n
     assert lib.uvc_mlp_create(0, 256, 16, 0, ctypes.byref(out)) == 1           # in_dim < 1

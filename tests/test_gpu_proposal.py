@@ -166,3 +166,102 @@ def test_mlp_rejects_oversized_batch():
     with pytest.raises(uvc.UvcError):
         m.forward(T(np.zeros((9, 66), np.float32)))
     m.close()
+
+
+@pytest.mark.parametrize("nc,np_,k", [(1, 1, 1), (50, 333, 10), (1200, 3000, 240), (7, 0, 3)])
+def test_probe_lost_matches_definition(nc, np_, k):
+    rng = np.random.default_rng(nc + np_)
+    A = rng.uniform(0, 1, (nc, np_)).astype(np.float32)
+    A[rng.uniform(size=A.shape) < 0.97] = 0.0
+    area = rng.uniform(0.001, 0.02, np_).astype(np.float32)
+    idx = np.sort(rng.choice(nc, k, replace=False)).astype(np.int32)
+    got = float(uvc.probe_lost(T(A), T(idx), T(area)).item())
+    lit_all = (A > 0).any(0)
+    lit_kept = (A[idx] > 0).any(0)
+    want = float((area * (lit_all & ~lit_kept)).sum() / area.sum()) if np_ else 0.0
+    assert abs(got - want) <= 1e-6 * max(want, 1e-30) + 1e-9
+
+
+@pytest.mark.parametrize("nc,np_", [(1, 1), (37, 200), (1200, 3001), (5, 0)])
+def test_probe_features_match_oracle(nc, np_):
+    rng = np.random.default_rng(nc * 7 + np_)
+    A = (rng.uniform(0, 3, (nc, np_)) ** 3).astype(np.float32)
+    A[rng.uniform(size=A.shape) < 0.4] = 0.0
+    if np_ > 4:
+        A[:, :3] = 0.0                                      # unlit patches
+        A[: max(1, nc // 2), 3] = 1.5                       # a tie for the best candidate
+    area = rng.uniform(0.001, 0.02, np_).astype(np.float32)
+    got = uvc.probe_features(T(A), T(area)).cpu().numpy().astype(np.float64)
+    want, amb = OF.probe_features(A, area)
+    lit = A.max(0) > 0 if np_ else np.zeros(0, bool)
+    tol_amb = float(area[amb & lit].sum() / max(area[lit].sum(), 1e-30)) if np_ else 0.0
+    tol = tol_amb + (np_ / 32 + 34) * U32 * want + 1e-7
+    assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want) - tol)
+
+
+def test_feature_columns_share_one_buffer():
+    s = tiny_room()
+    sc = build(s)
+    cand = T(s.cand)
+    rng = np.random.default_rng(0)
+    A = rng.uniform(0, 1, (s.nc, 300)).astype(np.float32)
+    area = rng.uniform(0.001, 0.02, 300).astype(np.float32)
+    wide = torch.full((s.nc, 128), -7.0, device="cuda")
+    uvc.candidate_features(sc, cand, feat=wide[:, :66])
+    uvc.probe_features(T(A)[:, 100:], T(area[100:]), feat=wide[:, 66:114])
+    a = uvc.candidate_features(sc, cand)
+    b = uvc.probe_features(T(np.ascontiguousarray(A[:, 100:])), T(area[100:]))
+    torch.testing.assert_close(wide[:, :66], a, rtol=0, atol=0)
+    torch.testing.assert_close(wide[:, 66:114], b, rtol=0, atol=0)
+    assert bool((wide[:, 114:] == -7.0).all())
+    sc.free()
+
+
+@pytest.mark.parametrize("nc,np_", [(1, 5), (40, 300), (3000, 257), (9, 0)])
+def test_mark_best_bit_exact(nc, np_):
+    rng = np.random.default_rng(nc + 3 * np_)
+    A = rng.integers(0, 5, (nc, np_)).astype(np.float32)    # many ties
+    if np_:
+        A[:, 0] = 0.0                                        # an unlit patch marks nothing
+    score = rng.standard_normal(nc).astype(np.float32)
+    got = uvc.mark_best(T(A), T(score), value=9.5).cpu().numpy()
+    want = score.copy()
+    for j in range(np_):
+        if A[:, j].max() > 0:
+            want[int(np.argmax(A[:, j]))] = 9.5              # first maximum = lowest index
+    np.testing.assert_array_equal(got, want)
+
+
+def test_learned_selection_keeps_best_sources():
+    """The shipped scorer end to end on one room: 20% kept, ascending indices,
+    every sketch patch's best source among them, the check in [0, 1]."""
+    from paper_2103_14137_gb300 import proposal as prop
+    from synth.batched import designs
+    from synth.scenes import line_lamp
+    room = batched_room(131)
+    h, L, K = designs()[4]
+    cand = design_candidates(room, h, L, 700, seed=5)
+    sc = build(room)
+    lamp = line_lamp(L, K, 120.0)
+    cd = T(cand)
+    probe, half = prop.probe_columns(room.np_, seed=9)
+    pi = torch.from_numpy(probe).cuda()
+    A, _ = uvc.irradiance_matrix(sc, cd, uvc.Lamp(lamp.offsets, lamp.weights, lamp.power))
+    Ap = A.index_select(1, pi).contiguous()
+    area = T(np.asarray(room.area, np.float32)).index_select(0, pi).contiguous()
+    scorer = prop.Scorer.load()
+    feat = prop.features(sc, cd, Ap[:, :half], area[:half])
+    assert bool(torch.isfinite(feat).all())
+    idx, kept = scorer.select(feat, cd, A_sketch=Ap[:, :half])
+    idx = idx.cpu().numpy()
+    assert idx.size == prop.keep_count(cand.shape[0]) and np.all(np.diff(idx) > 0)
+    np.testing.assert_array_equal(kept.cpu().numpy(), cand[idx])
+    Ah = Ap[:, :half].cpu().numpy()
+    lit = Ah.max(0) > 0
+    best = np.unique(Ah.argmax(0)[lit])
+    if best.size <= idx.size:
+        assert np.isin(best, idx).all()
+    lost = float(uvc.probe_lost(Ap[:, half:], T(idx.astype(np.int32)), area[half:]).item())
+    assert 0.0 <= lost <= 1.0
+    scorer.close()
+    sc.free()

@@ -36,3 +36,34 @@ def test_point_triangle_distance():
     for p in rng.uniform(-3, 3, size=(10, 3)):
         assert d(p) <= np.linalg.norm(pts - p, axis=1).min() + 1e-12
         assert d(p) >= np.linalg.norm(pts - p, axis=1).min() - 0.03
+
+
+def test_probe_features_hand_worked():
+    # E* = (1, 2, 0.5), all lit; Ebar = (1*1 + 1*2 + 2*0.5) / 4 = 1
+    # hardness: log2 (1, 2, 0.5) = (0, 1, -1) -> bins (4, 5, 3)
+    # efficiencies: cand 0 (1, 0, 1) -> (5, 0, 5); cand 1 (0.5, 1, 1) -> (1, 5, 5)
+    A = [[1.0, 0.0, 0.5], [0.5, 2.0, 0.5]]
+    f, amb = F.probe_features(A, [1.0, 1.0, 2.0])
+    want = np.zeros((2, 48))
+    want[0, 4 * 6 + 5], want[0, 5 * 6 + 0], want[0, 3 * 6 + 5] = 0.25, 0.25, 0.5
+    want[1, 4 * 6 + 1], want[1, 5 * 6 + 5], want[1, 3 * 6 + 5] = 0.25, 0.25, 0.5
+    np.testing.assert_array_equal(f, want)
+    assert amb.all()                                        # every ratio is an exact power of two
+
+
+def test_probe_features_invariants():
+    rng = np.random.default_rng(5)
+    A = rng.uniform(0, 3, (40, 500)).astype(np.float32)
+    A[rng.uniform(size=A.shape) < 0.5] = 0
+    A[:, :20] = 0                                          # unlit probe patches are left out
+    area = rng.uniform(0.001, 0.01, 500)
+    f, _ = F.probe_features(A, area)
+    np.testing.assert_allclose(f.sum(1), 1.0)              # every lit patch counted once per candidate
+    best = A.argmax(0)
+    # a candidate's top efficiency bin holds at least the patches it is best for
+    for i in range(5):
+        mine = (best == i) & (A.max(0) > 0)
+        assert f[i, 5::6].sum() >= area[mine].sum() / area[A.max(0) > 0].sum() - 1e-12
+    # scaling all irradiance leaves the sketch unchanged (bins are ratios)
+    f2, _ = F.probe_features(A * 4.0, area)
+    np.testing.assert_array_equal(f, f2)
