@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned"], default="ward")
+    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned", "area"], default="ward")
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
@@ -790,6 +790,68 @@ def run_learned(args):
     print(json.dumps(out), flush=True)
 
 
+def run_area(args):
+    """Area-mean irradiance (uvc_irradiance_area_mean: solid-angle closed form
+    with vertex checks, centroid sample as fallback) on the ward room, timed
+    beside the centroid-sample matrix (uvc_irradiance_matrix) on the same
+    inputs; A > L2, so no flush is needed between steps.  Metric: pairs/s."""
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    from synth import ward_room
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    s = ward_room(seed=1 + 1000 * rank)
+    if args.candidates:
+        s.cand = s.cand[:args.candidates]
+    Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    sc = uvc.build_scene(Td(s.verts), Td(s.tris), Td(s.centroid), Td(s.normal), Td(s.area), Td(s.excl))
+    cand, ptri = Td(s.cand), Td(s.ptri)
+    lamp = uvc.Lamp(s.lamp.offsets, s.lamp.weights, s.lamp.power)
+    A = torch.empty((s.nc, s.np_), dtype=torch.float32, device=dev)
+    ncl = torch.empty((s.nc, s.np_), dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(k):
+            a, b = ev(), ev()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_area = timed(lambda: uvc.irradiance_area_mean(sc, cand, lamp, ptri, A=A), args.steps, args.warmup)
+    clk = clocks.stop()
+    uvc.irradiance_area_mean(sc, cand, lamp, ptri, A=A, with_closed=True)
+    closed_frac = float(uvc.irradiance_area_mean(sc, cand, lamp, ptri, A=A, with_closed=True)[1].float().mean()
+                        .item()) / s.lamp.offsets.shape[0]
+    ms_point = timed(lambda: uvc.irradiance_matrix(sc, cand, lamp, A=A), args.steps, args.warmup)
+    assert uvc.scene_status(sc) == 0
+    pairs = s.nc * s.np_
+    out = {"metric": METRIC, "value": round(pairs / (ms_area * 1e-3) / 1e9, 4), "unit": "Gpairs/s (area mean)",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_area, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "area-mean irradiance, ward-sized room (51k triangles, 102k bisected triangle "
+                                  "patches, K=8 line lamp)", "candidates": s.nc, "patches": s.np_},
+           "area_mean": {"ms": round(ms_area, 3), "gpairs_per_s": round(pairs / (ms_area * 1e-3) / 1e9, 4),
+                         "closed_form_source_fraction": round(closed_frac, 4)},
+           "centroid_sample": {"ms": round(ms_point, 3), "gpairs_per_s": round(pairs / (ms_point * 1e-3) / 1e9, 4)},
+           "area_over_point_time": round(ms_area / ms_point, 3), "clocks": clk}
+    sc.free()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -798,6 +860,8 @@ def main():
         run_batched(args)
     elif args.workload == "learned":
         run_learned(args)
+    elif args.workload == "area":
+        run_area(args)
     else:
         run_ours(args)
 

@@ -169,6 +169,31 @@ int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t n
                             float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream);
 
 /*
+ * uvc_irradiance_area_mean - the patch-mean irradiance instead of the centroid
+ * sample: the flux each patch receives over its area, which is what the
+ * paper's raster estimator measures (Sec. IV-C, mean irradiance = flux /
+ * area).  A point source of power w_m P that sees all of a triangle delivers
+ * w_m P Omega / (4 pi) to it, Omega the triangle's solid angle (van Oosterom
+ * and Strackee, IEEE Trans. Biomed. Eng. 30(2), 1983); so, per source:
+ *   - not facing (<n_j, o - s_j> <= 0) or centroid occluded: 0
+ *   - centroid and every check point unoccluded: w_m P sum_t Omega_t / (4 pi a_j)
+ *     (check points: the patch vertices moved 1e-3 of the way to the centroid,
+ *     fl32(q + fl32(1e-3 * fl32(s_j - q))))
+ *   - otherwise: the centroid sample w_m P <n_j, v> / (4 pi d^3)
+ * The vertex checks are a test of full visibility at 4 (or 7) points, not a
+ * proof: an occluder that covers part of a patch but none of its check points
+ * is missed.
+ *   ptri     float[np][2][3][3] device: each patch as one or two triangles
+ *            (vertices in metres; an unused second triangle is all zero)
+ *   A, lda   as in uvc_irradiance_matrix (a_j is the area given at build)
+ *   nclosed  uint8[nc][np] device or NULL: sources that used the closed form
+ * FP32; a failed search writes NaN and records UVC_E_TIMEOUT/UVC_E_STACK in
+ * the scene status.  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                             const float* ptri, float* A, int64_t lda, uint8_t* nclosed, uvc_stream_t stream);
+
+/*
  * uvc_fluence - fluence of every patch for nvec dwell-time vectors (Eq. (5)):
  *
  *   mu[v][j] = sum_i t[v][i] * A[i][j]

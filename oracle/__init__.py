@@ -47,6 +47,9 @@ def load_library(path: str):
     lib.uvco_irradiance.argtypes = [P, i64, P, i64, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
                                     ctypes.c_double, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
     lib.uvco_irradiance.restype = ctypes.c_int
+    lib.uvco_area_mean.argtypes = [P, i64, P, i64, P, P, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
+                                   ctypes.c_double, ctypes.c_float, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
+    lib.uvco_area_mean.restype = ctypes.c_int
     lib.uvco_max_threads.restype = ctypes.c_int
     return lib
 
@@ -120,6 +123,55 @@ def irradiance(verts, tris, centroid, normal, excl, cand, offsets, weights, powe
     if flag is not None:
         flag = flag.reshape(shape)
     return E, vis, flag
+
+
+PULL = 1e-3   # check points: patch vertices moved this fraction of the way to the centroid
+
+
+def area_mean(verts, tris, centroid, normal, area, excl, ptri, cand, offsets, weights, power, delta=PULL,
+              pairs=None, eps=None, flags=True, threads=0):
+    """FP64 area-mean irradiance (solid-angle closed form where every check
+    segment of a source is unoccluded, centroid sample otherwise), see
+    uvco_area_mean.  Returns (E, nclosed, flag) shaped like irradiance()."""
+    lib = _load()
+    verts = _c(verts, np.float32).reshape(-1, 3)
+    tris = _c(tris, np.int32).reshape(-1, 3)
+    centroid = _c(centroid, np.float32).reshape(-1, 3)
+    normal = _c(normal, np.float32).reshape(-1, 3)
+    area = _c(area, np.float32).reshape(-1)
+    excl = _c(excl, np.int32).reshape(-1, 2)
+    ptri = _c(ptri, np.float32).reshape(-1, 18)
+    cand = _c(cand, np.float32).reshape(-1, 3)
+    offsets = _c(offsets, np.float32).reshape(-1, 3)
+    weights = _c(weights, np.float32).reshape(-1)
+    K = offsets.shape[0]
+    nc, np_ = cand.shape[0], centroid.shape[0]
+    assert ptri.shape[0] == np_ and area.shape[0] == np_
+    if pairs is None:
+        shape, npairs, pp = (nc, np_), nc * np_, None
+    else:
+        pp = _c(pairs, np.int64).reshape(-1, 2)
+        shape, npairs = (pp.shape[0],), pp.shape[0]
+    if eps is None:
+        eps = grazing_eps(verts)
+    E = np.zeros(npairs, np.float64)
+    ncl = np.zeros(npairs, np.uint8)
+    flag = np.zeros(npairs, np.uint8) if flags else None
+    ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    rc = lib.uvco_area_mean(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0], ptr(centroid), ptr(normal),
+                            ptr(area), ptr(excl), ptr(ptri), np_, ptr(cand), nc, ptr(offsets), ptr(weights), K,
+                            float(power), float(delta), ptr(pp), npairs, float(eps), ptr(E), ptr(ncl), ptr(flag),
+                            int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle: invalid input (rc={rc})")
+    return E.reshape(shape), ncl.reshape(shape), None if flag is None else flag.reshape(shape)
+
+
+def area_mean_scene(scene, pairs=None, **kw):
+    """area_mean() on a synth.Scene that carries its patch geometry."""
+    L = scene.lamp
+    return area_mean(scene.verts, scene.tris, scene.centroid, scene.normal, scene.area, scene.excl, scene.ptri,
+                     scene.cand, L.offsets, L.weights, L.power, pairs=pairs, **kw)
 
 
 def irradiance_scene(scene, pairs=None, **kw):

@@ -253,3 +253,146 @@ int uvco_max_threads(void) {
     return 1;
 #endif
 }
+
+/*
+ * Solid angle of triangle (a, b, c) seen from o, by van Oosterom and
+ * Strackee (IEEE Trans. Biomed. Eng. 30(2), 1983):
+ *   tan(Omega / 2) = |R1 . (R2 x R3)| /
+ *                    (r1 r2 r3 + (R1.R2) r3 + (R1.R3) r2 + (R2.R3) r1)
+ * with R_k the vectors from o to the vertices and r_k their lengths; the
+ * numerator is evaluated as R1 . ((b - a) x (c - a)), the same value.
+ */
+static double solid_angle(d3 o, d3 a, d3 b, d3 c) {
+    d3 R1 = vsub(a, o), R2 = vsub(b, o), R3 = vsub(c, o);
+    double r1 = vnorm(R1), r2 = vnorm(R2), r3 = vnorm(R3);
+    double num = fabs(vdot(R1, vcross(vsub(b, a), vsub(c, a))));
+    double den = r1 * r2 * r3 + vdot(R1, R2) * r3 + vdot(R1, R3) * r2 + vdot(R2, R3) * r1;
+    return 2.0 * atan2(num, den);
+}
+
+static int segment_visible(const tri64* T, int64_t nt, int32_t ex0, int32_t ex1, d3 o, d3 p) {
+    d3 dir = vsub(p, o);
+    for (int64_t t = 0; t < nt; ++t) {
+        if (t == ex0 || t == ex1) continue;
+        if (segment_meets_triangle(o, dir, T[t].a, T[t].b, T[t].c)) return 0;
+    }
+    return 1;
+}
+
+static int segment_grazing(const tri64* T, int64_t nt, int32_t ex0, int32_t ex1, d3 o, d3 p, double eps) {
+    int bits = 0;
+    for (int64_t t = 0; t < nt; ++t) {
+        if (t == ex0 || t == ex1) continue;
+        bits |= grazing_bits(&T[t], o, p, eps);
+    }
+    return bits;
+}
+
+/*
+ * Area-mean irradiance of patches with known geometry (the mean of Eq. (4)
+ * over the patch instead of its centroid sample): the flux a triangle
+ * receives from an isotropic point source of power P that sees all of it is
+ * P Omega / (4 pi), Omega its solid angle (the integral of cos / d^2 over
+ * the triangle), so the patch's mean irradiance is P sum_t Omega_t / (4 pi a_j).
+ *
+ * Per candidate i, source m, patch j with triangles ptri[j][0..1] (the second
+ * unused when its area is zero):
+ *   o        = fl32(c_i + off_m)
+ *   facing   <n_j, o - s_j> > 0 (centroid s_j)
+ *   checks   the open segments from o to s_j and to each vertex q pulled
+ *            towards the centroid, q' = fl32(q + fl32(delta * fl32(s_j - q)))
+ *            (single-precision operations, no contraction)
+ *   all visible      E += w_m P sum_t Omega_t(o) / (4 pi a_j)     (closed form)
+ *   centroid visible E += w_m P <n_j, v> / (4 pi d^3)             (point sample)
+ *   nclosed_out[k]   number of sources that used the closed form
+ *   flag_out[k]      grazing bits (as above) OR-ed over every check segment
+ *                    of the facing sources
+ * Returns 0, or -1 on an index out of range.
+ */
+int uvco_area_mean(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                   const float* centroid, const float* normal, const float* area, const int32_t* excl,
+                   const float* ptri, int64_t np, const float* cand, int64_t nc,
+                   const float* offsets, const float* weights, int32_t K, double power, float delta,
+                   const int64_t* pairs, int64_t npairs, double eps,
+                   double* E_out, uint8_t* nclosed_out, uint8_t* flag_out, int nthreads) {
+    if (K < 1 || nt < 0 || np < 0 || nc < 0) return -1;
+    if (pairs == NULL) npairs = nc * np;
+    for (int64_t j = 0; j < np; ++j)
+        for (int q = 0; q < 2; ++q)
+            if (excl[2 * j + q] < -1 || excl[2 * j + q] >= nt) return -1;
+    if (pairs != NULL)
+        for (int64_t k = 0; k < npairs; ++k)
+            if (pairs[2 * k] < 0 || pairs[2 * k] >= nc || pairs[2 * k + 1] < 0 || pairs[2 * k + 1] >= np)
+                return -1;
+    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
+    if (!T) return -2;
+    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
+    const double four_pi = 4.0 * M_PI;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 8)
+#endif
+    for (int64_t k = 0; k < npairs; ++k) {
+        int64_t i = pairs ? pairs[2 * k] : k / np;
+        int64_t j = pairs ? pairs[2 * k + 1] : k % np;
+        const float* sf = centroid + 3 * j;
+        d3 s = v3(sf[0], sf[1], sf[2]);
+        d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
+        int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
+        /* the patch triangles and the pulled-in check points */
+        d3 tv[2][3];
+        int ntri = 0;
+        d3 chk[6];
+        int nchk = 0;
+        for (int t = 0; t < 2; ++t) {
+            const float* g = ptri + 18 * j + 9 * t;
+            for (int q = 0; q < 3; ++q) tv[t][q] = v3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+            d3 cr = vcross(vsub(tv[t][1], tv[t][0]), vsub(tv[t][2], tv[t][0]));
+            if (vdot(cr, cr) == 0.0) continue;
+            if (t != ntri)
+                for (int q = 0; q < 3; ++q) tv[ntri][q] = tv[t][q];
+            for (int q = 0; q < 3; ++q) {
+                const float* gq = g + 3 * q;
+                float px = gq[0] + delta * (sf[0] - gq[0]);
+                float py = gq[1] + delta * (sf[1] - gq[1]);
+                float pz = gq[2] + delta * (sf[2] - gq[2]);
+                chk[nchk++] = v3(px, py, pz);
+            }
+            ++ntri;
+        }
+        double E = 0.0;
+        int flags = 0, nclosed = 0;
+        for (int m = 0; m < K; ++m) {
+            float ox = cand[3 * i] + offsets[3 * m];
+            float oy = cand[3 * i + 1] + offsets[3 * m + 1];
+            float oz = cand[3 * i + 2] + offsets[3 * m + 2];
+            d3 o = v3(ox, oy, oz);
+            d3 v = vsub(o, s);
+            double d = vnorm(v);
+            double nv_ = vdot(n, v);
+            if (flag_out && fabs(nv_) <= eps) flags |= 4;
+            if (!(nv_ > 0.0 && d > 0.0)) continue;
+            int vis_c = segment_visible(T, nt, ex0, ex1, o, s);
+            if (flag_out) flags |= segment_grazing(T, nt, ex0, ex1, o, s, eps);
+            int all = vis_c && ntri > 0;
+            for (int q = 0; q < nchk; ++q) {
+                if (all && !segment_visible(T, nt, ex0, ex1, o, chk[q])) all = 0;
+                if (flag_out && vis_c) flags |= segment_grazing(T, nt, ex0, ex1, o, chk[q], eps);
+            }
+            double pw = (double)weights[m] * power;
+            if (all) {
+                double om = 0.0;
+                for (int t = 0; t < ntri; ++t) om += solid_angle(o, tv[t][0], tv[t][1], tv[t][2]);
+                E += pw * om / (four_pi * (double)area[j]);
+                ++nclosed;
+            } else if (vis_c) {
+                E += pw * nv_ / (four_pi * d * d * d);
+            }
+        }
+        E_out[k] = E;
+        if (nclosed_out) nclosed_out[k] = (uint8_t)nclosed;
+        if (flag_out) flag_out[k] = (uint8_t)flags;
+    }
+    free(T);
+    return 0;
+}

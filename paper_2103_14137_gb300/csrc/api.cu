@@ -98,6 +98,17 @@ int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t n
                                     (cudaStream_t)stream);
 }
 
+int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
+                             const float* ptri, float* A, int64_t lda, uint8_t* nclosed, uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (lda < scene->np) return UVC_E_INVAL;
+    if (nc > 0 && scene->np > 0 && (!cand || !A || !ptri)) return UVC_E_INVAL;
+    return uvc::irradiance_area_mean(scene, cand, nc, L, ptri, A, lda, nclosed, (cudaStream_t)stream);
+}
+
 int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
                 float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256 || lda < scene->np) return UVC_E_INVAL;

@@ -90,6 +90,10 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
 int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* t,
                              int32_t nvec, float* mu, cudaStream_t stream);
 
+// area-mean irradiance (solid_angle.cu)
+int irradiance_area_mean(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* ptri,
+                         float* A, int64_t lda, uint8_t* nclosed, cudaStream_t stream);
+
 // fluence and coverage (fluence.cu)
 int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
             float* mu, cudaStream_t stream);

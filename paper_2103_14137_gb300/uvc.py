@@ -64,6 +64,7 @@ def library():
         "uvc_free_scene": [P],
         "uvc_irradiance_matrix": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence": [P, P, i64, i64, P, i32, P, P],
+        "uvc_irradiance_area_mean": [P, P, i64, ctypes.POINTER(_Lamp), P, P, i64, P, P],
         "uvc_irradiance_counters": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence_streamed": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
         "uvc_fluence_streamed_noalloc": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
@@ -252,6 +253,24 @@ def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> 
                                            ctypes.c_void_p(out.ctypes.data), _stream(stream))
     _check(rc, "uvc_irradiance_counters")
     return dict(zip(COUNTER_NAMES, (int(x) for x in out)))
+
+
+def irradiance_area_mean(scene: Scene, cand, lamp: Lamp, ptri, A=None, with_closed=False, stream=None):
+    """Patch-mean irradiance (nc, np): solid-angle closed form for sources that
+    see every check point of a patch, centroid sample otherwise.  ptri is the
+    (np, 2, 3, 3) float32 patch geometry.  Returns (A, nclosed or None)."""
+    nc = cand.shape[0]
+    if A is None:
+        A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
+    ncl = torch.empty((nc, scene.np), dtype=torch.uint8, device=cand.device) if with_closed else None
+    L = lamp._c()
+    rc = library().uvc_irradiance_area_mean(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
+                                            ctypes.byref(L), _dev(ptri, torch.float32, "ptri", (scene.np, 2, 3, 3)),
+                                            _dev(A, torch.float32, "A"), A.shape[1] if A.dim() == 2 else 0,
+                                            None if ncl is None else _dev(ncl, torch.uint8, "nclosed"),
+                                            _stream(stream))
+    _check(rc, "uvc_irradiance_area_mean")
+    return A, ncl
 
 
 def fluence(scene: Scene, A, t, mu=None, stream=None):

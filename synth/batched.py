@@ -61,16 +61,17 @@ def batched_room(seed: int) -> Scene:
     verts, tris, tnrm, tcell = mb.finish()
     nt = tris.shape[0]
     if np_t >= nt:
-        cen, nrm, ar, excl = patches_bisected(verts, tris, tnrm, float(area) / np_t)
+        cen, nrm, ar, excl, ptri = patches_bisected(verts, tris, tnrm, float(area) / np_t, with_tris=True)
     elif np_t >= nt // 2:
-        cen, nrm, ar, excl = patches_per_triangle(verts, tris, tnrm)
+        cen, nrm, ar, excl, ptri = patches_per_triangle(verts, tris, tnrm, with_tris=True)
     else:
-        cen, nrm, ar, excl = patches_quads(verts, tris, tnrm, tcell)
+        cen, nrm, ar, excl, ptri = patches_quads(verts, tris, tnrm, tcell, with_tris=True)
     if cen.shape[0] > np_t:        # seeded subset, kept in spatial order
         keep = np.sort(rng.choice(cen.shape[0], size=np_t, replace=False))
-        cen, nrm, ar, excl = cen[keep], nrm[keep], ar[keep], excl[keep]
+        cen, nrm, ar, excl, ptri = cen[keep], nrm[keep], ar[keep], excl[keep], ptri[keep]
     s = _finish(f"batch{seed}", verts, tris, cen, nrm, ar, excl, np.zeros((0, 3)), None,
-                {"seed": seed, "room": [W, D, H], "boxes": len(boxes), "cell": h, "targets": [nt_t, np_t, nc_t]})
+                {"seed": seed, "room": [W, D, H], "boxes": len(boxes), "cell": h, "targets": [nt_t, np_t, nc_t]},
+                ptri)
     s.info["box_list"] = boxes
     return s
 

@@ -58,6 +58,7 @@ class Scene:
     cand: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))
     lamp: Lamp | None = None
     info: dict = field(default_factory=dict)
+    ptri: np.ndarray | None = None   # (np, 2, 3, 3) patch geometry: one or two triangles (second all zero if unused)
 
     @property
     def nt(self):
@@ -87,27 +88,40 @@ def _tri_geom(verts64, tris):
     return a, b, c, area
 
 
-def patches_per_triangle(verts, tris, tri_normal):
-    """One patch per triangle: its centroid, area and free-side normal."""
+def _ptri(a, b, c, a2=None, b2=None, c2=None):
+    out = np.zeros((a.shape[0], 2, 3, 3), np.float32)
+    out[:, 0, 0], out[:, 0, 1], out[:, 0, 2] = a, b, c
+    if a2 is not None:
+        out[:, 1, 0], out[:, 1, 1], out[:, 1, 2] = a2, b2, c2
+    return out
+
+
+def patches_per_triangle(verts, tris, tri_normal, with_tris=False):
+    """One patch per triangle: its centroid, area and free-side normal (and,
+    with_tris, the patch geometry (np, 2, 3, 3))."""
     v = verts.astype(np.float64)
     a, b, c, area = _tri_geom(v, tris)
     cen = (a + b + c) / 3.0
     excl = np.stack([np.arange(tris.shape[0]), -np.ones(tris.shape[0], np.int64)], axis=1)
+    if with_tris:
+        return cen, tri_normal, area, excl, _ptri(a, b, c)
     return cen, tri_normal, area, excl
 
 
-def patches_bisected(verts, tris, tri_normal, amax):
+def patches_bisected(verts, tris, tri_normal, amax, with_tris=False):
     """Split every triangle at the midpoint of its longest edge until each piece
     has area <= amax; each piece is a patch whose parent triangle is excluded."""
     v = verts.astype(np.float64)
     a, b, c, area = _tri_geom(v, tris)
     parent = np.arange(tris.shape[0])
-    done_c, done_a, done_p = [], [], []
+    done_c, done_a, done_p, done_t = [], [], [], []
     while a.shape[0]:
         small = area <= amax
         done_c.append((a[small] + b[small] + c[small]) / 3.0)
         done_a.append(area[small])
         done_p.append(parent[small])
+        if with_tris:
+            done_t.append(_ptri(a[small], b[small], c[small]))
         a, b, c, parent, area = a[~small], b[~small], c[~small], parent[~small], area[~small]
         if not a.shape[0]:
             break
@@ -132,10 +146,12 @@ def patches_bisected(verts, tris, tri_normal, amax):
     order = np.lexsort((np.arange(par.size), par))   # keep triangle order (spatial)
     cen, ar, par = cen[order], ar[order], par[order]
     excl = np.stack([par, -np.ones(par.size, np.int64)], axis=1)
+    if with_tris:
+        return cen, tri_normal[par], ar, excl, np.concatenate(done_t)[order]
     return cen, tri_normal[par], ar, excl
 
 
-def patches_quads(verts, tris, tri_normal, tri_cell):
+def patches_quads(verts, tris, tri_normal, tri_cell, with_tris=False):
     """One patch per cell (a quad made of two consecutive triangles): the area
     centroid of the quad; both triangles are excluded."""
     assert tris.shape[0] % 2 == 0 and np.all(tri_cell[0::2] == tri_cell[1::2])
@@ -146,11 +162,14 @@ def patches_quads(verts, tris, tri_normal, tri_cell):
     cen = (g[0::2] * w0[:, None] + g[1::2] * w1[:, None]) / (w0 + w1)[:, None]
     idx = np.arange(0, tris.shape[0], 2)
     excl = np.stack([idx, idx + 1], axis=1)
+    if with_tris:
+        return cen, tri_normal[0::2], w0 + w1, excl, _ptri(a[0::2], b[0::2], c[0::2], a[1::2], b[1::2], c[1::2])
     return cen, tri_normal[0::2], w0 + w1, excl
 
 
-def _finish(name, verts, tris, cen, nrm, area, excl, cand, lamp, info):
+def _finish(name, verts, tris, cen, nrm, area, excl, cand, lamp, info, ptri=None):
     return Scene(
+        ptri=None if ptri is None else np.ascontiguousarray(ptri, np.float32),
         name=name,
         verts=np.ascontiguousarray(verts, np.float32),
         tris=np.ascontiguousarray(tris, np.int32),
@@ -203,13 +222,13 @@ def tiny_room(seed: int = 0, n_cand: int = 200) -> Scene:
     table = (np.array([tx, ty, 0.0]), np.array([tx + 1.0, ty + 0.6, 0.75]))
     mb.add(mesh_box(table[0], table[1], 0.42, free_side="out", omit=((2, 0),), jitter=0.01, rng=rng))
     verts, tris, tnrm, tcell = mb.finish()
-    cen, nrm, area, excl = patches_per_triangle(verts, tris, tnrm)
+    cen, nrm, area, excl, ptri = patches_per_triangle(verts, tris, tnrm, with_tris=True)
     xy = _grid_xy(W, D, 0.25, 0.25)
     ok = _clear_of(xy, 1.0, 1.0, [table], 0.1)
     xy = xy[ok][:n_cand]
     cand = np.concatenate([xy, np.full((xy.shape[0], 1), 1.0)], axis=1)
     return _finish("tiny", verts, tris, cen, nrm, area, excl, cand, point_lamp(80.0),
-                   {"seed": seed, "room": [W, D, H]})
+                   {"seed": seed, "room": [W, D, H]}, ptri)
 
 
 def ward_room(seed: int = 1, n_cand: int = 2000, h: float = 0.1165, amax: float = 0.005,
@@ -244,7 +263,7 @@ def ward_room(seed: int = 1, n_cand: int = 2000, h: float = 0.1165, amax: float 
     for lo, hi in boxes:
         mb.add(mesh_box(lo, hi, h, free_side="out", omit=((2, 0),), jitter=0.01, rng=rng))
     verts, tris, tnrm, tcell = mb.finish()
-    cen, nrm, area, excl = patches_bisected(verts, tris, tnrm, amax)
+    cen, nrm, area, excl, ptri = patches_bisected(verts, tris, tnrm, amax, with_tris=True)
     cands = []
     xy = _grid_xy(W, D, 0.2, 0.2)
     for zb in (0.5, 1.0, 1.5):
@@ -254,7 +273,7 @@ def ward_room(seed: int = 1, n_cand: int = 2000, h: float = 0.1165, amax: float 
     pick = np.sort(rng.choice(cands.shape[0], size=min(n_cand, cands.shape[0]), replace=False))
     lamp = line_lamp(lamp_len, K, power)
     return _finish("ward", verts, tris, cen, nrm, area, excl, cands[pick], lamp,
-                   {"seed": seed, "room": [W, D, H], "boxes": len(boxes), "cell": h, "amax": amax})
+                   {"seed": seed, "room": [W, D, H], "boxes": len(boxes), "cell": h, "amax": amax}, ptri)
 
 
 def large_floor(seed: int = 3, n_cand: int = 10000, h: float = 0.0638, K: int = 8,

@@ -1,0 +1,111 @@
+"""Pins of the area-mean oracle: solid angles with known closed forms, dense
+quadrature of cos/d^2 over a triangle, the hybrid's fallback to the centroid
+sample when a check segment is blocked, the facing rule, and convergence of
+the closed form to the centroid sample as the patch shrinks."""
+import math
+
+import numpy as np
+
+import oracle
+
+
+def one_patch(tri_list, normal, area, occluders=(), source=(0.0, 0.0, 0.0), power=1.0):
+    """A scene holding the patch's own triangles (excluded) plus occluders."""
+    tris = [np.asarray(t, np.float64) for t in tri_list] + [np.asarray(t, np.float64) for t in occluders]
+    verts = np.concatenate(tris).astype(np.float32)
+    T = np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3)
+    ptri = np.zeros((1, 2, 3, 3), np.float32)
+    for k, t in enumerate(tri_list):
+        ptri[0, k] = t
+    w = np.array([0.5 * np.linalg.norm(np.cross(t[1] - t[0], t[2] - t[0])) for t in tris[:len(tri_list)]])
+    cen = sum(wk * tk.mean(0) for wk, tk in zip(w, tris)) / w.sum()
+    excl = np.array([[0, 1 if len(tri_list) == 2 else -1]], np.int32)
+    E, ncl, _ = oracle.area_mean(verts, T, cen[None], np.asarray(normal, np.float32)[None], [area], excl, ptri,
+                                 np.asarray(source, np.float32)[None], [[0.0, 0.0, 0.0]], [1.0], power, flags=False)
+    return float(E[0, 0]), int(ncl[0, 0]), cen
+
+
+def test_octant_triangle_subtends_an_eighth_of_the_sphere():
+    t = np.eye(3)
+    area = float(np.float32(math.sqrt(3) / 2))              # the area as the library stores it
+    E, ncl, _ = one_patch([t], -np.ones(3) / math.sqrt(3), area)
+    # Omega = 4 pi / 8: flux P / 8 over the area
+    assert ncl == 1 and math.isclose(E, (1 / 8) / area, rel_tol=1e-12)
+
+
+def square(a, z=0.0):
+    h = a / 2
+    p = np.array([[-h, -h, z], [h, -h, z], [h, h, z], [-h, h, z]])
+    return [p[[0, 1, 2]], p[[0, 2, 3]]]
+
+
+def test_square_on_axis():
+    for a, h in ((2.0, 1.0), (0.5, 3.0), (3.0, 0.25)):            # all exact in binary32
+        E, ncl, _ = one_patch(square(a), [0, 0, 1], a * a, source=(0, 0, h), power=7.0)
+        omega = 4 * math.asin(a * a / (a * a + 4 * h * h))
+        assert ncl == 1 and math.isclose(E, 7.0 * omega / (4 * math.pi * a * a), rel_tol=1e-9)
+
+
+def subdivide(t, levels):
+    tris = [np.asarray(t, np.float64)]
+    for _ in range(levels):
+        nxt = []
+        for a, b, c in tris:
+            ab, bc, ca = (a + b) / 2, (b + c) / 2, (c + a) / 2
+            nxt += [np.array([a, ab, ca]), np.array([ab, b, bc]), np.array([ca, bc, c]), np.array([ab, bc, ca])]
+        tris = nxt
+    return np.array(tris)
+
+
+def test_closed_form_equals_dense_quadrature():
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        t = rng.uniform(-1, 1, (3, 3))
+        n = np.cross(t[1] - t[0], t[2] - t[0])
+        area = 0.5 * np.linalg.norm(n)
+        n /= np.linalg.norm(n)
+        src = t.mean(0) + n * rng.uniform(0.8, 2.0) + rng.uniform(-0.3, 0.3, 3)
+        t32 = t.astype(np.float32).astype(np.float64)
+        src32 = src.astype(np.float32).astype(np.float64)
+        E, ncl, _ = one_patch([t32], n, area, source=src32, power=1.0)
+        n32 = np.cross(t32[1] - t32[0], t32[2] - t32[0])
+        n32 /= np.linalg.norm(n32)
+
+        def quad(levels):                                    # centroid rule on 4^levels pieces
+            sub = subdivide(t32, levels)
+            g = sub.mean(1)
+            w = 0.5 * np.linalg.norm(np.cross(sub[:, 1] - sub[:, 0], sub[:, 2] - sub[:, 0]), axis=1)
+            v = src32 - g
+            d = np.linalg.norm(v, axis=1)
+            return np.sum(w * (v @ n32) / (4 * math.pi * d ** 3)), w.sum()
+        (q6, wsum), (q7, _) = quad(6), quad(7)
+        flux = q7 + (q7 - q6) / 3                            # Richardson: the rule's error is O(h^2)
+        A32 = float(np.float32(area))
+        assert ncl == 1 and math.isclose(E * A32, flux, rel_tol=1e-6), (E * A32, flux, q6, q7)
+
+
+def test_blocked_vertex_falls_back_to_the_centroid_sample():
+    occ = np.array([[0.4, 0.4, 1.0], [0.6, 0.4, 1.0], [0.5, 0.6, 1.0]])   # on the way to vertex (1, 1, 0) only
+    E, ncl, _ = one_patch(square(2.0), [0, 0, 1], 4.0, occluders=[occ], source=(0, 0, 2), power=3.0)
+    assert ncl == 0 and math.isclose(E, 3.0 / (4 * math.pi * 4.0), rel_tol=1e-12)
+    # the same occluder moved off the check segments changes nothing
+    E2, ncl2, _ = one_patch(square(2.0), [0, 0, 1], 4.0, occluders=[occ + [0, 0, 5.0]], source=(0, 0, 2), power=3.0)
+    omega = 4 * math.asin(4.0 / (4.0 + 16.0))
+    assert ncl2 == 1 and math.isclose(E2, 3.0 * omega / (4 * math.pi * 4.0), rel_tol=1e-9)
+
+
+def test_source_behind_the_patch_gives_zero():
+    E, ncl, _ = one_patch(square(1.0), [0, 0, 1], 1.0, source=(0.1, 0.2, -1.0))
+    assert E == 0.0 and ncl == 0
+
+
+def test_closed_form_tends_to_the_centroid_sample():
+    errs = []
+    for a in (0.4, 0.2, 0.1, 0.05):
+        E, _, _ = one_patch(square(a), [0, 0, 1], a * a, source=(0.3, 0.1, 1.0))
+        v = np.array([0.3, 0.1, 1.0])
+        point = v[2] / (4 * math.pi * np.linalg.norm(v) ** 3)
+        errs.append(abs(E / point - 1))
+    # second-order convergence: halving the patch divides the error by ~4
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 3.0 < e0 / e1 < 5.0, errs
