@@ -51,7 +51,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned", "area"], default="ward")
+    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned", "area", "raster"],
+                   default="ward")
+    p.add_argument("--resolution", type=int, default=512, help="raster workload: cube face resolution R")
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
@@ -852,6 +854,66 @@ def run_area(args):
     print(json.dumps(out), flush=True)
 
 
+def run_raster(args):
+    """The paper's own estimator (visibility cube, uvc_irradiance_raster) at
+    its configuration (R = 512 per face) on the ward room: per candidate one
+    column of mean irradiances over all triangles, K = 8 cubes per candidate.
+    Metric: ms per column (the paper states "milliseconds") and the
+    (candidate, triangle) pair rate.  Default: the first 64 candidates."""
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    from synth import ward_room
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    s = ward_room(seed=1 + 1000 * rank)
+    nc = args.candidates or 64
+    cand_h = s.cand[:nc]
+    Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    # per-triangle normals: the ward's patches are pieces of triangles (parent in excl[:, 0])
+    tnrm = np.zeros((s.nt, 3), np.float32)
+    tnrm[s.excl[:, 0]] = s.normal
+    sc = uvc.build_scene(Td(s.verts), Td(s.tris), Td(s.centroid), Td(s.normal), Td(s.area), Td(s.excl))
+    lamp = uvc.Lamp(s.lamp.offsets, s.lamp.weights, s.lamp.power)
+    cand, nrm = Td(cand_h), Td(tnrm)
+    R = args.resolution
+    per_batch = 4
+    ws = uvc.raster_workspace(sc, lamp, R, per_batch, dev)
+    A = torch.empty((nc, s.nt), dtype=torch.float32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    for _ in range(max(1, args.warmup)):
+        uvc.irradiance_raster(sc, nrm, cand[:per_batch], lamp, R=R, A=A[:per_batch], workspace=ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    a, b = ev(), ev()
+    a.record()
+    uvc.irradiance_raster(sc, nrm, cand, lamp, R=R, A=A, workspace=ws)
+    b.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = a.elapsed_time(b)
+    areas = torch.from_numpy(0.5 * np.linalg.norm(np.cross(
+        s.verts[s.tris[:, 1]].astype(np.float64) - s.verts[s.tris[:, 0]],
+        s.verts[s.tris[:, 2]].astype(np.float64) - s.verts[s.tris[:, 0]]), axis=1)).to(dev)
+    flux = (A.double() * areas[None, :]).sum(1)
+    out = {"metric": METRIC, "value": round(ms / nc, 4), "unit": "ms per irradiance column (visibility cube)",
+           "n_gpus": 1, "steps": 1, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (flux in 2^-40 W fixed point)", "data": "synthetic",
+           "config": {"workload": f"visibility-cube estimator, ward-sized room (51k triangles), R = {R} per face, "
+                                  f"K = 8 cubes per candidate, {nc} candidates", "resolution": R, "candidates": nc,
+                      "triangles": s.nt, "cubes": nc * 8},
+           "pairs_per_s": round(nc * s.nt / (ms * 1e-3), 1),
+           "absorbed_flux_fraction_mean": round(float(flux.mean().item()) / s.lamp.power, 6),
+           "paper_context": "the paper states milliseconds per column at 512x512 (unnamed GPU, OpenGL)",
+           "clocks": clk}
+    sc.free()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -862,6 +924,8 @@ def main():
         run_learned(args)
     elif args.workload == "area":
         run_area(args)
+    elif args.workload == "raster":
+        run_raster(args)
     else:
         run_ours(args)
 

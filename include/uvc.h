@@ -194,6 +194,36 @@ int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t 
                              const float* ptri, float* A, int64_t lda, uint8_t* nclosed, uvc_stream_t stream);
 
 /*
+ * uvc_irradiance_raster - the paper's own estimator (Sec. IV-C, Fig. 2): per
+ * source point a visibility cube of six R x R faces (the paper uses R = 512)
+ * holding the nearest triangle seen through each pixel centre (depth test);
+ * each pixel's power w_m P Omega_pixel / (4 pi) (the precomputed emission
+ * table E) is added to that triangle's flux when the pixel ray meets the
+ * triangle's front side (<dir, n_t> < 0) and is absorbed otherwise; the mean
+ * irradiance of triangle t is its flux over its area, A[i][t] = F_it / |s_t|
+ * (per triangle, not per patch).
+ * Cube layout: face f looks along axis a = f / 2 (sign + for even f); pixel
+ * (px, py) is the direction with component a = +-1, component (a+1) % 3 =
+ * fl32(fl32(2 px + 1) / R) - 1 and component (a+2) % 3 likewise from py, and
+ * covers the solid angle of its square on the unit-distance plane.
+ *   tri_normal  float[nt][3] device, the front (free) side of each triangle,
+ *               by the triangle's index in the build's `tris`
+ *   A           float[nc][lda] device, lda >= nt, columns by triangle index
+ *   workspace   device scratch; uvc_raster_workspace_bytes(scene, lamp, R, b)
+ *               bytes hold batches of b candidates (more bytes, larger
+ *               batches; less than b = 1 needs is UVC_E_INVAL)
+ * A software rasteriser (setup, prefix-sum balanced fragments, watertight
+ * pixel-centre ray tests with a 64-bit atomicMin of (depth, id)); the flux is
+ * summed in 2^-40 W fixed point, so results do not depend on thread order.
+ * R in [1, 4096].  Enqueued on `stream` (the table copy is synchronous with
+ * the host).  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+size_t uvc_raster_workspace_bytes(const uvc_scene* scene, const uvc_lamp* lamp, int32_t R, int64_t cand_per_batch);
+int uvc_irradiance_raster(const uvc_scene* scene, const float* tri_normal, const float* cand, int64_t nc,
+                          const uvc_lamp* lamp, int32_t R, float* A, int64_t lda, void* workspace, size_t bytes,
+                          uvc_stream_t stream);
+
+/*
  * uvc_fluence - fluence of every patch for nvec dwell-time vectors (Eq. (5)):
  *
  *   mu[v][j] = sum_i t[v][i] * A[i][j]

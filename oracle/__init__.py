@@ -50,6 +50,9 @@ def load_library(path: str):
     lib.uvco_area_mean.argtypes = [P, i64, P, i64, P, P, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_float, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
     lib.uvco_area_mean.restype = ctypes.c_int
+    lib.uvco_raster.argtypes = [P, i64, P, i64, P, P, i64, P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
+                                ctypes.c_double, P, P, ctypes.c_int]
+    lib.uvco_raster.restype = ctypes.c_int
     lib.uvco_max_threads.restype = ctypes.c_int
     return lib
 
@@ -172,6 +175,39 @@ def area_mean_scene(scene, pairs=None, **kw):
     L = scene.lamp
     return area_mean(scene.verts, scene.tris, scene.centroid, scene.normal, scene.area, scene.excl, scene.ptri,
                      scene.cand, L.offsets, L.weights, L.power, pairs=pairs, **kw)
+
+
+def raster(verts, tris, tri_normal, cand, offsets, weights, power, R, rel=1e-5, ambiguity=True, threads=0):
+    """FP64 visibility-cube estimator by ray casting through the pixel centres
+    (uvco_raster): per candidate and triangle the flux F (W) and the bound amb
+    on the flux an FP32 rasteriser may legitimately move (or None)."""
+    lib = _load()
+    verts = _c(verts, np.float32).reshape(-1, 3)
+    tris = _c(tris, np.int32).reshape(-1, 3)
+    tri_normal = _c(tri_normal, np.float32).reshape(-1, 3)
+    cand = _c(cand, np.float32).reshape(-1, 3)
+    offsets = _c(offsets, np.float32).reshape(-1, 3)
+    weights = _c(weights, np.float32).reshape(-1)
+    nc, nt = cand.shape[0], tris.shape[0]
+    F = np.zeros((nc, nt), np.float64)
+    amb = np.zeros((nc, nt), np.float64) if ambiguity else None
+    ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+    rc = lib.uvco_raster(ptr(verts), verts.shape[0], ptr(tris), nt, ptr(tri_normal), ptr(cand), nc, ptr(offsets),
+                         ptr(weights), offsets.shape[0], float(power), int(R), float(rel), ptr(F), ptr(amb),
+                         int(threads))
+    if rc != 0:
+        raise ValueError(f"oracle: invalid input (rc={rc})")
+    return F, amb
+
+
+def pixel_solid_angles(R):
+    """(R, R) solid angles of one cube face's pixels (FP64, the closed form
+    used by uvco_raster), indexed [py, px]."""
+    e = 2.0 * np.arange(R + 1) / R - 1.0
+    G = lambda u, v: np.arctan(u * v / np.sqrt(1.0 + u * u + v * v))  # noqa: E731
+    U, V = np.meshgrid(e, e, indexing="xy")
+    g = G(U, V)
+    return g[1:, 1:] - g[1:, :-1] - g[:-1, 1:] + g[:-1, :-1]
 
 
 def irradiance_scene(scene, pairs=None, **kw):

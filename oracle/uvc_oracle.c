@@ -396,3 +396,135 @@ int uvco_area_mean(const float* verts, int64_t nv, const int32_t* tris, int64_t 
     free(T);
     return 0;
 }
+
+/*
+ * Visibility-cube estimator of the paper (Sec. IV-C, Fig. 2), by ray casting
+ * through every pixel centre instead of rasterising.  Around each source point
+ * o a cube of six R x R faces; face f looks along axis a = f / 2 with sign
+ * s = +1 for even f, -1 for odd f; its pixel (px, py) is the direction
+ *   dir[a] = s,  dir[(a+1) % 3] = u,  dir[(a+2) % 3] = v,
+ *   u = fl32(fl32(2 px + 1) / R) - 1,  v = fl32(fl32(2 py + 1) / R) - 1
+ * (single-precision operations, as the library forms them) and covers the
+ * solid angle of the square [2px/R - 1, 2(px+1)/R - 1] x [2py/R - 1, ...] of
+ * the plane at unit distance, Omega = G(u1,v1) - G(u0,v1) - G(u1,v0) + G(u0,v0)
+ * with G(u, v) = atan(u v / sqrt(1 + u^2 + v^2)).  T = the nearest triangle
+ * met by the ray o + t dir, t > 0; the pixel's power w_m P Omega / (4 pi)
+ * goes to T when the ray meets T's front side (<dir, n_T> < 0) and is
+ * absorbed otherwise.  F_out[i][t] sums it over the sources of candidate i
+ * (flux, W); the mean irradiance is F / |s_t|.
+ *
+ * amb_out[i][t] bounds how much flux an FP32 implementation may legitimately
+ * move to or from triangle t: a pixel whose ray passes within rel * t of the
+ * boundary of a triangle not behind the nearest robust hit, or whose nearest
+ * triangle is met within rel of edge-on, adds its power to every triangle
+ * that could receive it.
+ */
+static double pixel_G(double u, double v) { return atan(u * v / sqrt(1.0 + u * u + v * v)); }
+
+int uvco_raster(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const float* tri_normal,
+                const float* cand, int64_t nc, const float* offsets, const float* weights, int32_t K, double power,
+                int32_t R, double rel, double* F_out, double* amb_out, int nthreads) {
+    if (K < 1 || nt < 0 || nc < 0 || R < 1) return -1;
+    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
+    if (!T) return -2;
+    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
+    for (int64_t k = 0; k < nc * nt; ++k) { F_out[k] = 0.0; if (amb_out) amb_out[k] = 0.0; }
+    const int64_t npix = 6 * (int64_t)R * R;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int64_t i = 0; i < nc; ++i)
+        for (int m = 0; m < K; ++m) {
+            float ox = cand[3 * i] + offsets[3 * m];
+            float oy = cand[3 * i + 1] + offsets[3 * m + 1];
+            float oz = cand[3 * i + 2] + offsets[3 * m + 2];
+            d3 o = v3(ox, oy, oz);
+            double pw = (double)weights[m] * power / (4.0 * M_PI);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64)
+#endif
+            for (int64_t q = 0; q < npix; ++q) {
+                int f = (int)(q / ((int64_t)R * R));
+                int px = (int)(q % ((int64_t)R * R)) % R, py = (int)(q % ((int64_t)R * R)) / R;
+                int a = f / 2;
+                double s = (f % 2 == 0) ? 1.0 : -1.0;
+                float uf = (float)(2 * px + 1) / (float)R - 1.0f;
+                float vf = (float)(2 * py + 1) / (float)R - 1.0f;
+                double dd[3];
+                dd[a] = s; dd[(a + 1) % 3] = uf; dd[(a + 2) % 3] = vf;
+                d3 dir = v3(dd[0], dd[1], dd[2]);
+                double dl = vnorm(dir);
+                double u0 = 2.0 * px / R - 1.0, u1 = 2.0 * (px + 1) / R - 1.0;
+                double v0 = 2.0 * py / R - 1.0, v1 = 2.0 * (py + 1) / R - 1.0;
+                double e = pw * (pixel_G(u1, v1) - pixel_G(u0, v1) - pixel_G(u1, v0) + pixel_G(u0, v0));
+                /* nearest hit, nearest robust hit, and the near candidates */
+                int64_t best = -1;
+                double tbest = INFINITY, trob = INFINITY;
+                for (int64_t t = 0; t < nt; ++t) {
+                    d3 e1 = vsub(T[t].b, T[t].a), e2 = vsub(T[t].c, T[t].a);
+                    d3 p = vcross(dir, e2);
+                    double det = vdot(e1, p);
+                    if (det == 0.0) continue;
+                    d3 r = vsub(o, T[t].a);
+                    double uu = vdot(r, p) / det;
+                    d3 qq = vcross(r, e1);
+                    double ww = vdot(dir, qq) / det;
+                    double tt = vdot(e2, qq) / det;
+                    if (!(tt > 0.0)) continue;
+                    int inside = uu >= 0.0 && ww >= 0.0 && uu + ww <= 1.0;
+                    if (inside && tt < tbest) { tbest = tt; best = t; }
+                    if (inside) {
+                        d3 h = vadd(o, vmul(dir, tt));
+                        double sd = fmin(point_segment_distance(h, T[t].a, T[t].b),
+                                         fmin(point_segment_distance(h, T[t].b, T[t].c),
+                                              point_segment_distance(h, T[t].c, T[t].a)));
+                        if (sd > rel * tt * dl && tt < trob) trob = tt;
+                    }
+                }
+                if (best >= 0) {
+                    d3 nb = v3(tri_normal[3 * best], tri_normal[3 * best + 1], tri_normal[3 * best + 2]);
+                    double dn = vdot(dir, nb);
+                    if (dn < 0.0) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        F_out[i * nt + best] += e;
+                    }
+                    if (amb_out && fabs(dn) <= rel * dl * vnorm(nb)) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        amb_out[i * nt + best] += e;
+                    }
+                }
+                if (!amb_out) continue;
+                /* receivers: inside or near, and not behind the nearest robust hit */
+                int64_t rec[16];
+                int nrec = 0;
+                for (int64_t t = 0; t < nt && nrec < 16; ++t) {
+                    d3 e1 = vsub(T[t].b, T[t].a), e2 = vsub(T[t].c, T[t].a);
+                    d3 p = vcross(dir, e2);
+                    double det = vdot(e1, p);
+                    d3 r = vsub(o, T[t].a);
+                    if (det == 0.0) {
+                        /* edge-on: near if the ray passes within rel of the triangle */
+                        continue;
+                    }
+                    d3 qq = vcross(r, e1);
+                    double tt = vdot(e2, qq) / det;
+                    if (!(tt > 0.0) || tt > trob * (1.0 + rel)) continue;
+                    d3 h = vadd(o, vmul(dir, tt));
+                    if (point_triangle_distance(h, T[t].a, T[t].b, T[t].c) <= rel * tt * dl) rec[nrec++] = t;
+                }
+                if (nrec >= 2)
+                    for (int k = 0; k < nrec; ++k) {
+#ifdef _OPENMP
+#pragma omp atomic
+#endif
+                        amb_out[i * nt + rec[k]] += e;
+                    }
+            }
+        }
+    free(T);
+    return 0;
+}

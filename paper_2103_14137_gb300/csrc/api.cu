@@ -109,6 +109,24 @@ int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t 
     return uvc::irradiance_area_mean(scene, cand, nc, L, ptri, A, lda, nclosed, (cudaStream_t)stream);
 }
 
+size_t uvc_raster_workspace_bytes(const uvc_scene* scene, const uvc_lamp* lamp, int32_t R, int64_t cand_per_batch) {
+    if (!scene || !lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES || R < 1 || R > 4096 || cand_per_batch < 1)
+        return 0;
+    return uvc::raster_workspace_bytes(scene->nt, lamp->K, R, cand_per_batch);
+}
+
+int uvc_irradiance_raster(const uvc_scene* scene, const float* tri_normal, const float* cand, int64_t nc,
+                          const uvc_lamp* lamp, int32_t R, float* A, int64_t lda, void* workspace, size_t bytes,
+                          uvc_stream_t stream) {
+    if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX || R < 1 || R > 4096) return UVC_E_INVAL;
+    uvc::LampDev L;
+    int rc = uvc::lamp_to_device(lamp, &L);
+    if (rc != UVC_OK) return rc;
+    if (lda < scene->nt) return UVC_E_INVAL;
+    if (nc > 0 && scene->nt > 0 && (!cand || !A || !tri_normal || !workspace)) return UVC_E_INVAL;
+    return uvc::irradiance_raster(scene, tri_normal, cand, nc, L, R, A, lda, workspace, bytes, (cudaStream_t)stream);
+}
+
 int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
                 float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256 || lda < scene->np) return UVC_E_INVAL;

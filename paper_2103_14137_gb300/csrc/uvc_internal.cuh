@@ -94,6 +94,11 @@ int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc,
 int irradiance_area_mean(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, const float* ptri,
                          float* A, int64_t lda, uint8_t* nclosed, cudaStream_t stream);
 
+// visibility-cube estimator (raster.cu)
+size_t raster_workspace_bytes(int64_t nt, int K, int R, int64_t cand_per_batch);
+int irradiance_raster(const uvc_scene* sc, const float* tri_normal, const float* cand, int64_t nc, const LampDev& L,
+                      int R, float* A, int64_t lda, void* work, size_t bytes, cudaStream_t stream);
+
 // fluence and coverage (fluence.cu)
 int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
             float* mu, cudaStream_t stream);

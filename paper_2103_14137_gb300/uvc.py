@@ -65,6 +65,7 @@ def library():
         "uvc_irradiance_matrix": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence": [P, P, i64, i64, P, i32, P, P],
         "uvc_irradiance_area_mean": [P, P, i64, ctypes.POINTER(_Lamp), P, P, i64, P, P],
+        "uvc_irradiance_raster": [P, P, P, i64, ctypes.POINTER(_Lamp), i32, P, i64, P, ctypes.c_size_t, P],
         "uvc_irradiance_counters": [P, P, i64, ctypes.POINTER(_Lamp), P, i64, P, P],
         "uvc_fluence_streamed": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
         "uvc_fluence_streamed_noalloc": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
@@ -99,6 +100,8 @@ def library():
         fn.restype = ctypes.c_int
     lib.uvc_batch_workspace_bytes.argtypes = [i32, i32]
     lib.uvc_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.uvc_raster_workspace_bytes.argtypes = [P, ctypes.POINTER(_Lamp), i32, i64]
+    lib.uvc_raster_workspace_bytes.restype = ctypes.c_size_t
     lib.uvc_probe_features_work_bytes.argtypes = [i64]
     lib.uvc_probe_features_work_bytes.restype = ctypes.c_size_t
     lib.uvc_mlp_param_count.argtypes = [P]
@@ -271,6 +274,31 @@ def irradiance_area_mean(scene: Scene, cand, lamp: Lamp, ptri, A=None, with_clos
                                             _stream(stream))
     _check(rc, "uvc_irradiance_area_mean")
     return A, ncl
+
+
+def raster_workspace(scene: Scene, lamp: Lamp, R: int, cand_per_batch: int, device="cuda"):
+    L = lamp._c()
+    n = int(library().uvc_raster_workspace_bytes(scene.handle, ctypes.byref(L), int(R), int(cand_per_batch)))
+    if n == 0:
+        raise UvcError(UVC_E_INVAL, "uvc_raster_workspace_bytes")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def irradiance_raster(scene: Scene, tri_normal, cand, lamp: Lamp, R: int = 512, A=None, workspace=None,
+                      cand_per_batch: int = 8, stream=None):
+    """The visibility-cube estimator: (nc, nt) mean irradiance per triangle."""
+    nc = cand.shape[0]
+    if A is None:
+        A = torch.empty((nc, scene.nt), dtype=torch.float32, device=cand.device)
+    if workspace is None:
+        workspace = raster_workspace(scene, lamp, R, max(1, min(cand_per_batch, nc)), cand.device)
+    L = lamp._c()
+    rc = library().uvc_irradiance_raster(scene.handle, _dev(tri_normal, torch.float32, "tri_normal", (scene.nt, 3)),
+                                         _dev(cand, torch.float32, "cand", (nc, 3)), nc, ctypes.byref(L), int(R),
+                                         _dev(A, torch.float32, "A"), A.shape[1] if A.dim() == 2 else 0,
+                                         ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+    _check(rc, "uvc_irradiance_raster")
+    return A
 
 
 def fluence(scene: Scene, A, t, mu=None, stream=None):
