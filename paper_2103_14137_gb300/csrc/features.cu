@@ -12,6 +12,10 @@ namespace uvc {
 namespace {
 
 constexpr int kBins = 64;
+// Probe-column kernels: a block covers 32 columns x 8 row slices; thread
+// (slice, column) scans rows slice, slice + 8, ... (coalesced across the 32
+// columns), and the 8 slices are combined in shared memory.
+constexpr int kColW = 32, kColSlices = 8;
 constexpr int kHistThreads = 256;
 
 struct Edges {
@@ -208,15 +212,27 @@ __global__ void __launch_bounds__(kSelectThreads) k_select_top(const float* __re
 __global__ void k_probe_lost(const float* __restrict__ A, int nc, int64_t lda, int np,
                              const int32_t* __restrict__ idx, int k, const float* __restrict__ area,
                              float* __restrict__ lost) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
+    __shared__ unsigned char pf[kColSlices][kColW], pr[kColSlices][kColW];
+    const int cx = threadIdx.x % kColW, sl = threadIdx.x / kColW;
+    const int j = blockIdx.x * kColW + cx;
     bool full = false, red = false;
-    for (int i = 0; i < nc && !full; ++i) full = A[(int64_t)i * lda + j] > 0.f;
-    for (int r = 0; r < k && full && !red; ++r) {
-        const int i = idx[r];
-        if (i >= 0 && i < nc) red = A[(int64_t)i * lda + j] > 0.f;   // rows out of range are ignored
+    if (j < np) {
+        for (int i = sl; i < nc && !full; i += kColSlices) full = A[(int64_t)i * lda + j] > 0.f;
+        for (int r = sl; r < k && !red; r += kColSlices) {
+            const int i = idx[r];
+            if (i >= 0 && i < nc) red = A[(int64_t)i * lda + j] > 0.f;   // rows out of range are ignored
+        }
     }
-    lost[j] = (full && !red) ? area[j] : 0.f;
+    pf[sl][cx] = full;
+    pr[sl][cx] = red;
+    __syncthreads();
+    if (sl == 0 && j < np) {
+        for (int q = 1; q < kColSlices; ++q) {
+            full |= pf[q][cx];
+            red |= pr[q][cx];
+        }
+        lost[j] = (full && !red) ? area[j] : 0.f;
+    }
 }
 
 // out = sum(lost) / sum(area), compensated sums in a fixed order (one block).
@@ -252,13 +268,20 @@ __global__ void k_probe_total(const float* __restrict__ lost, const float* __res
 constexpr int kHardBins = 8, kEffBins = 6, kProbeFeat = kHardBins * kEffBins;
 constexpr int kProbeWarps = 4;
 
-// E*_j = max_i A[i][j] (thread per probe patch, coalesced rows).
+// E*_j = max_i A[i][j].
 __global__ void k_col_max(const float* __restrict__ A, int nc, int64_t lda, int np, float* __restrict__ emax) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
+    __shared__ float part[kColSlices][kColW];
+    const int cx = threadIdx.x % kColW, sl = threadIdx.x / kColW;
+    const int j = blockIdx.x * kColW + cx;
     float m = 0.f;
-    for (int i = 0; i < nc; ++i) m = fmaxf(m, A[(int64_t)i * lda + j]);
-    emax[j] = m;
+    if (j < np)
+        for (int i = sl; i < nc; i += kColSlices) m = fmaxf(m, A[(int64_t)i * lda + j]);
+    part[sl][cx] = m;
+    __syncthreads();
+    if (sl == 0 && j < np) {
+        for (int q = 1; q < kColSlices; ++q) m = fmaxf(m, part[q][cx]);
+        emax[j] = m;
+    }
 }
 
 // Lit-area-weighted mean of E* (compensated sums, fixed order, one block),
@@ -346,25 +369,42 @@ __global__ void __launch_bounds__(kProbeWarps * 32) k_probe_feat(const float* __
 // with the same value.
 __global__ void k_mark_best(const float* __restrict__ A, int nc, int64_t lda, int np, float* __restrict__ score,
                             float value) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= np) return;
+    __shared__ float pv[kColSlices][kColW];
+    __shared__ int pi[kColSlices][kColW];
+    const int cx = threadIdx.x % kColW, sl = threadIdx.x / kColW;
+    const int j = blockIdx.x * kColW + cx;
     float m = 0.f;
     int best = -1;
-    for (int i = 0; i < nc; ++i) {
-        const float v = A[(int64_t)i * lda + j];
-        if (v > m) {
-            m = v;
-            best = i;
+    if (j < np)
+        for (int i = sl; i < nc; i += kColSlices) {
+            const float v = A[(int64_t)i * lda + j];
+            if (v > m) {        // rows ascend within a slice: the first maximum is kept
+                m = v;
+                best = i;
+            }
         }
+    pv[sl][cx] = m;
+    pi[sl][cx] = best;
+    __syncthreads();
+    if (sl == 0 && j < np) {
+        for (int q = 1; q < kColSlices; ++q) {
+            const float v = pv[q][cx];
+            const int b = pi[q][cx];
+            if (b >= 0 && (v > m || (v == m && (best < 0 || b < best)))) {
+                m = v;
+                best = b;
+            }
+        }
+        if (best >= 0) score[best] = value;
     }
-    if (best >= 0) score[best] = value;
 }
 
 }  // namespace
 
 int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, cudaStream_t stream) {
     if (np > 0 && nc > 0)
-        k_mark_best<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, score, value);
+        k_mark_best<<<(int)((np + kColW - 1) / kColW), kColW * kColSlices, 0, stream>>>(A, (int)nc, lda, (int)np,
+                                                                                      score, value);
     return status_from_cuda(cudaGetLastError());
 }
 
@@ -374,7 +414,8 @@ int probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const fl
     float* emax = work;
     float* stats = work + np;
     signed char* hb = reinterpret_cast<signed char*>(work + np + 4);
-    if (np > 0) k_col_max<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, emax);
+    if (np > 0)
+        k_col_max<<<(int)((np + kColW - 1) / kColW), kColW * kColSlices, 0, stream>>>(A, (int)nc, lda, (int)np, emax);
     k_probe_bins<<<1, 256, 0, stream>>>(emax, area, (int)np, stats, hb);
     k_probe_feat<<<(int)((nc + kProbeWarps - 1) / kProbeWarps), kProbeWarps * 32, 0, stream>>>(
         A, (int)nc, lda, (int)np, emax, hb, area, stats, feat, ldf);
@@ -384,7 +425,8 @@ int probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const fl
 int probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
                const float* area, float* lost, float* out, cudaStream_t stream) {
     if (np > 0) {
-        k_probe_lost<<<(int)((np + 255) / 256), 256, 0, stream>>>(A, (int)nc, lda, (int)np, idx, (int)k, area, lost);
+        k_probe_lost<<<(int)((np + kColW - 1) / kColW), kColW * kColSlices, 0, stream>>>(A, (int)nc, lda, (int)np, idx,
+                                                                                       (int)k, area, lost);
     }
     k_probe_total<<<1, 256, 0, stream>>>(lost, area, (int)np, out);
     return status_from_cuda(cudaGetLastError());

@@ -30,6 +30,7 @@ namespace {
 constexpr float kFixOne = 1099511627776.0f;          // 2^40
 constexpr float kFixInv = 1.0f / 1099511627776.0f;   // 2^-40
 constexpr int kScanBlock = 1024, kScanPer = 4;       // 4096 elements per scan block
+constexpr int kSampleShift = 8;                      // one search hint per 256 fragments
 
 struct RasterBatch {
     const float4* tri;        // sorted triangles (v0.w = original id)
@@ -43,6 +44,8 @@ struct RasterBatch {
     unsigned long long* F;        // [C / K][nt] flux, 2^-40 W units, by original id
     const float* e_unit;          // [R][R] Omega_pixel / (4 pi)
     const float* tri_normal;      // [nt][3] by original id
+    int* hint;                    // [total / 256 + 2] entry holding fragment 256 s (search hint)
+    int64_t hint_cap;             // capacity of hint
 };
 
 __device__ __forceinline__ float comp(float x, float y, float z, int k) { return k == 0 ? x : (k == 1 ? y : z); }
@@ -175,6 +178,21 @@ __global__ void k_fill64(unsigned long long* x, int64_t n, unsigned long long v)
         x[i] = v;
 }
 
+// hint[s] = the entry that holds fragment s << kSampleShift (thread per entry;
+// entries own disjoint fragment ranges, so every hint slot is written once).
+__global__ void k_rs_hints(RasterBatch B) {
+    const int64_t E = (int64_t)B.C * 6 * B.nt;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const unsigned long long lo = B.count[e], hi = B.count[e + 1];
+    if (hi == lo) return;
+    const unsigned long long step = 1ull << kSampleShift;
+    for (unsigned long long g = (lo + step - 1) & ~(step - 1); g < hi; g += step) {
+        const unsigned long long s = g >> kSampleShift;
+        if ((int64_t)s < B.hint_cap) B.hint[s] = (int)e;
+    }
+}
+
 // Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013) for the ray
 // o + t d, t > 0; returns t (or a negative value for a miss).
 __device__ __forceinline__ float ray_tri(float ox, float oy, float oz, float dx, float dy, float dz, float4 A4,
@@ -207,6 +225,36 @@ __device__ __forceinline__ float ray_tri(float ox, float oy, float oz, float dx,
     return t > 0.f ? t : -1.f;
 }
 
+// ray_tri for a pixel ray of face (a, s): the axis a holds the largest
+// component (+-1; |u|, |v| < 1 at pixel centres), so the shear of ray_tri
+// divides by s = +-1, which is exact: the same values without divisions.
+__device__ __forceinline__ float ray_tri_face(float ox, float oy, float oz, float dx, float dy, float dz, int a, float s,
+                                              float4 A4, float4 B4, float4 C4) {
+    const int kz = a;
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (s < 0.f) {
+        const int t = kx; kx = ky; ky = t;
+    }
+    const float sx = s * comp(dx, dy, dz, kx), sy = s * comp(dx, dy, dz, ky), sz = s;
+    const float Ax = __fsub_rn(A4.x, ox), Ay = __fsub_rn(A4.y, oy), Az = __fsub_rn(A4.z, oz);
+    const float Bx = __fsub_rn(B4.x, ox), By = __fsub_rn(B4.y, oy), Bz = __fsub_rn(B4.z, oz);
+    const float Cx = __fsub_rn(C4.x, ox), Cy = __fsub_rn(C4.y, oy), Cz = __fsub_rn(C4.z, oz);
+    const float akz = comp(Ax, Ay, Az, kz), bkz = comp(Bx, By, Bz, kz), ckz = comp(Cx, Cy, Cz, kz);
+    const float ax = __fmaf_rn(-sx, akz, comp(Ax, Ay, Az, kx)), ay = __fmaf_rn(-sy, akz, comp(Ax, Ay, Az, ky));
+    const float bx = __fmaf_rn(-sx, bkz, comp(Bx, By, Bz, kx)), by = __fmaf_rn(-sy, bkz, comp(Bx, By, Bz, ky));
+    const float cx = __fmaf_rn(-sx, ckz, comp(Cx, Cy, Cz, kx)), cy = __fmaf_rn(-sy, ckz, comp(Cx, Cy, Cz, ky));
+    const float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
+    const float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
+    const float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
+    if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return -1.f;
+    const float det = U + V + W;
+    if (det == 0.f) return -1.f;
+    const float T = U * __fmul_rn(sz, akz) + V * __fmul_rn(sz, bkz) + W * __fmul_rn(sz, ckz);
+    const float t = __fdiv_rn(T, det);
+    return t > 0.f ? t : -1.f;
+}
+
 __global__ void k_rs_raster(RasterBatch B) {
     const int64_t E = (int64_t)B.C * 6 * B.nt;
     const int64_t RR = (int64_t)B.R * B.R;
@@ -216,8 +264,17 @@ __global__ void k_rs_raster(RasterBatch B) {
     if (total > (unsigned long long)E * (unsigned long long)RR) return;
     for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
          g += (unsigned long long)gridDim.x * blockDim.x) {
-        // entry e: the last offset <= g
+        // entry e: the last offset <= g, searched between the hints of the
+        // 256-fragment slots around g
+        const unsigned long long sl = g >> kSampleShift;
         int64_t lo = 0, hi = E;   // count[lo] <= g < count[hi]
+        if ((int64_t)sl + 1 < B.hint_cap) {
+            lo = B.hint[sl];
+            const unsigned long long nx = (sl + 1) << kSampleShift;
+            hi = nx < total ? (int64_t)B.hint[sl + 1] + 1 : E;
+            if (lo < 0 || lo >= E || B.count[lo] > g) lo = 0;   // not a valid hint: full range
+            if (hi <= lo || hi > E || B.count[hi] <= g) hi = E;
+        }
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (B.count[mid] <= g) lo = mid; else hi = mid;
@@ -239,7 +296,7 @@ __global__ void k_rs_raster(RasterBatch B) {
                     oz = B.cand[3 * ci + 2] + B.L.oz[m];
         const float4 A4 = __ldg(&B.tri[3 * (size_t)k]), B4 = __ldg(&B.tri[3 * (size_t)k + 1]),
                      C4 = __ldg(&B.tri[3 * (size_t)k + 2]);
-        const float t = ray_tri(ox, oy, oz, d[0], d[1], d[2], A4, B4, C4);
+        const float t = ray_tri_face(ox, oy, oz, d[0], d[1], d[2], a, s, A4, B4, C4);
         if (t > 0.f) {
             const unsigned long long key =
                 ((unsigned long long)__float_as_uint(t) << 32) | (unsigned)__float_as_int(A4.w);
@@ -248,27 +305,48 @@ __global__ void k_rs_raster(RasterBatch B) {
     }
 }
 
+// Neighbouring pixels mostly see the same triangle: the lanes of a warp that
+// add to the same (candidate, triangle) sum their fixed-point powers first
+// (lanes grouped with __match_any_sync, the lowest lane adds for the group).
 __global__ void k_rs_resolve(RasterBatch B) {
+    __shared__ unsigned long long part[8][32];
     const int64_t RR = (int64_t)B.R * B.R;
     const int64_t n = (int64_t)B.C * 6 * RR;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long key = B.keys[q];
-        if (key == ~0ull) continue;
-        const int id = (int)(key & 0xffffffffull);
-        const int64_t cf = q / RR;
-        const int pix = (int)(q % RR);
-        const int px = pix % B.R, py = pix / B.R;
-        const int c = (int)(cf / 6), f = (int)(cf % 6);
-        const int a = f >> 1;
-        const float s = (f & 1) ? -1.f : 1.f;
-        float d[3];
-        d[a] = s; d[(a + 1) % 3] = pix_center(px, B.R); d[(a + 2) % 3] = pix_center(py, B.R);
-        const float* nrm = B.tri_normal + 3 * (size_t)id;
-        const float dn = d[0] * nrm[0] + d[1] * nrm[1] + d[2] * nrm[2];
-        if (!(dn < 0.f)) continue;   // back side: absorbed
-        const int ci = c / B.K, m = c % B.K;
-        const float pw = __fmul_rn(B.L.pw[m], B.e_unit[pix]);
-        atomicAdd(&B.F[(size_t)ci * B.nt + id], __float2ull_rn(__fmul_rn(pw, kFixOne)));
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + wib) * 32; base < n; base += nwarps * 32) {
+        const int64_t q = base + lane;
+        unsigned long long key = q < n ? B.keys[q] : ~0ull;
+        long long slot = -1;                  // (candidate, triangle) the lane adds to
+        unsigned long long val = 0;
+        if (key != ~0ull) {
+            const int id = (int)(key & 0xffffffffull);
+            const int64_t cf = q / RR;
+            const int pix = (int)(q % RR);
+            const int px = pix % B.R, py = pix / B.R;
+            const int c = (int)(cf / 6), f = (int)(cf % 6);
+            const int a = f >> 1;
+            const float s = (f & 1) ? -1.f : 1.f;
+            float d[3];
+            d[a] = s; d[(a + 1) % 3] = pix_center(px, B.R); d[(a + 2) % 3] = pix_center(py, B.R);
+            const float* nrm = B.tri_normal + 3 * (size_t)id;
+            const float dn = d[0] * nrm[0] + d[1] * nrm[1] + d[2] * nrm[2];
+            if (dn < 0.f) {                   // front side; the back side absorbs
+                const int ci = c / B.K, m = c % B.K;
+                const float pw = __fmul_rn(B.L.pw[m], B.e_unit[pix]);
+                val = __float2ull_rn(__fmul_rn(pw, kFixOne));
+                slot = (long long)ci * B.nt + id;
+            }
+        }
+        const unsigned group = __match_any_sync(0xffffffffu, slot);
+        part[wib][lane] = val;
+        __syncwarp();
+        if (slot >= 0 && lane == __ffs(group) - 1) {
+            unsigned long long sum = 0;
+            for (unsigned g = group; g; g &= g - 1) sum += part[wib][__ffs(g) - 1];
+            atomicAdd(&B.F[slot], sum);
+        }
+        __syncwarp();
     }
 }
 
@@ -309,11 +387,17 @@ const std::vector<float>& pixel_table(int R) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Hint slots for a batch of C cubes: fragments are bounded by 8 per pixel on
+// average (bounding boxes over-cover; scenes with more depth complexity fall
+// back to the full search beyond the slots).
+int64_t hint_slots(int64_t C, int R) { return ((C * 6 * (int64_t)R * R * 8) >> kSampleShift) + 2; }
+
 // Workspace layout for nb candidates per batch.
 size_t raster_bytes(int64_t nt, int K, int R, int64_t nb) {
     const int64_t C = nb * K, E = C * 6 * nt;
     const int64_t nblk = (E + 1 + kScanBlock * kScanPer - 1) / (kScanBlock * kScanPer);
-    return align256(sizeof(unsigned long long) * (size_t)C * 6 * R * R) +
+    return align256(sizeof(int) * (size_t)hint_slots(C, R)) +
+           align256(sizeof(unsigned long long) * (size_t)C * 6 * R * R) +
            align256(sizeof(unsigned long long) * (size_t)(E + 1)) + align256(sizeof(unsigned long long) * (size_t)E) +
            align256(sizeof(unsigned long long) * (size_t)(nb * nt)) + align256(sizeof(float) * (size_t)R * R) +
            align256(sizeof(unsigned long long) * (size_t)(nblk + 1)) + 256;
@@ -337,6 +421,9 @@ int irradiance_raster(const uvc_scene* sc, const float* tri_normal, const float*
     char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(work) + 255) & ~uintptr_t(255));
     const int64_t Cmax = nb * L.K, Emax = Cmax * 6 * nt;
     RasterBatch B;
+    B.hint = reinterpret_cast<int*>(p);
+    B.hint_cap = hint_slots(Cmax, R);
+    p += align256(sizeof(int) * (size_t)B.hint_cap);
     B.tri = sc->tri;
     B.order = sc->order;
     B.nt = (int)nt;
@@ -371,6 +458,7 @@ int irradiance_raster(const uvc_scene* sc, const float* tri_normal, const float*
         k_scan_blocks<<<(int)nblk, kScanBlock, 0, stream>>>(B.count, E, sums);
         k_scan_sums<<<1, 32, 0, stream>>>(sums, (int)nblk, B.count + E);
         k_scan_add<<<(int)((E + 255) / 256), 256, 0, stream>>>(B.count, E, sums);
+        k_rs_hints<<<(int)((E + 255) / 256), 256, 0, stream>>>(B);
         k_fill64<<<grid, 256, 0, stream>>>(B.keys, (int64_t)B.C * 6 * R * R, ~0ull);
         k_fill64<<<grid, 256, 0, stream>>>(B.F, n * nt, 0ull);
         k_rs_raster<<<grid, 256, 0, stream>>>(B);
