@@ -694,7 +694,9 @@ def run_learned(args):
         scorer.scores(feat[:nrows], out=score[:nrows])
         for R, j, Ap, Ar, row0 in lay:
             sj = score[row0:row0 + j["nc"]]
-            uvc.mark_best(Ap[:, :R["half"]], sj)
+            if prop.GROUP > 1:
+                uvc.group_boost(sj, prop.GROUP)
+            uvc.mark_best(Ap[:, :R["half"]], sj, rare=prop.rare_count(j["nc"]))
             uvc.select_top(sj, j["k"], cand=j["cand"], out_cand=j["kept"], out_idx=j["idx"])
             q = job_ids[id(j)]
             uvc.probe_lost(Ap[:, R["half"]:], j["idx"], R["area_p"][R["half"]:], out=flags[q:q + 1],

@@ -400,15 +400,28 @@ int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, 
                    uvc_stream_t stream);
 
 /*
+ * uvc_group_boost - stratified selection: in every group of `group`
+ * consecutive candidates (candidates come in spatial grid order, so a group
+ * is a neighbourhood) the highest score (lowest index among equal scores, NaN
+ * lowest) gets `bonus` added, so that a following uvc_select_top keeps one
+ * candidate of every neighbourhood before it ranks the rest globally.
+ *   score  float[n] device, updated;  group >= 1
+ * Enqueued on `stream`, capturable.  Errors: UVC_E_INVAL, UVC_E_CUDA.
+ */
+int uvc_group_boost(float* score, int64_t n, int32_t group, float bonus, uvc_stream_t stream);
+
+/*
  * uvc_mark_best - for every probe patch j that some candidate lights, set
  * score[i*] = value where i* = argmax_i A[i][j] (the lowest index among equal
  * maxima), so that a following uvc_select_top keeps the best source of every
  * probe patch whatever the scorer says (value = +inf; if more candidates are
- * marked than kept, the lower indices win).
+ * marked than kept, the lower indices win).  With rare > 0, every candidate
+ * that lights a probe patch lit by at most `rare` candidates is marked too
+ * (such patches go dark unless one of their few sources is kept).
  *   A  float[nc][lda] device, lda >= np;  score  float[nc] device, updated
  * Enqueued on `stream`, capturable.  Errors: UVC_E_INVAL, UVC_E_CUDA.
  */
-int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value,
+int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, int32_t rare,
                   uvc_stream_t stream);
 
 /*

@@ -191,11 +191,17 @@ int uvc_select_top(const float* score, int64_t n, int64_t k, const float* cand, 
     return uvc::select_top(score, n, k, cand, out_cand, out_idx, (cudaStream_t)stream);
 }
 
-int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value,
+int uvc_group_boost(float* score, int64_t n, int32_t group, float bonus, uvc_stream_t stream) {
+    if (n < 0 || n > INT32_MAX || group < 1 || (n > 0 && !score)) return UVC_E_INVAL;
+    return uvc::group_boost(score, n, group, bonus, (cudaStream_t)stream);
+}
+
+int uvc_mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, int32_t rare,
                   uvc_stream_t stream) {
-    if (!uvc::count_ok(nc) || !uvc::count_ok(np) || nc > INT32_MAX || np > INT32_MAX || lda < np) return UVC_E_INVAL;
+    if (!uvc::count_ok(nc) || !uvc::count_ok(np) || nc > INT32_MAX || np > INT32_MAX || lda < np || rare < 0)
+        return UVC_E_INVAL;
     if (nc > 0 && np > 0 && (!A || !score)) return UVC_E_INVAL;
-    return uvc::mark_best(A, nc, lda, np, score, value, (cudaStream_t)stream);
+    return uvc::mark_best(A, nc, lda, np, score, value, rare, (cudaStream_t)stream);
 }
 
 int uvc_probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,

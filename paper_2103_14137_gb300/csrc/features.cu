@@ -365,19 +365,21 @@ __global__ void __launch_bounds__(kProbeWarps * 32) k_probe_feat(const float* __
 }
 
 // For each lit probe patch j, score[argmax_i A[i][j]] = value (the lowest
-// index among equal maxima).  Several patches may write the same candidate
-// with the same value.
+// index among equal maxima); with rare > 0, also every candidate that lights
+// a patch lit by at most `rare` candidates.  Several patches may write the
+// same candidate with the same value.
 __global__ void k_mark_best(const float* __restrict__ A, int nc, int64_t lda, int np, float* __restrict__ score,
-                            float value) {
+                            float value, int rare) {
     __shared__ float pv[kColSlices][kColW];
-    __shared__ int pi[kColSlices][kColW];
+    __shared__ int pi[kColSlices][kColW], pn[kColSlices][kColW];
     const int cx = threadIdx.x % kColW, sl = threadIdx.x / kColW;
     const int j = blockIdx.x * kColW + cx;
     float m = 0.f;
-    int best = -1;
+    int best = -1, lit = 0;
     if (j < np)
         for (int i = sl; i < nc; i += kColSlices) {
             const float v = A[(int64_t)i * lda + j];
+            lit += v > 0.f;
             if (v > m) {        // rows ascend within a slice: the first maximum is kept
                 m = v;
                 best = i;
@@ -385,7 +387,10 @@ __global__ void k_mark_best(const float* __restrict__ A, int nc, int64_t lda, in
         }
     pv[sl][cx] = m;
     pi[sl][cx] = best;
+    pn[sl][cx] = lit;
     __syncthreads();
+    int total = 0;
+    for (int q = 0; q < kColSlices; ++q) total += pn[q][cx];
     if (sl == 0 && j < np) {
         for (int q = 1; q < kColSlices; ++q) {
             const float v = pv[q][cx];
@@ -397,14 +402,44 @@ __global__ void k_mark_best(const float* __restrict__ A, int nc, int64_t lda, in
         }
         if (best >= 0) score[best] = value;
     }
+    if (j < np && total > 0 && total <= rare)
+        for (int i = sl; i < nc; i += kColSlices)
+            if (A[(int64_t)i * lda + j] > 0.f) score[i] = value;
+}
+
+// score[winner of each group of `group` consecutive candidates] += bonus;
+// the winner is the highest score of the group (lowest index among equals,
+// NaN lowest).  One thread per group.
+__global__ void k_group_boost(float* __restrict__ score, int n, int group, float bonus) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i0 = g * group;
+    if (i0 >= n) return;
+    const int i1 = min(n, i0 + group);
+    int best = i0;
+    uint32_t bk = score_key(score[i0]);
+    for (int i = i0 + 1; i < i1; ++i) {
+        const uint32_t k = score_key(score[i]);
+        if (k > bk) {
+            bk = k;
+            best = i;
+        }
+    }
+    score[best] = score[best] + bonus;
 }
 
 }  // namespace
 
-int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, cudaStream_t stream) {
+int group_boost(float* score, int64_t n, int group, float bonus, cudaStream_t stream) {
+    const int64_t ng = (n + group - 1) / group;
+    if (ng > 0) k_group_boost<<<(int)((ng + 255) / 256), 256, 0, stream>>>(score, (int)n, group, bonus);
+    return status_from_cuda(cudaGetLastError());
+}
+
+int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, int rare,
+              cudaStream_t stream) {
     if (np > 0 && nc > 0)
         k_mark_best<<<(int)((np + kColW - 1) / kColW), kColW * kColSlices, 0, stream>>>(A, (int)nc, lda, (int)np,
-                                                                                      score, value);
+                                                                                      score, value, rare);
     return status_from_cuda(cudaGetLastError());
 }
 

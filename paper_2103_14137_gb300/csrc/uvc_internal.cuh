@@ -111,7 +111,9 @@ int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float
                        cudaStream_t stream);
 int probe_features(const float* A, int64_t nc, int64_t lda, int64_t np, const float* area, float* work,
                    float* feat, int64_t ldf, cudaStream_t stream);
-int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, cudaStream_t stream);
+int group_boost(float* score, int64_t n, int group, float bonus, cudaStream_t stream);
+int mark_best(const float* A, int64_t nc, int64_t lda, int64_t np, float* score, float value, int rare,
+              cudaStream_t stream);
 int probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const int32_t* idx, int64_t k,
                const float* area, float* lost, float* out, cudaStream_t stream);
 int select_top(const float* score, int64_t n, int64_t k, const float* cand, float* out_cand, int32_t* out_idx,

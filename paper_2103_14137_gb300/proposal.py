@@ -9,7 +9,8 @@ irradiance of all candidates on one half of a probe sample of PROBE of the
 patches.  The other half of the probe is the fallback check: if the kept
 candidates leave more than LOST_MAX of the area lit there dark
 (uvc_probe_lost), the job runs on all candidates.  Whatever the scores, the
-best source of every sketch patch is kept (uvc_mark_best).
+best source of every sketch patch is kept, and every source of a sketch
+patch that at most a fraction RARE_FRAC of the candidates light (uvc_mark_best).
 
 The scorer learns which candidates the relaxed LP of Sec. IV-D (Eq. (9))
 gives a non-zero dwell time; the plain method - every candidate, exact matrix,
@@ -30,12 +31,18 @@ from .lp import MU_MIN, T_MAX, patch_sample, solve_job, support
 KEEP = 0.2              # fraction of candidates kept
 PROBE = 0.01            # fraction of patches in the probe (half sketch, half fallback check)
 LOST_MAX = 0.0025       # check area lit by all candidates but dark for the kept ones -> fallback
+RARE_FRAC = 0.01        # sketch patches lit by at most this fraction of the candidates keep all their sources
+GROUP = 1               # > 1: also keep the best of every GROUP consecutive (neighbouring) candidates
 HIDDEN = 256
 IN_DIM = uvc.FEATURES + uvc.PROBE_FEATURES
 LP_PATCHES = 1000       # initial LP rows; row generation adds the violated patches
 LP_ADD = 1500           # violated patches added per round
 LP_ROUNDS = 4
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "scorer.npz")
+
+
+def rare_count(nc: int) -> int:
+    return max(3, int(math.ceil(RARE_FRAC * nc)))
 
 
 def keep_count(nc: int, keep: float = KEEP) -> int:
@@ -93,11 +100,14 @@ class Scorer:
 
     def select(self, feat, cand, A_sketch=None, keep: float = KEEP, score=None, stream=None):
         """(idx, kept candidates): the best source of every sketch patch
-        (A_sketch, if given), then the best scores, keep-fraction in all,
+        (A_sketch, if given), then the best-scoring candidate of every group
+        of GROUP neighbours, then the best scores, keep-fraction in all,
         ascending index."""
         score = self.scores(feat, out=score, stream=stream)
+        if GROUP > 1:
+            uvc.group_boost(score, GROUP, stream=stream)
         if A_sketch is not None:
-            uvc.mark_best(A_sketch, score, stream=stream)
+            uvc.mark_best(A_sketch, score, rare=rare_count(cand.shape[0]), stream=stream)
         return uvc.select_top(score, keep_count(cand.shape[0], keep), cand=cand, stream=stream)
 
 
@@ -213,5 +223,5 @@ def coverage_of(area, mu, lit=None):
 
 
 __all__ = ["KEEP", "PROBE", "LOST_MAX", "HIDDEN", "IN_DIM", "LP_PATCHES", "WEIGHTS", "Scorer", "train", "save",
-           "keep_count", "probe_columns", "features", "label_of", "fold_standardisation", "solve_many", "dwell_rowgen",
+           "keep_count", "rare_count", "probe_columns", "features", "label_of", "fold_standardisation", "solve_many", "dwell_rowgen",
            "coverage_of", "support"]

@@ -86,7 +86,8 @@ def library():
         "uvc_probe_features": [P, i64, i64, i64, P, P, P, i64, P],
         "uvc_select_top": [P, i64, i64, P, P, P, P],
         "uvc_probe_lost": [P, i64, i64, i64, P, i64, P, P, P, P],
-        "uvc_mark_best": [P, i64, i64, i64, P, ctypes.c_float, P],
+        "uvc_mark_best": [P, i64, i64, i64, P, ctypes.c_float, i32, P],
+        "uvc_group_boost": [P, i64, i32, ctypes.c_float, P],
         "uvc_mlp_create": [i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(P)],
         "uvc_mlp_free": [P],
         "uvc_mlp_params": [P, P, i64, i32],
@@ -421,13 +422,22 @@ def select_top(score, k: int, cand=None, out_cand=None, out_idx=None, stream=Non
     return out_idx, out_cand
 
 
-def mark_best(A, score, value=float("inf"), stream=None):
-    """score[argmax_i A[i, j]] = value for every lit column j of A (nc, np)."""
+def group_boost(score, group: int, bonus: float = 1e30, stream=None):
+    """Add `bonus` to the best score of every group of `group` consecutive candidates."""
+    n = score.shape[0]
+    _check(library().uvc_group_boost(_dev(score, torch.float32, "score", (n,)), n, int(group), float(bonus),
+                                     _stream(stream)), "uvc_group_boost")
+    return score
+
+
+def mark_best(A, score, value=float("inf"), rare: int = 0, stream=None):
+    """score[argmax_i A[i, j]] = value for every lit column j of A (nc, np);
+    with rare > 0 also every candidate lighting a column lit by <= rare rows."""
     nc, np_ = A.shape
     if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
         raise TypeError("A must be a float32 CUDA matrix with unit column stride")
     rc = library().uvc_mark_best(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, max(A.stride(0), np_), np_,
-                                 _dev(score, torch.float32, "score", (nc,)), float(value), _stream(stream))
+                                 _dev(score, torch.float32, "score", (nc,)), float(value), int(rare), _stream(stream))
     _check(rc, "uvc_mark_best")
     return score
 

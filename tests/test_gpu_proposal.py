@@ -217,18 +217,25 @@ def test_feature_columns_share_one_buffer():
     sc.free()
 
 
-@pytest.mark.parametrize("nc,np_", [(1, 5), (40, 300), (3000, 257), (9, 0)])
-def test_mark_best_bit_exact(nc, np_):
+@pytest.mark.parametrize("nc,np_,rare", [(1, 5, 0), (40, 300, 0), (3000, 257, 0), (9, 0, 0), (40, 300, 3),
+                                         (3000, 257, 2)])
+def test_mark_best_bit_exact(nc, np_, rare):
     rng = np.random.default_rng(nc + 3 * np_)
     A = rng.integers(0, 5, (nc, np_)).astype(np.float32)    # many ties
     if np_:
         A[:, 0] = 0.0                                        # an unlit patch marks nothing
+    if np_ > 10:
+        for j in range(1, 8):                                # patches lit by j candidates only
+            A[:, j] = 0.0
+            A[rng.choice(nc, min(j, nc), replace=False), j] = 2.0
     score = rng.standard_normal(nc).astype(np.float32)
-    got = uvc.mark_best(T(A), T(score), value=9.5).cpu().numpy()
+    got = uvc.mark_best(T(A), T(score), value=9.5, rare=rare).cpu().numpy()
     want = score.copy()
     for j in range(np_):
         if A[:, j].max() > 0:
             want[int(np.argmax(A[:, j]))] = 9.5              # first maximum = lowest index
+            if (A[:, j] > 0).sum() <= rare:
+                want[A[:, j] > 0] = 9.5
     np.testing.assert_array_equal(got, want)
 
 
@@ -265,3 +272,17 @@ def test_learned_selection_keeps_best_sources():
     assert 0.0 <= lost <= 1.0
     scorer.close()
     sc.free()
+
+
+@pytest.mark.parametrize("n,group", [(1, 10), (95, 10), (1000, 7), (333, 1)])
+def test_group_boost_bit_exact(n, group):
+    rng = np.random.default_rng(n + group)
+    score = rng.integers(-3, 3, n).astype(np.float32)        # ties within groups
+    score[rng.uniform(size=n) < 0.05] = np.nan
+    got = uvc.group_boost(T(score), group, bonus=1000.0).cpu().numpy()
+    want = score.copy()
+    for g0 in range(0, n, group):
+        seg = np.where(np.isnan(score[g0:g0 + group]), -np.inf, score[g0:g0 + group])
+        w = g0 + int(np.argmax(seg))                          # first maximum
+        want[w] = np.float32(score[w] + np.float32(1000.0))
+    np.testing.assert_array_equal(got, want)
