@@ -38,11 +38,22 @@ UNIT = "Gpairs/s"
 MU_MIN = 100.0          # 10 mJ/cm^2
 NVEC = 16
 L2_BYTES = 129 * 2 ** 20
-# ALU work per segment operation (FP32 arithmetic, min/max and compare
-# instructions of the kernels, per lane): see the design doc for the count.
+# ALU work per operation of the traversal (FP32 arithmetic, min/max, compare
+# and predicate-combining instructions of the kernels, per lane):
+#   segment box test: 6 subtractions, 6 multiplications, 2 three-way near/far
+#     combinations, 2 clamps, the far scaling and the comparison = 18
+#   triangle test: the watertight segment test = 40
+#   segment set-up: TwoSum, error-free dot product, ray set-up, Eq. (7) term = 60
+#   wedge box test: 4 subtractions, 4 multiplications, two three-way
+#     combinations (2 each), 4 FMAs for the z bounds at both ends, 1 min,
+#     1 max, 3 comparisons, 2 ANDs = 23
+#   wedge plane test: 3 vertices x (2 subtractions, 1 multiplication, 1 FMA),
+#     6 comparisons, 4 ANDs/ORs = 22
 OPS_BOX_TEST = 18
 OPS_TRI_TEST = 40
 OPS_SEGMENT_SETUP = 60
+OPS_WEDGE_BOX_TEST = 23
+OPS_WEDGE_PLANE_TEST = 22
 
 
 def parse():
@@ -284,7 +295,8 @@ def run_ours(args):
         cnt = uvc.irradiance_counters(sc, d["cand"], lamp, A=A)
         segments = pairs * s.lamp.K
         ops = (cnt["lane_box_tests"] * OPS_BOX_TEST + cnt["lane_tri_tests"] * OPS_TRI_TEST
-               + segments * OPS_SEGMENT_SETUP)
+               + segments * OPS_SEGMENT_SETUP + cnt["lane_wedge_box_tests"] * OPS_WEDGE_BOX_TEST
+               + cnt["lane_wedge_plane_tests"] * OPS_WEDGE_PLANE_TEST)
         irr_s = (sum(irr_ms) / len(irr_ms)) * 1e-3
         pk = measured_peaks()
         sm_max = float(pk.get("sm_max_mhz", 2070.0))

@@ -129,6 +129,23 @@ int uvc_build_scene_ex(const float* verts, int64_t nv, const int32_t* tris, int6
 int uvc_free_scene(uvc_scene* scene);
 
 /*
+ * uvc_set_wedge_traversal - how the K sources of a vertical line lamp are
+ * searched (process-wide; default 1).  Sec. IV-C ("Non-Point Light Sources")
+ * approximates a line light by point sources evenly spread along it; when
+ * every offset of a lamp is vertical (x = y = 0) and 2 <= K <= 16, all
+ * sources of a candidate lie on one vertical line, so the K segments to a
+ * patch point lie in one triangle (the wedge).  With 1, the matrix, streamed
+ * and batched calls search that wedge once per (candidate, patch) and test
+ * each triangle it reaches against every source still searching; with 0,
+ * every source is searched on its own.  Both give the visibility of Eq. (7)
+ * source by source with the same segment test; they can differ only where a
+ * segment grazes a triangle lying in the patch's own plane.  The setting is
+ * read when a call (or uvc_batch_create) converts its lamp.
+ * Returns the previous setting (0 or 1), or UVC_E_INVAL for other values.
+ */
+int uvc_set_wedge_traversal(int32_t enable);
+
+/*
  * uvc_irradiance_matrix - the irradiance matrix (Sec. IV-C, Eq. (4) and (7)):
  *
  *   A[i][j] = sum_m  w_m P <o_im - s_j, n_j> / (4 pi |o_im - s_j|^3) * V_ijm
@@ -156,14 +173,17 @@ int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc,
 /*
  * uvc_irradiance_counters - the same computation as uvc_irradiance_matrix
  * (writes A, no visibility words) with traversal instrumentation, for
- * profiling and for the benchmark's algorithmic byte count; slower than the
- * plain call because of the counting atomics.  Synchronises `stream`.
- *   counters  HOST uint64[6]: [0] node visits (per warp packet), [1] leaf
+ * profiling and for the benchmark's algorithmic operation count; slower than
+ * the plain call because of the counting atomics.  Synchronises `stream`.
+ *   counters  HOST uint64[8]: [0] node visits (per warp packet), [1] leaf
  *             triangle loads (per warp packet), [2] packet traversals,
  *             [3] per-segment box tests, [4] per-segment triangle tests,
- *             [5] facing segments (those that needed a search)
+ *             [5] facing segments that needed a search, [6] per-lane wedge
+ *             box tests, [7] per-lane wedge plane tests
  * A packet is one warp: 32 patches and one lamp source (Sec. IV-C: each
- * segment is one source-to-patch visibility query of Eq. (7)).
+ * segment is one source-to-patch visibility query of Eq. (7)), or, for a
+ * vertical line lamp on the wedge path, 32 patches and all K sources of one
+ * candidate (see uvc_set_wedge_traversal).
  */
 int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp,
                             float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream);

@@ -1,5 +1,6 @@
 // extern "C" entry points of libuvc: argument checks, lamp conversion, and
 // dispatch to the kernels.  See include/uvc.h for the contract of each call.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -29,6 +30,10 @@ const int64_t kLimit = int64_t(1) << 31;
 
 bool count_ok(int64_t n) { return n >= 0 && n < kLimit; }
 
+std::atomic<int> g_wedge{1};
+
+}  // namespace
+
 int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
     if (!lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES) return UVC_E_INVAL;
     if (!std::isfinite(lamp->power) || lamp->power < 0.f) return UVC_E_INVAL;
@@ -44,10 +49,12 @@ int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
         out->oz[m] = lamp->offsets[m][2];
         out->pw[m] = w * lamp->power;   // source power w_m P (one FP32 rounding)
     }
+    bool vertical = lamp->K >= 2 && lamp->K <= kWedgeMaxK;
+    for (int m = 0; m < lamp->K && vertical; ++m) vertical = out->ox[m] == 0.f && out->oy[m] == 0.f;
+    out->wedge = vertical && g_wedge.load(std::memory_order_relaxed) ? 1 : 0;
     return UVC_OK;
 }
 
-}  // namespace
 }  // namespace uvc
 
 extern "C" {
@@ -72,6 +79,11 @@ int uvc_free_scene(uvc_scene* scene) {
     if (scene->block) cudaFree(scene->block);
     delete scene;
     return uvc::status_from_cuda(e);
+}
+
+int uvc_set_wedge_traversal(int32_t enable) {
+    if (enable != 0 && enable != 1) return UVC_E_INVAL;
+    return uvc::g_wedge.exchange(enable);
 }
 
 int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp, float* A,

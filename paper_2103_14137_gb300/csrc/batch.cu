@@ -33,13 +33,18 @@ struct JobDev {
     int nc, lamp, nchunk, njb;
 };
 
-template <int CPT>
+// Lamps with the wedge path (LampDev::wedge) use the per-source shared
+// arrays, sized for the batch's largest such lamp (wedge_k).  MODE: 0 = no
+// lamp of the batch takes the wedge path, 1 = all do, 2 = mixed (chosen per
+// job; both paths inlined).
+template <int CPT, int MODE>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     k_irradiance_batch(const JobDev* __restrict__ jobs, int njobs, const LampDev* __restrict__ lamps,
-                       int64_t task_lo, int64_t task_hi, int stack_cap) {
-    extern __shared__ int smem[];
+                       int64_t task_lo, int64_t task_hi, int stack_cap, int wedge_k) {
+    extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * stack_cap;
+    const WedgeSmem ws = wedge_smem(reinterpret_cast<char*>(smem) + stack_smem_bytes(stack_cap), wedge_k, warp);
     for (int64_t task = task_lo + (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < task_hi;
          task += (int64_t)gridDim.x * kWarpsPerBlock) {
         int lo = 0, hi = njobs - 1;   // last job starting at or before `task`
@@ -54,23 +59,32 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
         const PatchLane P = load_patch(J.S, j);
         int cache = -1;
         const int i1 = min(J.nc, (ic + 1) * CPT);
+        const LampDev& L = lamps[J.lamp];
         for (int i = ic * CPT; i < i1; ++i) {
-            const float E = irradiance_entry<false>(J.S, J.cand, J.nc, lamps[J.lamp], i, jb, lane, stack, J.vis,
-                                                    J.njb, P, cache);
+            const bool wedge = MODE == 1 || (MODE == 2 && L.wedge);
+            const float E = wedge ? irradiance_wedge<false>(J.S, J.cand, J.nc, L, i, jb, lane, stack, ws, J.vis,
+                                                            J.njb, P, cache)
+                                  : irradiance_entry<false>(J.S, J.cand, J.nc, L, i, jb, lane, stack, J.vis,
+                                                            J.njb, P, cache);
             if (P.valid) J.A[(size_t)i * J.lda + j] = E;
         }
     }
 }
 
-using BatchKernel = void (*)(const JobDev*, int, const LampDev*, int64_t, int64_t, int);
+using BatchKernel = void (*)(const JobDev*, int, const LampDev*, int64_t, int64_t, int, int);
 
-BatchKernel kernel_for(int cpt) {
+template <int MODE>
+BatchKernel kernel_for_mode(int cpt) {
     switch (cpt) {
-        case 2: return k_irradiance_batch<2>;
-        case 4: return k_irradiance_batch<4>;
-        case 16: return k_irradiance_batch<16>;
-        default: return k_irradiance_batch<8>;
+        case 2: return k_irradiance_batch<2, MODE>;
+        case 4: return k_irradiance_batch<4, MODE>;
+        case 16: return k_irradiance_batch<16, MODE>;
+        default: return k_irradiance_batch<8, MODE>;
     }
+}
+
+BatchKernel kernel_for(int cpt, int mode) {
+    return mode == 0 ? kernel_for_mode<0>(cpt) : (mode == 1 ? kernel_for_mode<1>(cpt) : kernel_for_mode<2>(cpt));
 }
 
 bool valid_cpt(int c) { return c == 2 || c == 4 || c == 8 || c == 16; }
@@ -87,6 +101,8 @@ struct uvc_batch {
     uvc::JobDev* dev_jobs = nullptr;      // in the caller's workspace
     uvc::LampDev* dev_lamps = nullptr;
     int stack_cap = 1;
+    int wedge_k = 0;                      // largest K among the lamps with the wedge path
+    int mode = 0;                         // kernel variant: 0 no wedge lamp, 1 all wedge, 2 mixed
     int64_t total_pairs = 0;
     int uploaded_cpt = 0;                 // cand_per_task of the uploaded table
     uvc_batch_config tuned{8, 0};        // configuration used by uvc_batch_launch
@@ -118,8 +134,12 @@ int upload(uvc_batch* b, int cpt, cudaStream_t stream, int64_t* total_tasks) {
 
 int launch_range(const uvc_batch* b, int cpt, int blocks_per_sm, int64_t lo, int64_t hi, cudaStream_t stream) {
     if (hi <= lo) return UVC_OK;
-    BatchKernel k = kernel_for(cpt);
-    const size_t smem = sizeof(int) * kWarpsPerBlock * b->stack_cap;
+    BatchKernel k = kernel_for(cpt, b->mode);
+    const size_t smem = stack_smem_bytes(b->stack_cap) + wedge_smem_bytes(b->wedge_k);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, kThreads, smem) != cudaSuccess ||
         per_sm < 1)
@@ -128,7 +148,7 @@ int launch_range(const uvc_batch* b, int cpt, int blocks_per_sm, int64_t lo, int
     int64_t grid = (int64_t)per_sm * sm_count();
     const int64_t warps_needed = (hi - lo + kWarpsPerBlock - 1) / kWarpsPerBlock;
     grid = std::max<int64_t>(1, std::min(grid, warps_needed));
-    k<<<(int)grid, kThreads, smem, stream>>>(b->dev_jobs, b->njobs, b->dev_lamps, lo, hi, b->stack_cap);
+    k<<<(int)grid, kThreads, smem, stream>>>(b->dev_jobs, b->njobs, b->dev_lamps, lo, hi, b->stack_cap, b->wedge_k);
     return status_from_cuda(cudaGetLastError());
 }
 
@@ -170,21 +190,13 @@ int uvc_batch_create(const uvc_job* jobs, int32_t njobs, const uvc_lamp* lamps, 
     b->nlamps = nlamps;
     b->host_lamps.resize(nlamps);
     for (int l = 0; l < nlamps; ++l) {
-        const uvc_lamp* L = &lamps[l];
-        if (L->K < 1 || L->K > UVC_MAX_SOURCES || !std::isfinite(L->power) || L->power < 0.f) { delete b; return UVC_E_INVAL; }
         uvc::LampDev& D = b->host_lamps[l];
-        std::memset(&D, 0, sizeof(D));
-        D.K = L->K;
-        for (int m = 0; m < L->K; ++m) {
-            if (!std::isfinite(L->weight[m]) || L->weight[m] < 0.f) { delete b; return UVC_E_INVAL; }
-            for (int k = 0; k < 3; ++k)
-                if (!std::isfinite(L->offsets[m][k])) { delete b; return UVC_E_INVAL; }
-            D.ox[m] = L->offsets[m][0];
-            D.oy[m] = L->offsets[m][1];
-            D.oz[m] = L->offsets[m][2];
-            D.pw[m] = L->weight[m] * L->power;
-        }
+        if (uvc::lamp_to_device(&lamps[l], &D) != UVC_OK) { delete b; return UVC_E_INVAL; }
+        if (D.wedge) b->wedge_k = std::max(b->wedge_k, D.K);
     }
+    int nwedge = 0;
+    for (const auto& D : b->host_lamps) nwedge += D.wedge ? 1 : 0;
+    b->mode = nwedge == 0 ? 0 : (nwedge == nlamps ? 1 : 2);
     b->host_jobs.resize(njobs);
     b->pairs.resize(njobs);
     int maxcap = 1;

@@ -36,13 +36,15 @@ namespace {
 // cache) over this many consecutive candidates.
 constexpr int kCandPerTask = 8;
 
-template <bool COUNT>
+template <bool COUNT, bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,
                                                          LampDev L, float* __restrict__ A, int64_t lda,
                                                          uint32_t* __restrict__ vis, unsigned long long* ctr) {
-    extern __shared__ int smem[];
+    extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
+    WedgeSmem ws;
+    if (WEDGE) ws = wedge_smem(reinterpret_cast<char*>(smem) + stack_smem_bytes(S.stack_cap), L.K, warp);
     const int njb = (S.np + 31) >> 5;
     const int nchunk = (nc + kCandPerTask - 1) / kCandPerTask;
     const int64_t ntask = (int64_t)nchunk * njb;
@@ -54,7 +56,9 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(Sce
         int cache = -1;
         const int i1 = min(nc, (ic + 1) * kCandPerTask);
         for (int i = ic * kCandPerTask; i < i1; ++i) {
-            const float E = irradiance_entry<COUNT>(S, cand, nc, L, i, jb, lane, stack, vis, njb, P, cache, ctr);
+            const float E =
+                WEDGE ? irradiance_wedge<COUNT>(S, cand, nc, L, i, jb, lane, stack, ws, vis, njb, P, cache, ctr)
+                      : irradiance_entry<COUNT>(S, cand, nc, L, i, jb, lane, stack, vis, njb, P, cache, ctr);
             if (P.valid) A[(size_t)i * lda + j] = E;
         }
     }
@@ -63,13 +67,17 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(Sce
 // Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
 // E values of up to 32 candidates are staged in shared memory, multiplied by
 // the dwell times and added to the chunk's partial sums partial[s][v][j].
+template <bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,
                                                        float* __restrict__ partial, int nsplit, int chunk) {
-    extern __shared__ int smem[];
+    extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
-    float* Et = reinterpret_cast<float*>(smem + kWarpsPerBlock * S.stack_cap) + warp * 32 * 32;
+    char* after_stacks = reinterpret_cast<char*>(smem) + stack_smem_bytes(S.stack_cap);
+    float* Et = reinterpret_cast<float*>(after_stacks) + warp * 32 * 32;
+    WedgeSmem ws;
+    if (WEDGE) ws = wedge_smem(after_stacks + sizeof(float) * kWarpsPerBlock * 32 * 32, L.K, warp);
     const int njb = (S.np + 31) >> 5;
     const int64_t ntask = (int64_t)nsplit * njb;
     for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
@@ -82,7 +90,9 @@ __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(
         for (int ib = i0; ib < i1; ib += 32) {
             const int nb = min(32, i1 - ib);
             for (int q = 0; q < nb; ++q)
-                Et[q * 32 + lane] = irradiance_entry(S, cand, nc, L, ib + q, jb, lane, stack, nullptr, 0, P, cache);
+                Et[q * 32 + lane] =
+                    WEDGE ? irradiance_wedge(S, cand, nc, L, ib + q, jb, lane, stack, ws, nullptr, 0, P, cache)
+                          : irradiance_entry(S, cand, nc, L, ib + q, jb, lane, stack, nullptr, 0, P, cache);
             __syncwarp();
             if (j < S.np) {
                 for (int v = 0; v < nvec; ++v) {
@@ -121,19 +131,65 @@ int grid_for(const void* kernel, size_t smem) {
     return per_sm * sm_count();
 }
 
+
+// Dynamic shared memory above 48 KiB must be opted into per kernel.
+int allow_smem(const void* kernel, size_t smem) {
+    if (smem <= 48 * 1024) return UVC_OK;
+    return status_from_cuda(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+
+// k_streamed for this lamp: shared memory, grid, launch.
+size_t streamed_smem(const SceneView& S, const LampDev& lamp) {
+    return stack_smem_bytes(S.stack_cap) + sizeof(float) * kWarpsPerBlock * 32 * 32 +
+           (lamp.wedge ? wedge_smem_bytes(lamp.K) : 0);
+}
+
+const void* streamed_kernel(const LampDev& lamp) {
+    return lamp.wedge ? (const void*)k_streamed<true> : (const void*)k_streamed<false>;
+}
+
+int streamed_grid(const SceneView& S, const LampDev& lamp, int* grid) {
+    const int rc = allow_smem(streamed_kernel(lamp), streamed_smem(S, lamp));
+    *grid = grid_for(streamed_kernel(lamp), streamed_smem(S, lamp));
+    return rc;
+}
+
+void launch_streamed(int grid, const SceneView& S, const float* cand, int64_t nc, const LampDev& lamp,
+                     const float* t, int32_t nvec, float* partial, int64_t nsplit, int chunk, cudaStream_t stream) {
+    const size_t smem = streamed_smem(S, lamp);
+    if (lamp.wedge)
+        k_streamed<true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit,
+                                                           chunk);
+    else
+        k_streamed<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit,
+                                                            chunk);
+}
+
+template <bool COUNT>
+int launch_irradiance(const SceneView& S, const float* cand, int64_t nc, const LampDev& lamp, float* A, int64_t lda,
+                      uint32_t* vis, unsigned long long* ctr, cudaStream_t stream) {
+    const bool wedge = lamp.wedge != 0;
+    const size_t smem = stack_smem_bytes(S.stack_cap) + (wedge ? wedge_smem_bytes(lamp.K) : 0);
+    const void* kern = wedge ? (const void*)k_irradiance<COUNT, true> : (const void*)k_irradiance<COUNT, false>;
+    int rc = allow_smem(kern, smem);
+    if (rc != UVC_OK) return rc;
+    const int njb = (S.np + 31) / 32;
+    const int64_t ntask = ((nc + kCandPerTask - 1) / kCandPerTask) * njb;
+    int grid = grid_for(kern, smem);
+    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (wedge)
+        k_irradiance<COUNT, true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, vis, ctr);
+    else
+        k_irradiance<COUNT, false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, vis, ctr);
+    return status_from_cuda(cudaGetLastError());
+}
+
 }  // namespace
 
 int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
                       int64_t lda, uint32_t* vis, cudaStream_t stream) {
     if (nc == 0 || sc->np == 0) return UVC_OK;
-    SceneView S = view_of(sc);
-    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
-    const int njb = (S.np + 31) / 32;
-    const int64_t ntask = ((nc + kCandPerTask - 1) / kCandPerTask) * njb;
-    int grid = grid_for((const void*)k_irradiance<false>, smem);
-    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_irradiance<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, vis, nullptr);
-    return status_from_cuda(cudaGetLastError());
+    return launch_irradiance<false>(view_of(sc), cand, nc, lamp, A, lda, vis, nullptr, stream);
 }
 
 int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
@@ -141,20 +197,15 @@ int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, cons
     for (int k = 0; k < kNumCounters; ++k) out6[k] = 0;
     if (nc == 0 || sc->np == 0) return UVC_OK;
     SceneView S = view_of(sc);
-    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
     unsigned long long* dctr = nullptr;
     if (cudaMallocAsync(&dctr, sizeof(unsigned long long) * kNumCounters, stream) != cudaSuccess) {
         cudaGetLastError();
         return UVC_E_NOMEM;
     }
     cudaError_t e = cudaMemsetAsync(dctr, 0, sizeof(unsigned long long) * kNumCounters, stream);
-    const int njb = (S.np + 31) / 32;
-    const int64_t ntask = ((nc + kCandPerTask - 1) / kCandPerTask) * njb;
-    int grid = grid_for((const void*)k_irradiance<true>, smem);
-    if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
     if (e == cudaSuccess) {
-        k_irradiance<true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, A, lda, nullptr, dctr);
-        e = cudaGetLastError();
+        const int rc = launch_irradiance<true>(S, cand, nc, lamp, A, lda, nullptr, dctr, stream);
+        if (rc != UVC_OK) e = cudaErrorLaunchFailure;
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out6, dctr, sizeof(unsigned long long) * kNumCounters, cudaMemcpyDeviceToHost, stream);
@@ -168,9 +219,10 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
     if (sc->np == 0) return UVC_OK;
     SceneView S = view_of(sc);
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)nvec * S.np, stream));
-    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap + sizeof(float) * kWarpsPerBlock * 32 * 32;
     const int njb = (S.np + 31) / 32;
-    int grid = grid_for((const void*)k_streamed, smem);
+    int grid = 0;
+    int rc = streamed_grid(S, lamp, &grid);
+    if (rc != UVC_OK) return rc;
     // enough (chunk, block) tasks to fill the persistent grid several times over
     const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
     int64_t nsplit = (want + njb - 1) / njb;
@@ -186,7 +238,7 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
     }
     const int64_t ntask = nsplit * njb;
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_streamed<<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit, chunk);
+    launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk, stream);
     const int64_t total = (int64_t)nvec * S.np;
     k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
     cudaError_t e = cudaGetLastError();
@@ -256,9 +308,10 @@ int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc,
     if (rc != UVC_OK) return rc;
     SceneView S = view_of(sc);
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, per_split, stream));
-    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap + sizeof(float) * kWarpsPerBlock * 32 * 32;
     const int njb = (S.np + 31) / 32;
-    int grid = grid_for((const void*)k_streamed, smem);
+    int grid = 0;
+    rc = streamed_grid(S, lamp, &grid);
+    if (rc != UVC_OK) return rc;
     const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
     int64_t nsplit = (want + njb - 1) / njb;
     nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (nc + 31) / 32));
@@ -268,7 +321,7 @@ int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc,
     const int64_t ntask = nsplit * njb;
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
     // every partial is written before it is read, so the array needs no clearing
-    k_streamed<<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit, chunk);
+    launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk, stream);
     const int64_t total = (int64_t)nvec * S.np;
     k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
     return status_from_cuda(cudaGetLastError());

@@ -101,30 +101,36 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
 
 // Watertight segment/triangle test: hit iff the segment's line passes through
 // the closed triangle (all edge functions of one sign, non-degenerate) and
-// the parameter tau = T/det lies in the open interval (0, 1).
-__device__ __forceinline__ bool seg_tri(const Ray& r, float4 a, float4 b, float4 c) {
-    float Ax = __fsub_rn(a.x, r.ox), Ay = __fsub_rn(a.y, r.oy), Az = __fsub_rn(a.z, r.oz);
-    float Bx = __fsub_rn(b.x, r.ox), By = __fsub_rn(b.y, r.oy), Bz = __fsub_rn(b.z, r.oz);
-    float Cx = __fsub_rn(c.x, r.ox), Cy = __fsub_rn(c.y, r.oy), Cz = __fsub_rn(c.z, r.oz);
-    float akz = pick(Ax, Ay, Az, r.kz), bkz = pick(Bx, By, Bz, r.kz), ckz = pick(Cx, Cy, Cz, r.kz);
-    float ax = __fmaf_rn(-r.sx, akz, pick(Ax, Ay, Az, r.kx));
-    float ay = __fmaf_rn(-r.sy, akz, pick(Ax, Ay, Az, r.ky));
-    float bx = __fmaf_rn(-r.sx, bkz, pick(Bx, By, Bz, r.kx));
-    float by = __fmaf_rn(-r.sy, bkz, pick(Bx, By, Bz, r.ky));
-    float cx = __fmaf_rn(-r.sx, ckz, pick(Cx, Cy, Cz, r.kx));
-    float cy = __fmaf_rn(-r.sy, ckz, pick(Cx, Cy, Cz, r.ky));
+// the parameter tau = T/det lies in the open interval (0, 1).  The segment is
+// given by its start (ox, oy, oz) and the shear constants of setup_ray.
+__device__ __forceinline__ bool seg_tri_k(float ox, float oy, float oz, int kx, int ky, int kz, float sx, float sy,
+                                          float sz, float4 a, float4 b, float4 c) {
+    float Ax = __fsub_rn(a.x, ox), Ay = __fsub_rn(a.y, oy), Az = __fsub_rn(a.z, oz);
+    float Bx = __fsub_rn(b.x, ox), By = __fsub_rn(b.y, oy), Bz = __fsub_rn(b.z, oz);
+    float Cx = __fsub_rn(c.x, ox), Cy = __fsub_rn(c.y, oy), Cz = __fsub_rn(c.z, oz);
+    float akz = pick(Ax, Ay, Az, kz), bkz = pick(Bx, By, Bz, kz), ckz = pick(Cx, Cy, Cz, kz);
+    float ax = __fmaf_rn(-sx, akz, pick(Ax, Ay, Az, kx));
+    float ay = __fmaf_rn(-sy, akz, pick(Ax, Ay, Az, ky));
+    float bx = __fmaf_rn(-sx, bkz, pick(Bx, By, Bz, kx));
+    float by = __fmaf_rn(-sy, bkz, pick(Bx, By, Bz, ky));
+    float cx = __fmaf_rn(-sx, ckz, pick(Cx, Cy, Cz, kx));
+    float cy = __fmaf_rn(-sy, ckz, pick(Cx, Cy, Cz, ky));
     float U = __fsub_rn(__fmul_rn(cx, by), __fmul_rn(cy, bx));
     float V = __fsub_rn(__fmul_rn(ax, cy), __fmul_rn(ay, cx));
     float W = __fsub_rn(__fmul_rn(bx, ay), __fmul_rn(by, ax));
     if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
     float det = U + V + W;
     if (det == 0.f) return false;
-    float T = U * __fmul_rn(r.sz, akz) + V * __fmul_rn(r.sz, bkz) + W * __fmul_rn(r.sz, ckz);
+    float T = U * __fmul_rn(sz, akz) + V * __fmul_rn(sz, bkz) + W * __fmul_rn(sz, ckz);
     // tau = T / det in (0, 1), compared without dividing
     unsigned sgn = __float_as_uint(det) & 0x80000000u;
     float Ts = __uint_as_float(__float_as_uint(T) ^ sgn);
     float ds = __uint_as_float(__float_as_uint(det) ^ sgn);
     return Ts > 0.f && Ts < ds;
+}
+
+__device__ __forceinline__ bool seg_tri(const Ray& r, float4 a, float4 b, float4 c) {
+    return seg_tri_k(r.ox, r.oy, r.oz, r.kx, r.ky, r.kz, r.sx, r.sy, r.sz, a, b, c);
 }
 
 __device__ __forceinline__ uint32_t test_leaf(const SceneView& S, int k, const Ray& r, uint32_t mask, int lane) {
@@ -137,9 +143,10 @@ __device__ __forceinline__ uint32_t test_leaf(const SceneView& S, int k, const R
 
 // Traversal counters of the instrumented variant (one launch, outside timing):
 // [0] warp node visits, [1] warp leaf tests, [2] warp traversals,
-// [3] lane box tests (alive lanes x 4 per node), [4] lane triangle tests,
-// [5] facing segments.
-constexpr int kNumCounters = 6;
+// [3] lane segment box tests (alive lanes x 4 per node), [4] lane triangle
+// tests (one segment against one triangle), [5] facing segments, [6] lane
+// wedge box tests, [7] lane wedge plane tests (see the wedge traversal).
+constexpr int kNumCounters = 8;
 
 // Both boxes of a child pair (packed FP32x2).  Each lane loads, per axis, the
 // pair of planes its segment meets first (near) and last (far): the near
@@ -378,6 +385,394 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
         if ((visible >> lane) & 1u) {
             E = __fadd_rn(E, __fmul_rn(L.pw[m], __fdiv_rn(nv, __fmul_rn(__fmul_rn(kFourPi, d2), d))));
         }
+    }
+    return bad ? __int_as_float(0x7fffffff) : E;
+}
+
+// ---------------------------------------------------------------------------
+// Wedge traversal for vertical line lamps
+// ---------------------------------------------------------------------------
+// When every source offset is vertical (x = y = 0), the sources of candidate
+// c are o_m = (c.x, c.y, fl32(c.z + off_m.z)), all on the vertical line
+// through c, and the segments from them to a patch point s lie in one
+// triangle, the wedge conv(o_lo, o_hi, s) (o_lo, o_hi: the lowest and highest
+// source still searching).  One packet traversal of the wedges replaces the K
+// segment traversals: a child box is entered when it meets the lane's wedge,
+// widened by delta, and every triangle reached is tested, with the same
+// watertight segment test, against each source still searching; a source
+// stops at its first hit, a lane when all its sources have stopped, and the
+// wedge narrows as its outer sources stop.
+//
+// Every triangle that a source's own segment traversal would reach is reached
+// here (each segment lies inside the wedge, and delta = 1e-5 D exceeds the
+// segment box test's widening), so each source gets the result of its own
+// traversal; the only exception would be a triangle hit inside the patch's
+// clearance, which only a triangle in the patch's own plane touching the
+// patch point can be (a grazing pair).
+//
+// Coordinates: the horizontal part g of every segment of the lane is the same
+// (the ray direction's x and y, rounded once in the set-up), so the point at
+// segment parameter tau lies above c.xy + tau g whatever the source, and
+// lambda = tau is a common parameter.  At lambda the wedge spans
+//   zlow(lambda)  = z_lo + lambda (s.z - z_lo)  to
+//   zhigh(lambda) = z_hi + lambda (s.z - z_hi).
+// A box (widened by delta) meets the wedge iff its x and y slabs leave a
+// lambda interval [a, b] inside [0, lambda_end] with z1 >= min(zlow(a),
+// zlow(b)) and z0 <= max(zhigh(a), zhigh(b)) (both bounds are linear in
+// lambda).  lambda_end is the largest clearance cut (tend) of the lane's
+// searching sources.
+
+struct WedgeLane {
+    float2 oxn, oxf, oyn, oyf;   // -(c.x + delta sgn g.x), -(c.x - delta sgn g.x), same in y
+    float2 igx, igy;             // 1/g.x, 1/g.y (as safe_rcp)
+    float2 zl, zh, sl, sh;       // z_lo - delta, z_hi + delta, s.z - z_lo, s.z - z_hi
+    float lend;                  // lambda_end
+    float ig2;                   // 1 / |g|^2
+    float mz;                    // delta * (longest segment) / |g|: margin of lamp_interval before 1/(1 - lambda)
+    int onx, ony;                // byte offsets of the near planes in an axis record
+};
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
+// z range of the searching sources `want` (bit m = source m).
+__device__ __forceinline__ void wedge_z(WedgeLane& w, uint32_t want, float cz, const LampDev& L, float sz,
+                                        float delta) {
+    float zlo = 3.0e38f, zhi = -3.0e38f;
+    for (uint32_t b = want; b; b &= b - 1) {
+        const float oz = __fadd_rn(cz, L.oz[__ffs(b) - 1]);
+        zlo = fminf(zlo, oz);
+        zhi = fmaxf(zhi, oz);
+    }
+    w.zl = dup2(zlo - delta);
+    w.zh = dup2(zhi + delta);
+    w.sl = dup2(sz - zlo);
+    w.sh = dup2(sz - zhi);
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// The sources of `want` whose segment can meet triangle (a, b, c).  Project
+// the triangle orthogonally onto the wedge's vertical plane (the projection
+// holds every point where the triangle meets the plane, and a segment that
+// passes within e of the triangle passes within e of the projection) and then
+// centrally from s onto the lamp line: a segment from height z meets the
+// projection iff z lies in the image, which is the interval spanned by the
+// images z_s + (z_V - z_s) / (1 - lambda_V) of the three vertices while all
+// lambda_V < 1.  The interval is widened by mz / (1 - lambda_max): a
+// displacement e of a segment at parameter lambda moves its lamp end by at
+// most e |d| / (|g| (1 - lambda)), and mz = delta |d|max / |g| with delta
+// far above the rounding of the segment test and of this projection.  A
+// triangle reaching lambda >= 1 - 2^-10 (next to s or beyond) keeps every
+// source, as does a degenerate g (NaN comparisons fail).
+__device__ __forceinline__ uint32_t lamp_interval(const WedgeLane& w, uint32_t want, float4 a, float4 b, float4 c,
+                                                  float cx, float cy, float cz, float sz, float gx, float gy,
+                                                  const LampDev& L) {
+    const float la = __fmul_rn(__fmaf_rn(__fsub_rn(a.x, cx), gx, __fmul_rn(__fsub_rn(a.y, cy), gy)), w.ig2);
+    const float lb = __fmul_rn(__fmaf_rn(__fsub_rn(b.x, cx), gx, __fmul_rn(__fsub_rn(b.y, cy), gy)), w.ig2);
+    const float lc = __fmul_rn(__fmaf_rn(__fsub_rn(c.x, cx), gx, __fmul_rn(__fsub_rn(c.y, cy), gy)), w.ig2);
+    const float lmax = max3f(la, lb, lc);
+    if (!(lmax < 0.9990234375f)) return want;
+    const float za = __fmaf_rn(__fsub_rn(a.z, sz), rcp_approx(__fsub_rn(1.f, la)), sz);
+    const float zb = __fmaf_rn(__fsub_rn(b.z, sz), rcp_approx(__fsub_rn(1.f, lb)), sz);
+    const float zc = __fmaf_rn(__fsub_rn(c.z, sz), rcp_approx(__fsub_rn(1.f, lc)), sz);
+    const float m = __fmul_rn(w.mz, rcp_approx(__fsub_rn(1.f, lmax)));
+    const float z0 = __fsub_rn(min3f(za, zb, zc), m), z1 = __fadd_rn(max3f(za, zb, zc), m);
+    uint32_t in = 0;
+    for (uint32_t bits = want; bits; bits &= bits - 1) {
+        const int q = __ffs(bits) - 1;
+        const float oz = __fadd_rn(cz, L.oz[q]);
+        if (oz >= z0 && oz <= z1) in |= 1u << q;
+    }
+    return in;
+}
+
+__device__ __forceinline__ void wedge_pair_hits(const WedgeLane& w, float2 nx, float2 fx, float2 ny, float2 fy,
+                                                float2 z0, float2 z1, bool& h0, bool& h1) {
+    const float2 lnx = __fmul2_rn(__fadd2_rn(nx, w.oxn), w.igx), lfx = __fmul2_rn(__fadd2_rn(fx, w.oxf), w.igx);
+    const float2 lny = __fmul2_rn(__fadd2_rn(ny, w.oyn), w.igy), lfy = __fmul2_rn(__fadd2_rn(fy, w.oyf), w.igy);
+    const float2 a = make_float2(max3f(lnx.x, lny.x, 0.f), max3f(lnx.y, lny.y, 0.f));
+    const float2 b = make_float2(min3f(lfx.x, lfy.x, w.lend), min3f(lfx.y, lfy.y, w.lend));
+    const float2 la = __ffma2_rn(a, w.sl, w.zl), lb = __ffma2_rn(b, w.sl, w.zl);
+    const float2 ha = __ffma2_rn(a, w.sh, w.zh), hb = __ffma2_rn(b, w.sh, w.zh);
+    h0 = a.x <= b.x && z1.x >= fminf(la.x, lb.x) && z0.x <= fmaxf(ha.x, hb.x);
+    h1 = a.y <= b.y && z1.y >= fminf(la.y, lb.y) && z0.y <= fmaxf(ha.y, hb.y);
+}
+
+// Per (source, lane) data of the wedge path, in shared memory (one warp's
+// slice): shear constants and axis permutation of the source's segment, and
+// its Eq. (7) term w_m P <n, v> / (4 pi |v|^3).
+struct WedgeSmem {
+    float4* shear;   // [K][32]: (sx, sy, sz, kx | ky << 2 | kz << 4)
+    float* term;     // [K][32]
+};
+
+// Shared memory of a block of the traversal kernels: the warps' stacks
+// (16-byte aligned size), then kernel-specific staging, then the wedge arrays
+// of all warps (shear of every warp, then term of every warp).
+__host__ __device__ inline size_t stack_smem_bytes(int stack_cap) {
+    return ((size_t)kWarpsPerBlock * stack_cap * sizeof(int) + 15) & ~size_t(15);
+}
+inline size_t wedge_smem_bytes(int K) { return (size_t)kWarpsPerBlock * K * 32 * (sizeof(float4) + sizeof(float)); }
+
+__device__ __forceinline__ WedgeSmem wedge_smem(char* base, int K, int warp) {
+    WedgeSmem w;
+    w.shear = reinterpret_cast<float4*>(base) + (size_t)warp * K * 32;
+    w.term = reinterpret_cast<float*>(base + (size_t)kWarpsPerBlock * K * 32 * sizeof(float4)) + (size_t)warp * K * 32;
+    return w;
+}
+
+// Lane-level wedge search.  `want` holds the lane's searching sources and
+// loses the bit of each source found occluded; `hit_tri` gets the last
+// occluding leaf.
+template <bool COUNT>
+__device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev& L, WedgeLane& w, uint32_t& want,
+                                               uint32_t alive, int* stack, int lane, const WedgeSmem& ws, float cx,
+                                               float cy, float cz, float sz, float gx, float gy, float mh, int ex0,
+                                               int ex1, uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
+    int top = 0, node = 0, visits = 0;
+    unsigned long long c_leaf = 0, c_box = 0, c_tri = 0, c_plane = 0;
+    const float delta = S.cut_eps;
+    while (true) {
+        if (++visits > S.visit_cap) {
+            failed = alive;
+            if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
+            break;
+        }
+        const Node4* nd = S.nodes4 + node;
+        const char* b = reinterpret_cast<const char*>(nd);
+        const char *bnx = b + w.onx, *bfx = b + (8 - w.onx), *bny = b + 16 + w.ony, *bfy = b + 16 + (8 - w.ony);
+        const char* bz = b + 32;
+        const int4 rr = __ldg(&nd->r);
+        const int4 mm = __ldg(&nd->m);
+        bool h0, h1, h2, h3;
+        wedge_pair_hits(w, ldg2(bnx), ldg2(bfx), ldg2(bny), ldg2(bfy), ldg2(bz), ldg2(bz + 8), h0, h1);
+        wedge_pair_hits(w, ldg2(bnx + 48), ldg2(bfx + 48), ldg2(bny + 48), ldg2(bfy + 48), ldg2(bz + 48),
+                        ldg2(bz + 56), h2, h3);
+        if (COUNT) c_box += 4 * __popc(alive);
+        const unsigned nib = ((alive >> lane) & 1u) ? (unsigned)h0 | ((unsigned)h1 << 1) | ((unsigned)h2 << 2) |
+                                                          ((unsigned)h3 << 3)
+                                                    : 0u;
+        const unsigned hit = __reduce_or_sync(kFull, nib);
+        unsigned leaves = hit & (unsigned)mm.x;
+        const bool had_leaves = leaves != 0;
+        while (leaves) {
+            const int c = __ffs(leaves) - 1;
+            leaves &= leaves - 1;
+            const uint32_t m = __ballot_sync(kFull, (nib >> c) & 1u) & alive;
+            if (!m) continue;
+            const int leaf = ~pick4(rr, c);
+            const float4* t = S.tri + 3 * (size_t)leaf;
+            const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
+            const int id = __float_as_int(ta.w);
+            if (COUNT) { ++c_leaf; c_plane += __popc(m); }
+            if (((m >> lane) & 1u) && id != ex0 && id != ex1) {
+                // triangle entirely on one side of the wedge's vertical plane,
+                // farther than delta: no segment of the lane can meet it
+                const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));
+                const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
+                const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
+                const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
+                if (!beside) {
+                    const uint32_t before = want;
+                    const uint32_t test = want & lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
+                    for (uint32_t bits = test; bits; bits &= bits - 1) {
+                        const int q = __ffs(bits) - 1;
+                        const float4 sh = ws.shear[q * 32 + lane];
+                        const int kb = __float_as_int(sh.w);
+                        if (COUNT) ++c_tri;
+                        if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), (kb >> 0) & 3, (kb >> 2) & 3, (kb >> 4) & 3,
+                                      sh.x, sh.y, sh.z, ta, tb, tc))
+                            want &= ~(1u << q);
+                    }
+                    if (want != before) {
+                        hit_tri = leaf;
+                        if (want) wedge_z(w, want, cz, L, sz, delta);
+                    }
+                }
+            }
+            alive &= __ballot_sync(kFull, want != 0u);
+        }
+        if (!alive) break;
+        unsigned inner = hit & (unsigned)mm.y;
+        if (had_leaves && inner) {
+            const unsigned nib2 = ((alive >> lane) & 1u) ? nib : 0u;
+            inner &= __reduce_or_sync(kFull, nib2);
+        }
+        if (inner) {
+            const int first = __ffs(inner) - 1;
+            if (top + 3 > S.stack_cap) {
+                failed = alive;
+                if (lane == 0) atomicCAS(S.status, 0, UVC_E_STACK);
+                break;
+            }
+            const unsigned rest = inner & (inner - 1);
+            stack[top] = rr.w; top += (rest >> 3) & 1u;
+            stack[top] = rr.z; top += (rest >> 2) & 1u;
+            stack[top] = rr.y; top += (rest >> 1) & 1u;
+            node = pick4(rr, first);
+        } else {
+            if (top == 0) break;
+            node = stack[--top];
+        }
+    }
+    if (COUNT && lane == 0) {
+        atomicAdd(&ctr[0], (unsigned long long)visits);
+        atomicAdd(&ctr[1], c_leaf);
+        atomicAdd(&ctr[2], 1ull);
+        atomicAdd(&ctr[6], c_box);
+        atomicAdd(&ctr[7], c_plane);
+    }
+    if (COUNT) {   // triangle tests are per lane
+        const unsigned long long s = __reduce_add_sync(kFull, (unsigned)c_tri);
+        if (lane == 0) atomicAdd(&ctr[4], s);
+    }
+}
+
+// Irradiance of candidate i at this lane's patch for a vertical line lamp
+// (L.wedge): the same entry as irradiance_entry, with one wedge search per
+// candidate instead of one segment search per source.
+template <bool COUNT = false>
+__device__ __forceinline__ float irradiance_wedge(const SceneView& S, const float* __restrict__ cand, int nc,
+                                                  const LampDev& L, int i, int jb, int lane, int* stack,
+                                                  const WedgeSmem& ws, uint32_t* __restrict__ vis, int nwords,
+                                                  const PatchLane& P, int& cache, unsigned long long* ctr = nullptr) {
+    const float4 s4 = P.s, n4 = P.n;
+    const float cx = __ldg(&cand[3 * (size_t)i]), cy = __ldg(&cand[3 * (size_t)i + 1]),
+                cz = __ldg(&cand[3 * (size_t)i + 2]);
+    uint32_t facing = 0, want = 0;
+    float lend = 0.f, gx = 0.f, gy = 0.f, dmax = 0.f;
+    for (int m = 0; m < L.K; ++m) {
+        // the set-up of irradiance_entry, source by source
+        const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
+        float hx = __fsub_rn(ox, s4.x), hy = __fsub_rn(oy, s4.y), hz = __fsub_rn(oz, s4.z);
+        float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
+        float lx = __fadd_rn(__fsub_rn(ox, __fsub_rn(hx, qx)), __fsub_rn(-s4.x, qx));
+        float ly = __fadd_rn(__fsub_rn(oy, __fsub_rn(hy, qy)), __fsub_rn(-s4.y, qy));
+        float lz = __fadd_rn(__fsub_rn(oz, __fsub_rn(hz, qz)), __fsub_rn(-s4.z, qz));
+        float p = __fmul_rn(n4.x, hx);
+        float err = __fmaf_rn(n4.x, hx, -p);
+        err = __fmaf_rn(n4.x, lx, err);
+        float acc = p;
+        {
+            float p2 = __fmul_rn(n4.y, hy);
+            float e2 = __fmaf_rn(n4.y, hy, -p2);
+            float s = __fadd_rn(acc, p2);
+            float z = __fsub_rn(s, acc);
+            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p2, z));
+            acc = s;
+            err = __fadd_rn(err, __fadd_rn(q, e2));
+            err = __fmaf_rn(n4.y, ly, err);
+        }
+        {
+            float p3 = __fmul_rn(n4.z, hz);
+            float e3 = __fmaf_rn(n4.z, hz, -p3);
+            float s = __fadd_rn(acc, p3);
+            float z = __fsub_rn(s, acc);
+            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p3, z));
+            acc = s;
+            err = __fadd_rn(err, __fadd_rn(q, e3));
+            err = __fmaf_rn(n4.z, lz, err);
+        }
+        const float nv = __fadd_rn(acc, err);
+        const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+        const float d = sqrtf(d2);
+        const bool fac = P.valid && nv > 0.f && d2 > 0.f;
+        Ray r;
+        r.ox = ox; r.oy = oy; r.oz = oz;
+        r.dx = -hx; r.dy = -hy; r.dz = -hz;
+        setup_ray(r);
+        const float cut = __fmaf_rn(0.99f, P.n.w, -S.cut_eps);
+        const float tend = cut > 0.f ? 1.f - cut * __frcp_rn(d) : 1.f;
+        ws.shear[m * 32 + lane] = make_float4(r.sx, r.sy, r.sz, __int_as_float(r.kx | (r.ky << 2) | (r.kz << 4)));
+        ws.term[m * 32 + lane] = fac ? __fmul_rn(L.pw[m], __fdiv_rn(nv, __fmul_rn(__fmul_rn(kFourPi, d2), d))) : 0.f;
+        if (fac) {
+            facing |= 1u << m;
+            if (tend > 0.f) {   // a segment shorter than the cut meets no triangle at all
+                want |= 1u << m;
+                lend = fmaxf(lend, tend);
+                dmax = fmaxf(dmax, d);
+            }
+        }
+        gx = r.dx;
+        gy = r.dy;
+    }
+    // the lane's last occluder first, against every searching source
+    uint32_t occl = 0;
+    if (want && cache >= 0) {
+        const float4* t = S.tri + 3 * (size_t)cache;
+        const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
+        for (uint32_t bits = want; bits; bits &= bits - 1) {
+            const int q = __ffs(bits) - 1;
+            const float4 sh = ws.shear[q * 32 + lane];
+            const int kb = __float_as_int(sh.w);
+            if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), kb & 3, (kb >> 2) & 3, (kb >> 4) & 3, sh.x, sh.y, sh.z, ta,
+                          tb, tc))
+                occl |= 1u << q;
+        }
+        want &= ~occl;
+    }
+    if (COUNT) {   // segments that need a search
+        const unsigned nseg = __reduce_add_sync(kFull, (unsigned)__popc(want));
+        if (lane == 0) atomicAdd(&ctr[5], (unsigned long long)nseg);
+    }
+    uint32_t failed = 0;
+    int hit_tri = -1;
+    const uint32_t alive = __ballot_sync(kFull, want != 0u);
+    if (alive && S.nt > 0) {
+        const uint32_t before = want;
+        if (S.root < 0) {   // a single triangle: test it directly
+            const float4* t = S.tri + 3 * (size_t)(~S.root);
+            const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
+            const int id = __float_as_int(ta.w);
+            if (id != P.ex.x && id != P.ex.y) {
+                for (uint32_t bits = want; bits; bits &= bits - 1) {
+                    const int q = __ffs(bits) - 1;
+                    const float4 sh = ws.shear[q * 32 + lane];
+                    const int kb = __float_as_int(sh.w);
+                    if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), kb & 3, (kb >> 2) & 3, (kb >> 4) & 3, sh.x, sh.y,
+                                  sh.z, ta, tb, tc))
+                        want &= ~(1u << q);
+                }
+                if (want != before) hit_tri = ~S.root;
+            }
+        } else {
+            const float delta = S.cut_eps;
+            WedgeLane w;
+            const float sgx = (__float_as_uint(gx) >> 31) ? -delta : delta;
+            const float sgy = (__float_as_uint(gy) >> 31) ? -delta : delta;
+            w.oxn = dup2(-(cx + sgx));
+            w.oxf = dup2(-(cx - sgx));
+            w.oyn = dup2(-(cy + sgy));
+            w.oyf = dup2(-(cy - sgy));
+            w.igx = dup2(safe_rcp(gx));
+            w.igy = dup2(safe_rcp(gy));
+            w.lend = lend;
+            w.onx = (int)(__float_as_uint(gx) >> 31) * 8;
+            w.ony = (int)(__float_as_uint(gy) >> 31) * 8;
+            if (want) wedge_z(w, want, cz, L, s4.z, delta);
+            const float g2 = __fmaf_rn(gx, gx, __fmul_rn(gy, gy));
+            const float gn = sqrtf(g2);
+            const float mh = delta * gn;
+            w.ig2 = 1.f / g2;
+            w.mz = delta * dmax / gn;
+            wedge_traverse<COUNT>(S, L, w, want, alive, stack, lane, ws, cx, cy, cz, s4.z, gx, gy, mh, P.ex.x, P.ex.y,
+                                  failed, ctr, hit_tri);
+        }
+        occl |= before & ~want;
+    }
+    if (hit_tri >= 0) cache = hit_tri;
+    const bool bad = (failed >> lane) & 1u;
+    const uint32_t visible = bad ? 0u : (facing & ~occl);
+    float E = 0.f;
+    for (int m = 0; m < L.K; ++m) {
+        const bool v = (visible >> m) & 1u;
+        const uint32_t word = __ballot_sync(kFull, v);
+        if (vis && lane == 0) vis[((size_t)m * nc + i) * nwords + jb] = word;
+        if (v) E = __fadd_rn(E, ws.term[m * 32 + lane]);
     }
     return bad ? __int_as_float(0x7fffffff) : E;
 }

@@ -37,12 +37,22 @@ struct __align__(16) Node4 {
     int4 m;
 };
 
+// Largest lamp for the wedge traversal of vertical line lamps (its shared
+// memory per warp grows with K).
+constexpr int kWedgeMaxK = 16;
+
 // Lamp as seen by the kernels: source offsets and source powers w_m * P.
+// wedge = 1: every offset is vertical (x = y = 0), 2 <= K <= kWedgeMaxK, and
+// the wedge traversal is switched on (uvc_set_wedge_traversal).
 struct LampDev {
     int K;
+    int wedge;
     float ox[UVC_MAX_SOURCES], oy[UVC_MAX_SOURCES], oz[UVC_MAX_SOURCES];
     float pw[UVC_MAX_SOURCES];
 };
+
+// Host: validate a lamp and convert it (api.cu).
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out);
 
 }  // namespace uvc
 

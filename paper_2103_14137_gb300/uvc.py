@@ -71,6 +71,7 @@ def library():
         "uvc_fluence_streamed_noalloc": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
         "uvc_coverage": [P, P, i32, ctypes.c_float, P, P, P],
         "uvc_scene_status": [P, P],
+        "uvc_set_wedge_traversal": [i32],
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "uvc_scene_export_bvh": [P, P, P, P, P],
     }
@@ -242,7 +243,18 @@ def irradiance_matrix(scene: Scene, cand, lamp: Lamp, A=None, vis=None, with_vis
     return A, vis
 
 
-COUNTER_NAMES = ("node_visits", "leaf_tests", "traversals", "lane_box_tests", "lane_tri_tests", "facing_segments")
+COUNTER_NAMES = ("node_visits", "leaf_tests", "traversals", "lane_box_tests", "lane_tri_tests", "facing_segments",
+                 "lane_wedge_box_tests", "lane_wedge_plane_tests")
+
+
+def set_wedge_traversal(enable: bool) -> bool:
+    """Search a vertical line lamp's sources as one wedge per (candidate,
+    patch) (True, the default) or source by source (False); returns the
+    previous setting (see uvc_set_wedge_traversal)."""
+    rc = library().uvc_set_wedge_traversal(1 if enable else 0)
+    if rc not in (0, 1):
+        _check(rc, "uvc_set_wedge_traversal")
+    return bool(rc)
 
 
 def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> dict:
@@ -250,7 +262,7 @@ def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> 
     nc = cand.shape[0]
     if A is None:
         A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
-    out = np.zeros(6, np.uint64)
+    out = np.zeros(len(COUNTER_NAMES), np.uint64)
     L = lamp._c()
     rc = library().uvc_irradiance_counters(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
                                            ctypes.byref(L), _dev(A, torch.float32, "A"), A.shape[1],

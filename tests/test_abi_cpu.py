@@ -107,3 +107,12 @@ def test_product_never_imports_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("no oracle", ""), f
+
+
+def test_wedge_switch_is_host_only(lib):
+    """uvc_set_wedge_traversal returns the previous setting and rejects other values."""
+    import paper_2103_14137_gb300 as uvc
+    assert lib.uvc_set_wedge_traversal(2) == 1          # UVC_E_INVAL
+    prev = uvc.set_wedge_traversal(False)
+    assert prev is True and uvc.set_wedge_traversal(True) is False
+    assert lib.uvc_set_wedge_traversal(1) == 1          # was on
