@@ -52,6 +52,15 @@ int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
     bool vertical = lamp->K >= 2 && lamp->K <= kWedgeMaxK;
     for (int m = 0; m < lamp->K && vertical; ++m) vertical = out->ox[m] == 0.f && out->oy[m] == 0.f;
     out->wedge = vertical && g_wedge.load(std::memory_order_relaxed) ? 1 : 0;
+    if (out->wedge) {
+        const int K = lamp->K;
+        const double z0 = out->oz[0], dz = ((double)out->oz[K - 1] - z0) / (K - 1);
+        bool even = dz > 0.0 && std::isfinite(1.0 / dz);
+        for (int m = 0; m < K && even; ++m) even = std::fabs((double)out->oz[m] - (z0 + m * dz)) <= dz / 64.0;
+        out->wuniform = even ? 1 : 0;
+        out->wz0 = (float)z0;
+        out->wrdz = even ? (float)(1.0 / dz) : 0.f;
+    }
     return UVC_OK;
 }
 

@@ -481,6 +481,15 @@ __device__ __forceinline__ uint32_t lamp_interval(const WedgeLane& w, uint32_t w
     const float zc = __fmaf_rn(__fsub_rn(c.z, sz), rcp_approx(__fsub_rn(1.f, lc)), sz);
     const float m = __fmul_rn(w.mz, rcp_approx(__fsub_rn(1.f, lmax)));
     const float z0 = __fsub_rn(min3f(za, zb, zc), m), z1 = __fadd_rn(max3f(za, zb, zc), m);
+    if (L.wuniform) {
+        // source q sits at fl32(cz + off_q), off_q within dz/64 of wz0 + q dz:
+        // every q with a height in [z0, z1] lies in [ceil(t0 - 1/32), floor(t1 + 1/32)]
+        const float t0 = fminf(fmaxf((z0 - cz - L.wz0) * L.wrdz, -4.f), 40.f);
+        const float t1 = fminf(fmaxf((z1 - cz - L.wz0) * L.wrdz, -4.f), 40.f);
+        const int qlo = max(0, (int)ceilf(t0 - 0.03125f)), qhi = min(L.K - 1, (int)floorf(t1 + 0.03125f));
+        if (qhi < qlo) return 0u;
+        return want & ((2u << qhi) - 1u) & ~((1u << qlo) - 1u);
+    }
     uint32_t in = 0;
     for (uint32_t bits = want; bits; bits &= bits - 1) {
         const int q = __ffs(bits) - 1;
@@ -700,12 +709,24 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
         gx = r.dx;
         gy = r.dy;
     }
-    // the lane's last occluder first, against every searching source
+    const float delta = S.cut_eps;
+    WedgeLane w;
+    const float g2 = __fmaf_rn(gx, gx, __fmul_rn(gy, gy));
+    const float gn = sqrtf(g2);
+    const float mh = delta * gn;   // plane margin (the plane's normal (-g.y, g.x) is not normalised)
+    w.ig2 = 1.f / g2;
+    w.mz = delta * dmax / gn;
+    // the lane's last occluder first, against the searching sources it can reach
     uint32_t occl = 0;
     if (want && cache >= 0) {
         const float4* t = S.tri + 3 * (size_t)cache;
         const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
-        for (uint32_t bits = want; bits; bits &= bits - 1) {
+        const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));
+        const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
+        const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
+        const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
+        const uint32_t test = beside ? 0u : lamp_interval(w, want, ta, tb, tc, cx, cy, cz, s4.z, gx, gy, L);
+        for (uint32_t bits = test; bits; bits &= bits - 1) {
             const int q = __ffs(bits) - 1;
             const float4 sh = ws.shear[q * 32 + lane];
             const int kb = __float_as_int(sh.w);
@@ -740,8 +761,6 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
                 if (want != before) hit_tri = ~S.root;
             }
         } else {
-            const float delta = S.cut_eps;
-            WedgeLane w;
             const float sgx = (__float_as_uint(gx) >> 31) ? -delta : delta;
             const float sgy = (__float_as_uint(gy) >> 31) ? -delta : delta;
             w.oxn = dup2(-(cx + sgx));
@@ -754,11 +773,6 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
             w.onx = (int)(__float_as_uint(gx) >> 31) * 8;
             w.ony = (int)(__float_as_uint(gy) >> 31) * 8;
             if (want) wedge_z(w, want, cz, L, s4.z, delta);
-            const float g2 = __fmaf_rn(gx, gx, __fmul_rn(gy, gy));
-            const float gn = sqrtf(g2);
-            const float mh = delta * gn;
-            w.ig2 = 1.f / g2;
-            w.mz = delta * dmax / gn;
             wedge_traverse<COUNT>(S, L, w, want, alive, stack, lane, ws, cx, cy, cz, s4.z, gx, gy, mh, P.ex.x, P.ex.y,
                                   failed, ctr, hit_tri);
         }

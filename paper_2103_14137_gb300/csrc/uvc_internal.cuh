@@ -44,9 +44,14 @@ constexpr int kWedgeMaxK = 16;
 // Lamp as seen by the kernels: source offsets and source powers w_m * P.
 // wedge = 1: every offset is vertical (x = y = 0), 2 <= K <= kWedgeMaxK, and
 // the wedge traversal is switched on (uvc_set_wedge_traversal).
+// Wedge lamps whose offsets rise evenly (off_m.z within 1/64 of a step of
+// wz0 + m dz, dz > 0) have wuniform = 1 and wz0, wrdz = 1/dz set: the
+// sources in a height interval are then a range of indices.
 struct LampDev {
     int K;
     int wedge;
+    int wuniform;
+    float wz0, wrdz;
     float ox[UVC_MAX_SOURCES], oy[UVC_MAX_SOURCES], oz[UVC_MAX_SOURCES];
     float pw[UVC_MAX_SOURCES];
 };
