@@ -33,8 +33,11 @@ namespace uvc {
 namespace {
 
 // Candidates per warp task: the warp keeps its 32 patches (and its occluder
-// cache) over this many consecutive candidates.
-constexpr int kCandPerTask = 8;
+// cache) over this many consecutive candidates (a tuning constant).
+#ifndef UVC_CAND_PER_TASK
+#define UVC_CAND_PER_TASK 4
+#endif
+constexpr int kCandPerTask = UVC_CAND_PER_TASK;
 
 template <bool COUNT, bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(SceneView S, const float* __restrict__ cand, int nc,

@@ -552,15 +552,17 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
             break;
         }
         const Node4* nd = S.nodes4 + node;
-        const char* b = reinterpret_cast<const char*>(nd);
-        const char *bnx = b + w.onx, *bfx = b + (8 - w.onx), *bny = b + 16 + w.ony, *bfy = b + 16 + (8 - w.ony);
-        const char* bz = b + 32;
         const int4 rr = __ldg(&nd->r);
         const int4 mm = __ldg(&nd->m);
         bool h0, h1, h2, h3;
-        wedge_pair_hits(w, ldg2(bnx), ldg2(bfx), ldg2(bny), ldg2(bfy), ldg2(bz), ldg2(bz + 8), h0, h1);
-        wedge_pair_hits(w, ldg2(bnx + 48), ldg2(bfx + 48), ldg2(bny + 48), ldg2(bfy + 48), ldg2(bz + 48),
-                        ldg2(bz + 56), h2, h3);
+        {
+            const char* b = reinterpret_cast<const char*>(nd);
+            const char *bnx = b + w.onx, *bfx = b + (8 - w.onx), *bny = b + 16 + w.ony, *bfy = b + 16 + (8 - w.ony);
+            const char* bz = b + 32;
+            wedge_pair_hits(w, ldg2(bnx), ldg2(bfx), ldg2(bny), ldg2(bfy), ldg2(bz), ldg2(bz + 8), h0, h1);
+            wedge_pair_hits(w, ldg2(bnx + 48), ldg2(bfx + 48), ldg2(bny + 48), ldg2(bfy + 48), ldg2(bz + 48),
+                            ldg2(bz + 56), h2, h3);
+        }
         if (COUNT) c_box += 4 * __popc(alive);
         const unsigned nib = ((alive >> lane) & 1u) ? (unsigned)h0 | ((unsigned)h1 << 1) | ((unsigned)h2 << 2) |
                                                           ((unsigned)h3 << 3)
