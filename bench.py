@@ -429,8 +429,11 @@ def cpu_baseline(s, seconds: float):
     import oracle
     threads = os.cpu_count() or 1
     oracle.build()
+    # calibrate on enough pairs that thread start-up does not dominate the estimate
     probe = 64
     dt = _oracle_rate(s, probe, 101, threads)
+    probe = int(min(max(probe, probe * 0.1 * seconds / max(dt, 1e-6)), 200_000))
+    dt = _oracle_rate(s, probe, 103, threads)
     n = int(min(max(probe, probe * seconds / max(dt, 1e-6)), 2_000_000))
     dt = _oracle_rate(s, n, 102, threads)
     rate = n / dt
