@@ -176,7 +176,8 @@ int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc,
  * profiling and for the benchmark's algorithmic operation count; slower than
  * the plain call because of the counting atomics.  Synchronises `stream`.
  *   counters  HOST uint64[8]: [0] node visits (per warp packet), [1] leaf
- *             triangle loads (per warp packet), [2] packet traversals,
+ *             triangle loads (per warp packet; per lane on the wedge path),
+ *             [2] packet traversals,
  *             [3] per-segment box tests, [4] per-segment triangle tests,
  *             [5] facing segments that needed a search, [6] per-lane wedge
  *             box tests, [7] per-lane wedge plane tests

@@ -568,51 +568,50 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
                                                           ((unsigned)h3 << 3)
                                                     : 0u;
         const unsigned hit = __reduce_or_sync(kFull, nib);
-        unsigned leaves = hit & (unsigned)mm.x;
-        const bool had_leaves = leaves != 0;
-        while (leaves) {
-            const int c = __ffs(leaves) - 1;
-            leaves &= leaves - 1;
-            const uint32_t m = __ballot_sync(kFull, (nib >> c) & 1u) & alive;
-            if (!m) continue;
-            const int leaf = ~pick4(rr, c);
-            const float4* t = S.tri + 3 * (size_t)leaf;
-            const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
-            const int id = __float_as_int(ta.w);
-            if (COUNT) { ++c_leaf; c_plane += __popc(m); }
-            if (((m >> lane) & 1u) && id != ex0 && id != ex1) {
-                // triangle entirely on one side of the wedge's vertical plane,
-                // farther than delta: no segment of the lane can meet it
-                const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));
-                const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
-                const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
-                const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
-                if (!beside) {
-                    const uint32_t before = want;
-                    const uint32_t test = want & lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
-                    for (uint32_t bits = test; bits; bits &= bits - 1) {
-                        const int q = __ffs(bits) - 1;
-                        const float4 sh = ws.shear[q * 32 + lane];
-                        const int kb = __float_as_int(sh.w);
-                        if (COUNT) ++c_tri;
-                        if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), (kb >> 0) & 3, (kb >> 2) & 3, (kb >> 4) & 3,
-                                      sh.x, sh.y, sh.z, ta, tb, tc))
-                            want &= ~(1u << q);
-                    }
-                    if (want != before) {
-                        hit_tri = leaf;
-                        if (want) wedge_z(w, want, cz, L, sz, delta);
+        // leaf children: each lane works through the leaves it wants itself
+        // (the warp iterates as often as the busiest lane, not once per leaf
+        // any lane wants)
+        unsigned mine = ((alive >> lane) & 1u) ? (nib & (unsigned)mm.x) : 0u;
+        while (__any_sync(kFull, mine != 0u)) {
+            if (mine) {
+                const int c = __ffs(mine) - 1;
+                mine &= mine - 1;
+                const int leaf = ~pick4(rr, c);
+                const float4* t = S.tri + 3 * (size_t)leaf;
+                const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
+                const int id = __float_as_int(ta.w);
+                if (COUNT) { ++c_leaf; ++c_plane; }
+                if (id != ex0 && id != ex1) {
+                    // triangle entirely on one side of the wedge's vertical plane,
+                    // farther than delta: no segment of the lane can meet it
+                    const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));
+                    const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
+                    const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
+                    const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
+                    if (!beside) {
+                        const uint32_t before = want;
+                        const uint32_t test = want & lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
+                        for (uint32_t bits = test; bits; bits &= bits - 1) {
+                            const int q = __ffs(bits) - 1;
+                            const float4 sh = ws.shear[q * 32 + lane];
+                            const int kb = __float_as_int(sh.w);
+                            if (COUNT) ++c_tri;
+                            if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), kb & 3, (kb >> 2) & 3, (kb >> 4) & 3, sh.x,
+                                          sh.y, sh.z, ta, tb, tc))
+                                want &= ~(1u << q);
+                        }
+                        if (want != before) {
+                            hit_tri = leaf;
+                            if (want) wedge_z(w, want, cz, L, sz, delta);
+                        }
                     }
                 }
+                if (!want) mine = 0u;
             }
-            alive &= __ballot_sync(kFull, want != 0u);
         }
+        alive &= __ballot_sync(kFull, want != 0u);
         if (!alive) break;
         unsigned inner = hit & (unsigned)mm.y;
-        if (had_leaves && inner) {
-            const unsigned nib2 = ((alive >> lane) & 1u) ? nib : 0u;
-            inner &= __reduce_or_sync(kFull, nib2);
-        }
         if (inner) {
             const int first = __ffs(inner) - 1;
             if (top + 3 > S.stack_cap) {
@@ -632,14 +631,18 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
     }
     if (COUNT && lane == 0) {
         atomicAdd(&ctr[0], (unsigned long long)visits);
-        atomicAdd(&ctr[1], c_leaf);
         atomicAdd(&ctr[2], 1ull);
         atomicAdd(&ctr[6], c_box);
-        atomicAdd(&ctr[7], c_plane);
     }
-    if (COUNT) {   // triangle tests are per lane
-        const unsigned long long s = __reduce_add_sync(kFull, (unsigned)c_tri);
-        if (lane == 0) atomicAdd(&ctr[4], s);
+    if (COUNT) {   // leaf loads, plane tests and triangle tests are per lane
+        const unsigned nleaf = __reduce_add_sync(kFull, (unsigned)c_leaf);
+        const unsigned nplane = __reduce_add_sync(kFull, (unsigned)c_plane);
+        const unsigned ntri = __reduce_add_sync(kFull, (unsigned)c_tri);
+        if (lane == 0) {
+            atomicAdd(&ctr[1], (unsigned long long)nleaf);
+            atomicAdd(&ctr[7], (unsigned long long)nplane);
+            atomicAdd(&ctr[4], (unsigned long long)ntri);
+        }
     }
 }
 

@@ -98,3 +98,30 @@ def test_batch_cuda_graph_replay():
     g.replay()
     _check(jobs, ref)
     b.free()
+
+
+@pytest.mark.parametrize("which", ["line_lamps_only", "point_and_tilted_only"])
+def test_batch_path_modes_match_single_calls(which):
+    """A batch whose lamps all take the wedge path, and one where none does
+    (point lamp, tilted line lamp), against the single-matrix calls."""
+    room = batched_room(103)
+    sc = build(room)
+    if which == "line_lamps_only":
+        lamps = [line_lamp(L, K, 120.0) for (L, K) in LAMPS]
+    else:
+        tilted = line_lamp(1.2, 8, 120.0)
+        tilted.offsets[:, 1] = np.linspace(-0.1, 0.1, 8, dtype=np.float32)
+        lamps = [tiny_room().lamp, tilted]
+    L = [uvc.Lamp(x.offsets, x.weights, x.power) for x in lamps]
+    jobs = []
+    for d in range(len(lamps)):
+        cand = design_candidates(room, 0.5 + 0.2 * d, 1.2, 45 + 7 * d, seed=31 + d)
+        A = torch.full((cand.shape[0], sc.np), -1.0, device="cuda")
+        vis = torch.zeros((lamps[d].K, cand.shape[0], (sc.np + 31) // 32), dtype=torch.int32, device="cuda")
+        jobs.append((sc, T(cand), d, A, vis))
+    ref = _reference(jobs, L)
+    b = uvc.Batch(jobs, L)
+    b.launch()
+    _check(jobs, ref)
+    b.free()
+    sc.free()
