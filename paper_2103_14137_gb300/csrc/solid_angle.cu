@@ -11,7 +11,8 @@
 //
 // Work unit as in irradiance.cu: one warp = 32 patches x one source, walking
 // the four-wide tree as a packet; the vertex checks are further packets from
-// the same source point.
+// the same source point.  Vertical line lamps take the wedge searches instead
+// (one per check point for all sources).
 #include "traverse.cuh"
 
 namespace uvc {
@@ -129,12 +130,19 @@ __device__ __forceinline__ uint32_t packet_to(const SceneView& S, float ox, floa
     return occl;
 }
 
+// Vertical line lamps (WEDGE): the centroid and each check point get one wedge
+// search for all of a candidate's sources that still need it (see the wedge
+// traversal in traverse.cuh); the per-source results, and so the entries, are
+// those of the source-by-source searches.
+template <bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     k_area_mean(SceneView S, const float* __restrict__ cand, int nc, LampDev L, const float* __restrict__ ptri,
                 float* __restrict__ A, int64_t lda, uint8_t* __restrict__ nclosed) {
-    extern __shared__ int smem[];
+    extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
+    WedgeSmem ws;
+    if (WEDGE) ws = wedge_smem(reinterpret_cast<char*>(smem) + stack_smem_bytes(S.stack_cap), L.K, warp);
     const int njb = (S.np + 31) >> 5;
     const int nchunk = (nc + kAreaCandPerTask - 1) / kAreaCandPerTask;
     const int64_t ntask = (int64_t)nchunk * njb;
@@ -154,7 +162,44 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
             float E = 0.f;
             int closed = 0;
             uint32_t failed_all = 0;
-            for (int m = 0; m < L.K; ++m) {
+            if (WEDGE) {
+                uint32_t want, failed;
+                float lend, dmax, gx, gy;
+                const uint32_t facing = wedge_setup_patch(S, L, cx, cy, cz, P, lane, ws, want, lend, dmax, gx, gy);
+                const uint32_t occl = wedge_search<false>(S, L, cx, cy, cz, P.s.z, gx, gy, want, lend, dmax, P.ex, lane,
+                                                          stack, ws, cache, failed, nullptr);
+                failed_all |= failed;
+                const uint32_t vis_c = ((failed >> lane) & 1u) ? 0u : (facing & ~occl);
+                uint32_t all = tmask != 0 ? vis_c : 0u;   // sources that saw every check point so far
+                for (int q = 0; q < 6; ++q) {
+                    const uint32_t want_q = ((tmask >> (q / 3)) & 1) ? all : 0u;
+                    if (!__any_sync(kFull, want_q != 0u)) continue;
+                    const float3 pq = want_q ? pulled(vertex(g, q), P.s) : make_float3(0.f, 0.f, 0.f);
+                    float dq = 0.f, gxq = 0.f, gyq = 0.f;
+                    if (want_q) wedge_setup_point(L, cx, cy, cz, pq, want_q, lane, ws, dq, gxq, gyq);
+                    uint32_t fq;
+                    const uint32_t oc = wedge_search<false>(S, L, cx, cy, cz, pq.z, gxq, gyq, want_q, 1.f, dq, P.ex,
+                                                            lane, stack, ws, cache, fq, nullptr);
+                    failed_all |= fq;
+                    all &= ~oc;
+                }
+                for (int m = 0; m < L.K; ++m) {
+                    if ((all >> m) & 1u) {
+                        const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]),
+                                    oz = __fadd_rn(cz, L.oz[m]);
+                        float om = 0.f;
+                        for (int t = 0; t < 2; ++t)
+                            if ((tmask >> t) & 1)
+                                om = __fadd_rn(om, solid_angle(ox, oy, oz, vertex(g, 3 * t), vertex(g, 3 * t + 1),
+                                                               vertex(g, 3 * t + 2)));
+                        E = __fadd_rn(E, __fmul_rn(__fmul_rn(L.pw[m], om), inv_area));
+                        ++closed;
+                    } else if ((vis_c >> m) & 1u) {
+                        E = __fadd_rn(E, ws.term[m * 32 + lane]);
+                    }
+                }
+            }
+            for (int m = 0; m < (WEDGE ? 0 : L.K); ++m) {
                 const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
                 float hx, hy, hz, lx, ly, lz;   // v = o - s exactly
                 two_diff(ox, P.s.x, hx, lx);
@@ -225,16 +270,24 @@ int irradiance_area_mean(const uvc_scene* sc, const float* cand, int64_t nc, con
                          float* A, int64_t lda, uint8_t* nclosed, cudaStream_t stream) {
     if (nc == 0 || sc->np == 0) return UVC_OK;
     SceneView S = view_of(sc);
-    const size_t smem = sizeof(int) * kWarpsPerBlock * S.stack_cap;
+    const bool wedge = lamp.wedge != 0;
+    const size_t smem = stack_smem_bytes(S.stack_cap) + (wedge ? wedge_smem_bytes(lamp.K) : 0);
+    const void* kern = wedge ? (const void*)k_area_mean<true> : (const void*)k_area_mean<false>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return status_from_cuda(e);
+    }
     const int njb = (S.np + 31) / 32;
     const int64_t ntask = ((nc + kAreaCandPerTask - 1) / kAreaCandPerTask) * njb;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_area_mean, kThreads, smem) != cudaSuccess ||
-        per_sm < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem) != cudaSuccess || per_sm < 1)
         per_sm = 1;
     int grid = per_sm * sm_count();
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    k_area_mean<<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, ptri, A, lda, nclosed);
+    if (wedge)
+        k_area_mean<true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, ptri, A, lda, nclosed);
+    else
+        k_area_mean<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, ptri, A, lda, nclosed);
     return status_from_cuda(cudaGetLastError());
 }
 

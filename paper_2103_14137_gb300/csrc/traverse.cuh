@@ -646,21 +646,24 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
     }
 }
 
-// Irradiance of candidate i at this lane's patch for a vertical line lamp
-// (L.wedge): the same entry as irradiance_entry, with one wedge search per
-// candidate instead of one segment search per source.
-template <bool COUNT = false>
-__device__ __forceinline__ float irradiance_wedge(const SceneView& S, const float* __restrict__ cand, int nc,
-                                                  const LampDev& L, int i, int jb, int lane, int* stack,
-                                                  const WedgeSmem& ws, uint32_t* __restrict__ vis, int nwords,
-                                                  const PatchLane& P, int& cache, unsigned long long* ctr = nullptr) {
+// Per-source set-up of the segments from candidate c's sources to the lane's
+// patch point (the arithmetic of irradiance_entry, source by source): shear
+// constants and Eq. (7) terms go to shared memory; returns the facing sources
+// and, in `want`, those that need a search (facing, longer than the clearance
+// cut), with the largest cut parameter `lend`, the longest such segment
+// `dmax` and the common horizontal direction (gx, gy).
+__device__ __forceinline__ uint32_t wedge_setup_patch(const SceneView& S, const LampDev& L, float cx, float cy,
+                                                      float cz, const PatchLane& P, int lane, const WedgeSmem& ws,
+                                                      uint32_t& want, float& lend, float& dmax, float& gx,
+                                                      float& gy) {
     const float4 s4 = P.s, n4 = P.n;
-    const float cx = __ldg(&cand[3 * (size_t)i]), cy = __ldg(&cand[3 * (size_t)i + 1]),
-                cz = __ldg(&cand[3 * (size_t)i + 2]);
-    uint32_t facing = 0, want = 0;
-    float lend = 0.f, gx = 0.f, gy = 0.f, dmax = 0.f;
+    uint32_t facing = 0;
+    want = 0;
+    lend = 0.f;
+    dmax = 0.f;
+    gx = 0.f;
+    gy = 0.f;
     for (int m = 0; m < L.K; ++m) {
-        // the set-up of irradiance_entry, source by source
         const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
         float hx = __fsub_rn(ox, s4.x), hy = __fsub_rn(oy, s4.y), hz = __fsub_rn(oz, s4.z);
         float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
@@ -714,6 +717,40 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
         gx = r.dx;
         gy = r.dy;
     }
+    return facing;
+}
+
+// Per-source set-up of the segments from the sources in `want` to point p
+// (direction p - o rounded once, as a plain segment query; no clearance cut):
+// shear constants to shared memory, the longest segment `dmax` and the common
+// horizontal direction (gx, gy).
+__device__ __forceinline__ void wedge_setup_point(const LampDev& L, float cx, float cy, float cz, float3 p,
+                                                  uint32_t want, int lane, const WedgeSmem& ws, float& dmax,
+                                                  float& gx, float& gy) {
+    dmax = 0.f;
+    gx = __fsub_rn(p.x, cx);
+    gy = __fsub_rn(p.y, cy);
+    for (uint32_t bits = want; bits; bits &= bits - 1) {
+        const int m = __ffs(bits) - 1;
+        Ray r;
+        r.ox = __fadd_rn(cx, L.ox[m]); r.oy = __fadd_rn(cy, L.oy[m]); r.oz = __fadd_rn(cz, L.oz[m]);
+        r.dx = __fsub_rn(p.x, r.ox); r.dy = __fsub_rn(p.y, r.oy); r.dz = __fsub_rn(p.z, r.oz);
+        setup_ray(r);
+        ws.shear[m * 32 + lane] = make_float4(r.sx, r.sy, r.sz, __int_as_float(r.kx | (r.ky << 2) | (r.kz << 4)));
+        dmax = fmaxf(dmax, sqrtf(__fmaf_rn(r.dx, r.dx, __fmaf_rn(r.dy, r.dy, __fmul_rn(r.dz, r.dz)))));
+    }
+}
+
+// The wedge search from the lamp line of candidate c to the lane's point
+// (height sz, horizontal direction (gx, gy) from c) for the sources in `want`
+// (shear constants already in shared memory): the lane's cached occluder
+// first, then the packet traversal.  Returns the sources found occluded;
+// `failed` gets the lanes whose search hit the visit cap or the stack limit.
+template <bool COUNT>
+__device__ __forceinline__ uint32_t wedge_search(const SceneView& S, const LampDev& L, float cx, float cy, float cz,
+                                                 float sz, float gx, float gy, uint32_t want, float lend, float dmax,
+                                                 int2 ex, int lane, int* stack, const WedgeSmem& ws, int& cache,
+                                                 uint32_t& failed, unsigned long long* ctr) {
     const float delta = S.cut_eps;
     WedgeLane w;
     const float g2 = __fmaf_rn(gx, gx, __fmul_rn(gy, gy));
@@ -730,7 +767,7 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
         const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
         const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
         const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
-        const uint32_t test = beside ? 0u : lamp_interval(w, want, ta, tb, tc, cx, cy, cz, s4.z, gx, gy, L);
+        const uint32_t test = beside ? 0u : lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
         for (uint32_t bits = test; bits; bits &= bits - 1) {
             const int q = __ffs(bits) - 1;
             const float4 sh = ws.shear[q * 32 + lane];
@@ -745,7 +782,7 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
         const unsigned nseg = __reduce_add_sync(kFull, (unsigned)__popc(want));
         if (lane == 0) atomicAdd(&ctr[5], (unsigned long long)nseg);
     }
-    uint32_t failed = 0;
+    failed = 0;
     int hit_tri = -1;
     const uint32_t alive = __ballot_sync(kFull, want != 0u);
     if (alive && S.nt > 0) {
@@ -754,7 +791,7 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
             const float4* t = S.tri + 3 * (size_t)(~S.root);
             const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
             const int id = __float_as_int(ta.w);
-            if (id != P.ex.x && id != P.ex.y) {
+            if (id != ex.x && id != ex.y) {
                 for (uint32_t bits = want; bits; bits &= bits - 1) {
                     const int q = __ffs(bits) - 1;
                     const float4 sh = ws.shear[q * 32 + lane];
@@ -777,13 +814,32 @@ __device__ __forceinline__ float irradiance_wedge(const SceneView& S, const floa
             w.lend = lend;
             w.onx = (int)(__float_as_uint(gx) >> 31) * 8;
             w.ony = (int)(__float_as_uint(gy) >> 31) * 8;
-            if (want) wedge_z(w, want, cz, L, s4.z, delta);
-            wedge_traverse<COUNT>(S, L, w, want, alive, stack, lane, ws, cx, cy, cz, s4.z, gx, gy, mh, P.ex.x, P.ex.y,
+            if (want) wedge_z(w, want, cz, L, sz, delta);
+            wedge_traverse<COUNT>(S, L, w, want, alive, stack, lane, ws, cx, cy, cz, sz, gx, gy, mh, ex.x, ex.y,
                                   failed, ctr, hit_tri);
         }
         occl |= before & ~want;
     }
     if (hit_tri >= 0) cache = hit_tri;
+    return occl;
+}
+
+// Irradiance of candidate i at this lane's patch for a vertical line lamp
+// (L.wedge): the same entry as irradiance_entry, with one wedge search per
+// candidate instead of one segment search per source.
+template <bool COUNT = false>
+__device__ __forceinline__ float irradiance_wedge(const SceneView& S, const float* __restrict__ cand, int nc,
+                                                  const LampDev& L, int i, int jb, int lane, int* stack,
+                                                  const WedgeSmem& ws, uint32_t* __restrict__ vis, int nwords,
+                                                  const PatchLane& P, int& cache, unsigned long long* ctr = nullptr) {
+    const float cx = __ldg(&cand[3 * (size_t)i]), cy = __ldg(&cand[3 * (size_t)i + 1]),
+                cz = __ldg(&cand[3 * (size_t)i + 2]);
+    uint32_t want;
+    float lend, dmax, gx, gy;
+    const uint32_t facing = wedge_setup_patch(S, L, cx, cy, cz, P, lane, ws, want, lend, dmax, gx, gy);
+    uint32_t failed;
+    const uint32_t occl =
+        wedge_search<COUNT>(S, L, cx, cy, cz, P.s.z, gx, gy, want, lend, dmax, P.ex, lane, stack, ws, cache, failed, ctr);
     const bool bad = (failed >> lane) & 1u;
     const uint32_t visible = bad ? 0u : (facing & ~occl);
     float E = 0.f;

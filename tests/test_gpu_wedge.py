@@ -152,3 +152,42 @@ def test_streamed_fluence_wedge_equals_per_source():
     torch.cuda.synchronize()
     assert torch.equal(mu_w, mu_p)
     sc.free()
+
+
+def _area(sc, cand, lamp, ptri, enable):
+    with wedge(enable):
+        A, ncl = uvc.irradiance_area_mean(sc, T(np.asarray(cand, np.float32)), lamp, T(ptri), with_closed=True)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    return A, ncl
+
+
+@pytest.mark.parametrize("which", ["ward", "quad_patches", "tiny_k5"])
+def test_area_mean_wedge_equals_per_source(which):
+    """Area-mean irradiance: the wedge searches (centroid and every check
+    point) give the per-source kernel's entries and closed-form counts; any
+    differing pair must be one the oracle flags as grazing."""
+    from synth.batched import batched_room, design_candidates
+    if which == "ward":
+        s = ward_room()
+        cand, L = s.cand[:256], s.lamp
+    elif which == "quad_patches":
+        s = batched_room(136)
+        cand, L = design_candidates(s, 0.8, 1.2, 300, seed=4), line_lamp(1.2, 8, 120.0)
+    else:
+        s = tiny_room(n_cand=45)
+        cand = s.cand.copy()
+        cand[:, 2] = 0.62
+        L = line_lamp(0.9, 5, 100.0)
+    sc = build(s)
+    lamp = lamp_of(L)
+    Aw, cw = _area(sc, cand, lamp, s.ptri, True)
+    Ap, cp = _area(sc, cand, lamp, s.ptri, False)
+    if not (torch.equal(Aw, Ap) and torch.equal(cw, cp)):
+        diff = np.argwhere(((Aw != Ap) | (cw != cp)).cpu().numpy())
+        _, _, flag = oracle.area_mean(s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, s.ptri, cand,
+                                      L.offsets, L.weights, L.power, pairs=diff)
+        assert np.all(flag != 0), f"{int((flag == 0).sum())} non-grazing pairs differ"
+        assert diff.shape[0] <= max(1, int(1e-6 * Aw.numel() * L.K))
+    assert (cw > 0).float().mean().item() > 0.2          # the closed form is exercised
+    sc.free()
