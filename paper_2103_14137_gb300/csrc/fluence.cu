@@ -1,11 +1,12 @@
 // Fluence mu = A^T t (paper Eq. (5)) and the covered-area fraction (the dose
 // constraint mu >= mu_min of Eq. (8)).
 //
-// Fluence: each lane owns one patch column j and keeps NV dwell-vector
-// accumulators; terms are summed in blocks of 32 candidates and the block sums
-// are added with Kahan compensation (relative error near 34 ulp whatever nc
-// is).  At nvec = 16 the kernel is bound by the HBM read of A (16 FMA per
-// 4 bytes).
+// Fluence: each thread owns two patch columns of a quarter of the candidate
+// rows and keeps NV dwell-vector accumulators per column; terms are summed in
+// blocks of 32 candidates and the block sums are added with Kahan
+// compensation, the quarters in a fixed order (relative error near 36 ulp
+// whatever nc is).  At nvec = 16 the kernel should be bound by the HBM read of
+// A (16 FMA per 4 bytes).
 #include <algorithm>
 
 #include "uvc_internal.cuh"
@@ -22,111 +23,111 @@ __device__ __forceinline__ void kahan_add(float& sum, float& c, float x) {
     sum = t;
 }
 
-constexpr int kRows = 16;     // candidate rows per pipeline stage
-constexpr int kStages = 3;    // stages in flight per warp
-constexpr size_t kFluenceSmem = sizeof(float) * kWarpsPerBlock * kStages * kRows * (32 + kNV);
+// One block = 128 patch columns x all candidates.  Its 256 threads form 4
+// row groups of 64 threads; a group takes a contiguous quarter of the
+// candidate rows and each of its threads two adjacent columns, read straight
+// from global memory as one 8-byte load per row when the row stride allows
+// (lda even, A 8-byte aligned), else as two 4-byte loads; a warp reads 256
+// contiguous bytes per row.  The dwell times of the group's rows are staged in
+// shared memory transposed (row-major, 16 per row), so one 16-byte broadcast
+// serves four vectors of both columns, and the 16 products per row and column
+// pair run as packed FP32x2 FMAs.  Sums: blocks of 32 rows plain, block sums
+// Kahan-compensated, the 4 group results added in a fixed order.
+constexpr int kFlGroups = 4;                      // row groups per block
+constexpr int kFlGroupThreads = 64;              // threads per row group
+constexpr int kFlCols = 2 * kFlGroupThreads;     // columns per block
+constexpr int kFlChunk = 128;                     // rows of dwell times staged per group at a time
+constexpr int kFlUnroll = 4;                      // rows of A loaded ahead
+constexpr size_t kFluenceSmem = sizeof(float) * kFlGroups * kFlChunk * kNV;
 
-__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src, bool pred) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(smem_dst);
-    const int n = pred ? 4 : 0;   // 0: zero-fill, nothing read
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(gmem_src), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// One block = 32 patch columns; its 8 warps split the candidates into 8
-// contiguous ranges.  Each warp streams its rows of A (one coalesced 128-byte
-// segment per row) and the matching dwell times through a kStages-deep ring
-// of cp.async copies into shared memory, so that many rows are in flight per
-// SM without holding them in registers; each lane then reads its column from
-// shared memory.  The 8 warp results are added in a fixed order at the end.
 __global__ void __launch_bounds__(256, 2) k_fluence(const float* __restrict__ A, int nc, int64_t lda,
                                                     const float* __restrict__ t, int nvec, int v0,
-                                                    float* __restrict__ mu, int np) {
+                                                    float* __restrict__ mu, int np, int vec2) {
     extern __shared__ float4 fluence_smem[];
-    auto abuf = reinterpret_cast<float (*)[kStages][kRows][32]>(fluence_smem);
-    auto tbuf = reinterpret_cast<float (*)[kStages][kRows][kNV]>(reinterpret_cast<float*>(fluence_smem) +
-                                                                 kWarpsPerBlock * kStages * kRows * 32);
-    // after the main loop the row buffers are reused for the cross-warp sums
-    auto red = reinterpret_cast<float (*)[kNV][33]>(fluence_smem);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j = blockIdx.x * 32 + lane;
-    const bool valid = j < np;
-    const int per = (nc + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const int i_begin = min(nc, warp * per), i_end = min(nc, i_begin + per);
-    const int nstage = (i_end - i_begin + kRows - 1) / kRows;
-    const float* colp = A + (valid ? j : 0);
-
-    // stage k covers rows i_begin + k*kRows ...; lane copies its column of each
-    // row, and lanes 0..15 copy the dwell times of the stage's rows
-    auto issue = [&](int k) {
-        if (k < nstage) {
-            const int ib = i_begin + k * kRows;
-            const int buf = k % kStages;
+    const int g = threadIdx.x / kFlGroupThreads, gt = threadIdx.x % kFlGroupThreads;
+    float4* ts = fluence_smem + (size_t)g * kFlChunk * (kNV / 4);   // [kFlChunk][kNV / 4]
+    const int j0 = blockIdx.x * kFlCols + 2 * gt;
+    const bool ok0 = j0 < np, ok1 = j0 + 1 < np;
+    const int per = (((nc + kFlGroups - 1) / kFlGroups) + 31) / 32 * 32;   // rows per group, multiple of 32
+    const int r0 = min(nc, g * per), r1 = min(nc, r0 + per);
+    float2 part[kNV], acc[kNV], comp[kNV];
 #pragma unroll
-            for (int q = 0; q < kRows; ++q) {
-                const int i = ib + q;
-                const bool ok = valid && i < i_end;
-                cp_async4(&abuf[warp][buf][q][lane], ok ? colp + (size_t)i * lda : A, ok);
+    for (int v = 0; v < kNV; ++v) {
+        part[v] = make_float2(0.f, 0.f);
+        acc[v] = part[v];
+        comp[v] = part[v];
+    }
+    const int nchunk = (per + kFlChunk - 1) / kFlChunk;   // the same for every group
+    for (int ck = 0; ck < nchunk; ++ck) {
+        const int c0 = r0 + ck * kFlChunk, c1 = min(r1, c0 + kFlChunk);
+        __syncthreads();
+        // stage t[v0 + v][c0 .. c1) transposed: ts[row][v]
+        float* tsf = reinterpret_cast<float*>(ts);
+        for (int e = gt; e < kFlChunk * kNV; e += kFlGroupThreads) {
+            const int v = e / kFlChunk, q = e % kFlChunk;
+            const int i = c0 + q;
+            tsf[q * kNV + v] = (i < c1 && v0 + v < nvec) ? __ldg(&t[(size_t)(v0 + v) * nc + i]) : 0.f;
+        }
+        __syncthreads();
+        for (int q0 = 0; q0 < c1 - c0; q0 += kFlUnroll) {
+            float2 a[kFlUnroll];
+#pragma unroll
+            for (int u = 0; u < kFlUnroll; ++u) {
+                const int i = c0 + q0 + u;
+                a[u] = make_float2(0.f, 0.f);
+                if (i < c1) {
+                    const float* row = A + (size_t)i * lda + j0;
+                    if (vec2 && ok1) {
+                        a[u] = __ldcs(reinterpret_cast<const float2*>(row));
+                    } else {
+                        if (ok0) a[u].x = __ldcs(row);
+                        if (ok1) a[u].y = __ldcs(row + 1);
+                    }
+                }
             }
-            if (lane < kRows) {
-                const int i = ib + lane;
+#pragma unroll
+            for (int u = 0; u < kFlUnroll; ++u) {
+#pragma unroll
+                for (int v4 = 0; v4 < kNV / 4; ++v4) {
+                    const float4 w = ts[(q0 + u) * (kNV / 4) + v4];   // rows past c1 hold zeros
+                    part[4 * v4 + 0] = ffma2(make_float2(w.x, w.x), a[u], part[4 * v4 + 0]);
+                    part[4 * v4 + 1] = ffma2(make_float2(w.y, w.y), a[u], part[4 * v4 + 1]);
+                    part[4 * v4 + 2] = ffma2(make_float2(w.z, w.z), a[u], part[4 * v4 + 2]);
+                    part[4 * v4 + 3] = ffma2(make_float2(w.w, w.w), a[u], part[4 * v4 + 3]);
+                }
+            }
+            if (((q0 + kFlUnroll) & 31) == 0 || q0 + kFlUnroll >= c1 - c0) {   // a block of 32 rows ends
 #pragma unroll
                 for (int v = 0; v < kNV; ++v) {
-                    const bool ok = i < i_end && v0 + v < nvec;
-                    cp_async4(&tbuf[warp][buf][lane][v], ok ? t + (size_t)(v0 + v) * nc + i : t, ok);
+                    kahan_add(acc[v].x, comp[v].x, part[v].x);
+                    kahan_add(acc[v].y, comp[v].y, part[v].y);
+                    part[v] = make_float2(0.f, 0.f);
                 }
             }
         }
-        cp_async_commit();
-    };
-
-    float acc[kNV], comp[kNV], part[kNV];
-#pragma unroll
-    for (int v = 0; v < kNV; ++v) { acc[v] = 0.f; comp[v] = 0.f; part[v] = 0.f; }
-#pragma unroll
-    for (int k = 0; k < kStages - 1; ++k) issue(k);
-    for (int k = 0; k < nstage; ++k) {
-        issue(k + kStages - 1);
-        cp_async_wait<kStages - 1>();
-        __syncwarp();
-        const int buf = k % kStages;
-#pragma unroll
-        for (int q = 0; q < kRows; ++q) {
-            const float a = abuf[warp][buf][q][lane];
-            const float4* tq = reinterpret_cast<const float4*>(&tbuf[warp][buf][q][0]);
-#pragma unroll
-            for (int v4 = 0; v4 < kNV / 4; ++v4) {
-                const float4 w = tq[v4];
-                part[4 * v4 + 0] = __fmaf_rn(w.x, a, part[4 * v4 + 0]);
-                part[4 * v4 + 1] = __fmaf_rn(w.y, a, part[4 * v4 + 1]);
-                part[4 * v4 + 2] = __fmaf_rn(w.z, a, part[4 * v4 + 2]);
-                part[4 * v4 + 3] = __fmaf_rn(w.w, a, part[4 * v4 + 3]);
-            }
-        }
-        __syncwarp();
-        if ((k & 1) || k == nstage - 1) {   // blocks of 32 rows (2 stages) into the compensated sums
-#pragma unroll
-            for (int v = 0; v < kNV; ++v) {
-                kahan_add(acc[v], comp[v], part[v]);
-                part[v] = 0.f;
-            }
-        }
     }
-    cp_async_wait<0>();
-    __syncthreads();   // every warp is done with its row buffers
-#pragma unroll
-    for (int v = 0; v < kNV; ++v) red[warp][v][lane] = __fsub_rn(acc[v], comp[v]);
+    // fixed-order (group 0..3) compensated sum of the group results
     __syncthreads();
-    // fixed-order (warp 0..7) compensated sum; thread (v, lane) per output
-    for (int idx = threadIdx.x; idx < kNV * 32; idx += blockDim.x) {
-        const int v = idx >> 5, l = idx & 31;
-        const int jj = blockIdx.x * 32 + l;
-        if (jj >= np || v0 + v >= nvec) continue;
-        float s = 0.f, c = 0.f;
-        for (int w = 0; w < kWarpsPerBlock; ++w) kahan_add(s, c, red[w][v][l]);
-        mu[(size_t)(v0 + v) * np + jj] = s;
+    float2* red = reinterpret_cast<float2*>(fluence_smem);   // [kFlGroups][kNV][kFlGroupThreads]
+#pragma unroll
+    for (int v = 0; v < kNV; ++v)
+        red[((size_t)g * kNV + v) * kFlGroupThreads + gt] =
+            make_float2(__fsub_rn(acc[v].x, comp[v].x), __fsub_rn(acc[v].y, comp[v].y));
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kNV * kFlGroupThreads; idx += blockDim.x) {
+        const int v = idx / kFlGroupThreads, l = idx % kFlGroupThreads;
+        const int jj = blockIdx.x * kFlCols + 2 * l;
+        if (v0 + v >= nvec) continue;
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+        for (int w = 0; w < kFlGroups; ++w) {
+            const float2 x = red[((size_t)w * kNV + v) * kFlGroupThreads + l];
+            kahan_add(s0, c0, x.x);
+            kahan_add(s1, c1, x.y);
+        }
+        if (jj < np) mu[(size_t)(v0 + v) * np + jj] = s0;
+        if (jj + 1 < np) mu[(size_t)(v0 + v) * np + jj + 1] = s1;
     }
 }
 
@@ -195,14 +196,16 @@ int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const 
     const int np = (int)sc->np;
     if (np == 0) return UVC_OK;
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)nvec * np, stream));
-    static_assert(kWarpsPerBlock * kNV * 33 <= kWarpsPerBlock * kStages * kRows * (32 + kNV), "red fits");
+    static_assert(sizeof(float2) * kFlGroups * kNV * kFlGroupThreads <= kFluenceSmem, "group results fit");
+    static_assert(kFlGroups * kFlGroupThreads == kThreads, "block shape");
     // once per process (and so not during a stream capture that follows a first call)
     static const cudaError_t attr =
         cudaFuncSetAttribute(k_fluence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFluenceSmem);
     if (attr != cudaSuccess) return status_from_cuda(attr);
-    const int grid = (np + 31) / 32;
+    const int grid = (np + kFlCols - 1) / kFlCols;
+    const int vec2 = (lda % 2 == 0) && (reinterpret_cast<uintptr_t>(A) % 8 == 0);
     for (int v0 = 0; v0 < nvec; v0 += kNV)
-        k_fluence<<<grid, kThreads, kFluenceSmem, stream>>>(A, (int)nc, lda, t, nvec, v0, mu, np);
+        k_fluence<<<grid, kThreads, kFluenceSmem, stream>>>(A, (int)nc, lda, t, nvec, v0, mu, np, vec2);
     return status_from_cuda(cudaGetLastError());
 }
 
