@@ -47,6 +47,8 @@ def load_library(path: str):
     lib.uvco_irradiance.argtypes = [P, i64, P, i64, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
                                     ctypes.c_double, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
     lib.uvco_irradiance.restype = ctypes.c_int
+    lib.uvco_irradiance_bvh.argtypes = lib.uvco_irradiance.argtypes
+    lib.uvco_irradiance_bvh.restype = ctypes.c_int
     lib.uvco_area_mean.argtypes = [P, i64, P, i64, P, P, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_float, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
     lib.uvco_area_mean.restype = ctypes.c_int
@@ -81,8 +83,9 @@ def grazing_eps(verts, rel: float = 1e-7) -> float:
 
 
 def irradiance(verts, tris, centroid, normal, excl, cand, offsets, weights, power,
-               pairs=None, eps=None, flags=True, threads=0, lib=None):
-    """FP64 brute-force irradiance.
+               pairs=None, eps=None, flags=True, threads=0, lib=None, bvh=False):
+    """FP64 brute-force irradiance (bvh=True: the same entries through the
+    oracle's CPU hierarchy, for large samples).
 
     pairs: None for the full (nc, np) matrix, else an (npairs, 2) array of (i, j).
     Returns (E, vis, flag): E float64 (nc,np) or (npairs,), vis uint8 (..., K),
@@ -115,7 +118,8 @@ def irradiance(verts, tris, centroid, normal, excl, cand, offsets, weights, powe
     vis = np.zeros(npairs * K, np.uint8)
     flag = np.zeros(npairs, np.uint8) if flags else None
     ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
-    rc = lib.uvco_irradiance(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0],
+    fn = lib.uvco_irradiance_bvh if bvh else lib.uvco_irradiance
+    rc = fn(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0],
                              ptr(centroid), ptr(normal), ptr(excl), np_, ptr(cand), nc,
                              ptr(offsets), ptr(weights), K, float(power),
                              ptr(pp), npairs, float(eps), ptr(E), ptr(vis), ptr(flag), int(threads))

@@ -5,7 +5,8 @@
  * call this file; only the test suite, the smoke check and the benchmark's
  * CPU-baseline leg use it.  It shares no code, header or constant with the
  * CUDA library and is deliberately plain: every segment is tested against
- * every triangle (brute force), in double precision.
+ * every triangle (brute force), in double precision; a CPU-BVH mode
+ * (uvco_irradiance_bvh) gives the same results faster, for larger samples.
  *
  * What it computes (paper Sec. IV-C, "Discrete Radiative Fluence"):
  *
@@ -173,21 +174,275 @@ static int grazing_bits(const tri64* t, d3 o, d3 s, double eps) {
 }
 
 /*
- * Irradiance entries for a list of (candidate, patch) pairs.
+ * CPU-BVH mode.  A binary bounding-volume hierarchy over the triangles (boxes
+ * from the FP64 vertices, exact; median split of the triangle centres along
+ * the widest axis; leaves of at most 4 triangles) restricts each segment's
+ * triangle tests to the triangles whose box, padded by `pad`, the closed
+ * segment crosses.  The tests themselves are the brute force's
+ * (segment_meets_triangle, grazing_bits), so the mode gives the same entries,
+ * bits and flags whenever the box test never rejects a triangle the brute
+ * force would count: a segment point inside a triangle lies inside its box,
+ * and the padding (1e-9 of the scene's diagonal, plus eps for the flags) is
+ * far above the rounding of the FP64 slab test.
+ */
+typedef struct {
+    double lo[3], hi[3];
+    int64_t left, right;   /* children, or -1 for a leaf */
+    int64_t first, count;  /* leaf: order[first .. first+count) */
+} bnode;
+
+typedef struct {
+    bnode* nodes;
+    int64_t* order;
+    int64_t nnodes;
+    double diag;
+} bvh64;
+
+typedef struct { double key; int64_t idx; } keyed;
+
+static int keyed_cmp(const void* a, const void* b) {
+    const keyed* x = (const keyed*)a;
+    const keyed* y = (const keyed*)b;
+    if (x->key < y->key) return -1;
+    if (x->key > y->key) return 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static void box_of(const tri64* T, const int64_t* order, int64_t first, int64_t count, double lo[3], double hi[3]) {
+    for (int k = 0; k < 3; ++k) { lo[k] = INFINITY; hi[k] = -INFINITY; }
+    for (int64_t q = first; q < first + count; ++q) {
+        const tri64* t = &T[order[q]];
+        const d3 v[3] = {t->a, t->b, t->c};
+        for (int e = 0; e < 3; ++e) {
+            const double c[3] = {v[e].x, v[e].y, v[e].z};
+            for (int k = 0; k < 3; ++k) {
+                if (c[k] < lo[k]) lo[k] = c[k];
+                if (c[k] > hi[k]) hi[k] = c[k];
+            }
+        }
+    }
+}
+
+static void bvh_free(bvh64* B) {
+    free(B->nodes);
+    free(B->order);
+    B->nodes = NULL;
+    B->order = NULL;
+}
+
+static int bvh_build(const tri64* T, int64_t nt, bvh64* B) {
+    B->nnodes = 0;
+    B->nodes = (bnode*)malloc(sizeof(bnode) * (size_t)(2 * (nt > 0 ? nt : 1)));
+    B->order = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nt > 0 ? nt : 1));
+    keyed* tmp = (keyed*)malloc(sizeof(keyed) * (size_t)(nt > 0 ? nt : 1));
+    int64_t* stack = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * (nt > 0 ? nt : 1)));
+    if (!B->nodes || !B->order || !tmp || !stack) { free(tmp); free(stack); bvh_free(B); return -2; }
+    for (int64_t t = 0; t < nt; ++t) B->order[t] = t;
+    B->diag = 0.0;
+    if (nt == 0) { free(tmp); free(stack); return 0; }
+    bnode* root = &B->nodes[B->nnodes++];
+    root->first = 0;
+    root->count = nt;
+    box_of(T, B->order, 0, nt, root->lo, root->hi);
+    B->diag = sqrt((root->hi[0] - root->lo[0]) * (root->hi[0] - root->lo[0]) +
+                   (root->hi[1] - root->lo[1]) * (root->hi[1] - root->lo[1]) +
+                   (root->hi[2] - root->lo[2]) * (root->hi[2] - root->lo[2]));
+    int64_t top = 0;
+    stack[top++] = 0;
+    while (top > 0) {
+        bnode* nd = &B->nodes[stack[--top]];
+        nd->left = nd->right = -1;
+        if (nd->count <= 4) continue;
+        double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t q = nd->first; q < nd->first + nd->count; ++q) {
+            const d3 c = T[B->order[q]].center;
+            const double cc[3] = {c.x, c.y, c.z};
+            for (int k = 0; k < 3; ++k) {
+                if (cc[k] < clo[k]) clo[k] = cc[k];
+                if (cc[k] > chi[k]) chi[k] = cc[k];
+            }
+        }
+        int axis = 0;
+        for (int k = 1; k < 3; ++k)
+            if (chi[k] - clo[k] > chi[axis] - clo[axis]) axis = k;
+        for (int64_t q = 0; q < nd->count; ++q) {
+            const d3 c = T[B->order[nd->first + q]].center;
+            tmp[q].key = axis == 0 ? c.x : (axis == 1 ? c.y : c.z);
+            tmp[q].idx = B->order[nd->first + q];
+        }
+        qsort(tmp, (size_t)nd->count, sizeof(keyed), keyed_cmp);
+        for (int64_t q = 0; q < nd->count; ++q) B->order[nd->first + q] = tmp[q].idx;
+        const int64_t half = nd->count / 2;
+        const int64_t li = B->nnodes++, ri = B->nnodes++;
+        bnode* L = &B->nodes[li];
+        bnode* R = &B->nodes[ri];
+        L->first = nd->first;
+        L->count = half;
+        R->first = nd->first + half;
+        R->count = nd->count - half;
+        box_of(T, B->order, L->first, L->count, L->lo, L->hi);
+        box_of(T, B->order, R->first, R->count, R->lo, R->hi);
+        nd->left = li;
+        nd->right = ri;
+        stack[top++] = li;
+        stack[top++] = ri;
+    }
+    free(tmp);
+    free(stack);
+    return 0;
+}
+
+/* Does the closed segment o + tau dir, 0 <= tau <= 1, meet the box padded by pad? */
+static int segment_meets_box(d3 o, d3 dir, const double lo[3], const double hi[3], double pad) {
+    const double oo[3] = {o.x, o.y, o.z}, dd[3] = {dir.x, dir.y, dir.z};
+    double t0 = 0.0, t1 = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        const double l = lo[k] - pad, h = hi[k] + pad;
+        if (dd[k] == 0.0) {
+            if (oo[k] < l || oo[k] > h) return 0;
+            continue;
+        }
+        double ta = (l - oo[k]) / dd[k], tb = (h - oo[k]) / dd[k];
+        if (ta > tb) { const double x = ta; ta = tb; tb = x; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+        if (t0 > t1) return 0;
+    }
+    return 1;
+}
+
+/* Visibility of the open segment o -> o + dir through the hierarchy (any hit). */
+static int bvh_visible(const bvh64* B, const tri64* T, int32_t ex0, int32_t ex1, d3 o, d3 dir, int64_t* stack) {
+    if (B->nnodes == 0) return 1;
+    const double pad = 1e-9 * B->diag + 1e-300;
+    int64_t top = 0;
+    stack[top++] = 0;
+    while (top > 0) {
+        const bnode* nd = &B->nodes[stack[--top]];
+        if (!segment_meets_box(o, dir, nd->lo, nd->hi, pad)) continue;
+        if (nd->left < 0) {
+            for (int64_t q = nd->first; q < nd->first + nd->count; ++q) {
+                const int64_t t = B->order[q];
+                if (t == ex0 || t == ex1) continue;
+                if (segment_meets_triangle(o, dir, T[t].a, T[t].b, T[t].c)) return 0;
+            }
+        } else {
+            stack[top++] = nd->left;
+            stack[top++] = nd->right;
+        }
+    }
+    return 1;
+}
+
+/* Grazing bits 0 and 1 of the closed segment [o, s] through the hierarchy. */
+static int bvh_grazing(const bvh64* B, const tri64* T, int32_t ex0, int32_t ex1, d3 o, d3 s, double eps,
+                       int64_t* stack) {
+    if (B->nnodes == 0) return 0;
+    const double pad = eps + 1e-9 * B->diag + 1e-300;
+    const d3 dir = vsub(s, o);
+    int bits = 0;
+    int64_t top = 0;
+    stack[top++] = 0;
+    while (top > 0 && bits != 3) {
+        const bnode* nd = &B->nodes[stack[--top]];
+        if (!segment_meets_box(o, dir, nd->lo, nd->hi, pad)) continue;
+        if (nd->left < 0) {
+            for (int64_t q = nd->first; q < nd->first + nd->count; ++q) {
+                const int64_t t = B->order[q];
+                if (t == ex0 || t == ex1) continue;
+                bits |= grazing_bits(&T[t], o, s, eps);
+            }
+        } else {
+            stack[top++] = nd->left;
+            stack[top++] = nd->right;
+        }
+    }
+    return bits;
+}
+
+/*
+ * Irradiance entries for a list of (candidate, patch) pairs; with B non-NULL
+ * the segment and flag tests go through the hierarchy (same results).
  *   pairs    npairs*2 int64 (i, j); NULL means every pair, i major (k = i*np + j)
  *   E_out    npairs doubles (W/m^2)
  *   vis_out  npairs*K bytes (1 = source m sees the patch point), may be NULL
  *   flag_out npairs bytes of grazing bits, may be NULL (then no flag work)
  * Returns 0, or -1 on an index out of range.
  */
-int uvco_irradiance(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
-                    const float* centroid, const float* normal, const int32_t* excl, int64_t np,
-                    const float* cand, int64_t nc,
-                    const float* offsets, const float* weights, int32_t K, double power,
-                    const int64_t* pairs, int64_t npairs, double eps,
-                    double* E_out, uint8_t* vis_out, uint8_t* flag_out, int nthreads) {
+static int irradiance_entries(const tri64* T, int64_t nt, const bvh64* B, const float* centroid,
+                              const float* normal, const int32_t* excl, int64_t np, const float* cand,
+                              const float* offsets, const float* weights, int32_t K, double power,
+                              const int64_t* pairs, int64_t npairs, double eps, double* E_out, uint8_t* vis_out,
+                              uint8_t* flag_out, int nthreads) {
+    const double four_pi = 4.0 * M_PI;
+    int failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t* stack = B ? (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * B->nnodes + 2)) : NULL;
+        if (B && !stack) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int64_t k = 0; k < npairs; ++k) {
+            if (B && !stack) continue;
+            int64_t i = pairs ? pairs[2 * k] : k / np;
+            int64_t j = pairs ? pairs[2 * k + 1] : k % np;
+            d3 s = v3(centroid[3 * j], centroid[3 * j + 1], centroid[3 * j + 2]);
+            d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
+            int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
+            double E = 0.0;
+            int flags = 0;
+            for (int m = 0; m < K; ++m) {
+                /* the source point in FP32 (one IEEE single add per coordinate) */
+                float ox = cand[3 * i] + offsets[3 * m];
+                float oy = cand[3 * i + 1] + offsets[3 * m + 1];
+                float oz = cand[3 * i + 2] + offsets[3 * m + 2];
+                d3 o = v3(ox, oy, oz);
+                d3 v = vsub(o, s);
+                double d = vnorm(v);
+                double nv_ = vdot(n, v);
+                int visible = 0;
+                if (flag_out && fabs(nv_) <= eps) flags |= 4;
+                if (nv_ > 0.0 && d > 0.0) {
+                    d3 dir = vsub(s, o);
+                    if (B) {
+                        visible = bvh_visible(B, T, ex0, ex1, o, dir, stack);
+                        if (flag_out) flags |= bvh_grazing(B, T, ex0, ex1, o, s, eps, stack);
+                    } else {
+                        visible = 1;
+                        for (int64_t t = 0; t < nt; ++t) {
+                            if (t == ex0 || t == ex1) continue;
+                            if (segment_meets_triangle(o, dir, T[t].a, T[t].b, T[t].c)) { visible = 0; break; }
+                        }
+                        if (flag_out)
+                            for (int64_t t = 0; t < nt; ++t) {
+                                if (t == ex0 || t == ex1) continue;
+                                flags |= grazing_bits(&T[t], o, s, eps);
+                            }
+                    }
+                    if (visible) E += (double)weights[m] * power * nv_ / (four_pi * d * d * d);
+                }
+                if (vis_out) vis_out[k * K + m] = (uint8_t)visible;
+            }
+            E_out[k] = E;
+            if (flag_out) flag_out[k] = (uint8_t)flags;
+        }
+        free(stack);
+    }
+    return failed ? -2 : 0;
+}
+
+static int check_irradiance_args(const int32_t* excl, int64_t np, int64_t nc, int64_t nt, int32_t K,
+                                 const int64_t* pairs, int64_t npairs) {
     if (K < 1 || nt < 0 || np < 0 || nc < 0) return -1;
-    if (pairs == NULL) npairs = nc * np;
     for (int64_t j = 0; j < np; ++j)
         for (int q = 0; q < 2; ++q)
             if (excl[2 * j + q] < -1 || excl[2 * j + q] >= nt) return -1;
@@ -195,54 +450,48 @@ int uvco_irradiance(const float* verts, int64_t nv, const int32_t* tris, int64_t
         for (int64_t k = 0; k < npairs; ++k)
             if (pairs[2 * k] < 0 || pairs[2 * k] >= nc || pairs[2 * k + 1] < 0 || pairs[2 * k + 1] >= np)
                 return -1;
+    return 0;
+}
+
+/* Brute force: every segment against every triangle. */
+int uvco_irradiance(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const float* centroid, const float* normal, const int32_t* excl, int64_t np,
+                    const float* cand, int64_t nc,
+                    const float* offsets, const float* weights, int32_t K, double power,
+                    const int64_t* pairs, int64_t npairs, double eps,
+                    double* E_out, uint8_t* vis_out, uint8_t* flag_out, int nthreads) {
+    if (pairs == NULL) npairs = nc * np;
+    if (check_irradiance_args(excl, np, nc, nt, K, pairs, npairs) != 0) return -1;
     tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
     if (!T) return -2;
     if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
-    const double four_pi = 4.0 * M_PI;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 8)
-#endif
-    for (int64_t k = 0; k < npairs; ++k) {
-        int64_t i = pairs ? pairs[2 * k] : k / np;
-        int64_t j = pairs ? pairs[2 * k + 1] : k % np;
-        d3 s = v3(centroid[3 * j], centroid[3 * j + 1], centroid[3 * j + 2]);
-        d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
-        int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
-        double E = 0.0;
-        int flags = 0;
-        for (int m = 0; m < K; ++m) {
-            /* the source point in FP32 (one IEEE single add per coordinate) */
-            float ox = cand[3 * i] + offsets[3 * m];
-            float oy = cand[3 * i + 1] + offsets[3 * m + 1];
-            float oz = cand[3 * i + 2] + offsets[3 * m + 2];
-            d3 o = v3(ox, oy, oz);
-            d3 v = vsub(o, s);
-            double d = vnorm(v);
-            double nv_ = vdot(n, v);
-            int visible = 0;
-            if (flag_out && fabs(nv_) <= eps) flags |= 4;
-            if (nv_ > 0.0 && d > 0.0) {
-                visible = 1;
-                d3 dir = vsub(s, o);
-                for (int64_t t = 0; t < nt; ++t) {
-                    if (t == ex0 || t == ex1) continue;
-                    if (segment_meets_triangle(o, dir, T[t].a, T[t].b, T[t].c)) { visible = 0; break; }
-                }
-                if (flag_out)
-                    for (int64_t t = 0; t < nt; ++t) {
-                        if (t == ex0 || t == ex1) continue;
-                        flags |= grazing_bits(&T[t], o, s, eps);
-                    }
-                if (visible) E += (double)weights[m] * power * nv_ / (four_pi * d * d * d);
-            }
-            if (vis_out) vis_out[k * K + m] = (uint8_t)visible;
-        }
-        E_out[k] = E;
-        if (flag_out) flag_out[k] = (uint8_t)flags;
+    int rc = irradiance_entries(T, nt, NULL, centroid, normal, excl, np, cand, offsets, weights, K, power, pairs,
+                                npairs, eps, E_out, vis_out, flag_out, nthreads);
+    free(T);
+    return rc;
+}
+
+/* The same entries through the CPU hierarchy (see bvh_build). */
+int uvco_irradiance_bvh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                        const float* centroid, const float* normal, const int32_t* excl, int64_t np,
+                        const float* cand, int64_t nc,
+                        const float* offsets, const float* weights, int32_t K, double power,
+                        const int64_t* pairs, int64_t npairs, double eps,
+                        double* E_out, uint8_t* vis_out, uint8_t* flag_out, int nthreads) {
+    if (pairs == NULL) npairs = nc * np;
+    if (check_irradiance_args(excl, np, nc, nt, K, pairs, npairs) != 0) return -1;
+    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
+    if (!T) return -2;
+    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
+    bvh64 B;
+    int rc = bvh_build(T, nt, &B);
+    if (rc == 0) {
+        rc = irradiance_entries(T, nt, &B, centroid, normal, excl, np, cand, offsets, weights, K, power, pairs,
+                                npairs, eps, E_out, vis_out, flag_out, nthreads);
+        bvh_free(&B);
     }
     free(T);
-    return 0;
+    return rc;
 }
 
 /* Number of threads an OpenMP region will use (1 without OpenMP). */

@@ -105,6 +105,33 @@ def test_ward_full_size_sampled_pairs():
     sc.free()
 
 
+def test_ward_full_rows_against_bvh_oracle():
+    """Whole rows of the full-size ward matrix (48 candidates spread over the
+    list x all 102,030 patches, K = 8), computed in the benchmark's launch
+    configuration, against the oracle's CPU-BVH mode (bit-identical to its
+    brute force, tests/test_oracle_bvh.py); pairs whose visibility differs get
+    the brute force's grazing flags."""
+    s = ward_room()
+    sc = build(s)
+    A, vis = uvc.irradiance_matrix(sc, T(s.cand), lamp_of(s.lamp), with_vis=True)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    rows = np.linspace(0, s.nc - 1, 48).astype(np.int64)
+    pairs = np.stack([np.repeat(rows, s.np_), np.tile(np.arange(s.np_), rows.size)], axis=1)
+    E, ovis, _ = oracle.irradiance_scene(s, pairs=pairs, bvh=True, flags=False)
+    ri = torch.from_numpy(rows).cuda()
+    Ag = A.index_select(0, ri).cpu().numpy().reshape(-1)
+    visg = uvc.vis_to_bool(vis.index_select(1, ri).contiguous(), s.np_).reshape(-1, s.lamp.K)
+    flag = np.zeros(pairs.shape[0], np.uint8)
+    diff = np.flatnonzero((visg != ovis.astype(bool)).any(axis=1))
+    if diff.size:
+        _, _, f = oracle.irradiance_scene(s, pairs=pairs[diff])
+        flag[diff] = f
+    st = compare_irradiance(Ag, visg, E, ovis, flag)
+    assert st["pairs"] == 48 * s.np_ and 0.05 < st["visible_frac"] < 0.95
+    sc.free()
+
+
 def test_lda_larger_than_np_leaves_padding_untouched():
     s = tiny_room(n_cand=5)
     sc = build(s)

@@ -17,7 +17,7 @@ MUTANTS = {
     "two_pi": ("const double four_pi = 4.0 * M_PI;", "const double four_pi = 2.0 * M_PI;"),
     "ignore_source_weights": ("(double)weights[m] * power", "power"),
     "facing_sign_flipped": ("if (nv_ > 0.0 && d > 0.0) {", "if (nv_ < 0.0 && d > 0.0) {"),
-    "no_exclusion": ("if (t == ex0 || t == ex1) continue;\n                    if (segment_meets_triangle",
+    "no_exclusion": ("if (t == ex0 || t == ex1) continue;\n                            if (segment_meets_triangle",
                      "if (segment_meets_triangle"),
     "ray_not_segment": ("return tau > 0.0 && tau < 1.0;", "return tau > 0.0;"),
     "closed_segment": ("return tau > 0.0 && tau < 1.0;", "return tau >= 0.0 && tau <= 1.0;"),
