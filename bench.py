@@ -328,6 +328,7 @@ def run_ours(args):
         out["e2e"] = run_e2e(args, s, host, lamp, streamed, nvec, world, dist if world > 1 else None)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
+        out["cpu_baseline_bvh"] = cpu_baseline_bvh(s, args.cpu_seconds)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -441,6 +442,31 @@ def cpu_baseline(s, seconds: float):
             "sample": f"{n} seeded (candidate, patch) pairs of the same workload, K={s.lamp.K} sources, "
                       f"brute force against all {s.nt} triangles, FP64, {dt:.1f} s",
             "threads_available": oracle.max_threads()}
+
+
+def cpu_baseline_bvh(s, seconds: float):
+    """The oracle's CPU-BVH mode (the same entries as its brute force) on all
+    host cores, on whole rows of the workload's matrix sized to about
+    `seconds` of CPU time."""
+    import oracle
+    threads = os.cpu_count() or 1
+
+    def rows_rate(rows):
+        pairs = np.stack([np.repeat(rows, s.np_), np.tile(np.arange(s.np_), rows.size)], axis=1)
+        t0 = time.perf_counter()
+        oracle.irradiance_scene(s, pairs=pairs, flags=False, threads=threads, bvh=True)
+        return time.perf_counter() - t0
+
+    rng = np.random.default_rng(104)
+    probe = min(s.nc, 8)   # enough rows that thread start-up does not dominate the estimate
+    dt = rows_rate(rng.choice(s.nc, probe, replace=False))
+    nrows = int(min(s.nc, max(1, probe * seconds / max(dt, 1e-6))))
+    rows = np.sort(rng.choice(s.nc, nrows, replace=False))
+    dt = rows_rate(rows)
+    rate = nrows * s.np_ / dt
+    return {"value": round(rate / 1e9, 9), "unit": UNIT, "cores": threads, "kind": "oracle (CPU-BVH mode)",
+            "sample": f"{nrows} seeded whole rows ({nrows * s.np_} (candidate, patch) pairs) of the same workload, "
+                      f"K={s.lamp.K} sources, FP64 bounding-volume hierarchy over {s.nt} triangles, {dt:.1f} s"}
 
 
 def run_reference(args):
