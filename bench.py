@@ -289,8 +289,32 @@ def run_ours(args):
     # instrumented run (outside timing) for the dominant kernel's algorithmic work
     sc = scenes[-1]
     if streamed:
-        roof = None
-        cnt = None
+        # the streamed kernel runs the same per-(candidate, patch) search as the
+        # matrix kernel, plus nvec FMAs per pair for the dwell-time products:
+        # operations from the instrumented matrix run on evenly spaced rows
+        rows = np.unique(np.linspace(0, s.nc - 1, min(s.nc, 48)).astype(np.int64))
+        ri = torch.from_numpy(rows).to(dev)
+        A_s = torch.empty((rows.size, s.np_), dtype=torch.float32, device=dev)
+        cnt = uvc.irradiance_counters(sc, d["cand"].index_select(0, ri).contiguous(), lamp, A=A_s)
+        del A_s
+        pairs_s = rows.size * s.np_
+        ops_s = (cnt["lane_box_tests"] * OPS_BOX_TEST + cnt["lane_tri_tests"] * OPS_TRI_TEST
+                 + pairs_s * s.lamp.K * OPS_SEGMENT_SETUP + cnt["lane_wedge_box_tests"] * OPS_WEDGE_BOX_TEST
+                 + cnt["lane_wedge_plane_tests"] * OPS_WEDGE_PLANE_TEST)
+        ops = int(ops_s * pairs / pairs_s) + pairs * nvec
+        irr_s = (sum(irr_ms) / len(irr_ms)) * 1e-3
+        pk = measured_peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * sm_max * 1e6 / 1e12
+        achieved = ops / irr_s / 1e12
+        traffic = measured_traffic(pairs, STREAMED_SUMMARY)
+        roof = {"bound": "alu", "kernel": "k_streamed", "achieved": round(achieved, 3), "peak": round(peak, 3),
+                "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
+                "ops_per_launch": ops, "launch_ms": round(irr_s * 1e3, 3),
+                "ops_sample": f"search operations counted on {rows.size} evenly spaced rows (uvc_irradiance_counters) "
+                              f"and scaled to all {s.nc} candidates, plus {nvec} FMAs per pair",
+                "counters_sample": cnt}
     else:
         cnt = uvc.irradiance_counters(sc, d["cand"], lamp, A=A)
         segments = pairs * s.lamp.K
@@ -302,7 +326,7 @@ def run_ours(args):
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         peak = 152 * 128 * sm_max * 1e6 / 1e12      # lane-instructions per second, in T/s
         achieved = ops / irr_s / 1e12
-        traffic = measured_traffic(pairs)
+        traffic = measured_traffic(pairs, TRAFFIC_SUMMARY)
         roof = {"bound": "alu", "kernel": "k_irradiance", "achieved": round(achieved, 3),
                 "peak": round(peak, 3), "unit": "Tops/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
@@ -389,15 +413,18 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
 
 _KERNEL_FILES = ("irradiance.cu", "traverse.cuh", "uvc_internal.cuh")
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "k_irradiance_ward.txt")
+STREAMED_SUMMARY = os.path.join(ROOT, "profiles", "k_streamed_large.txt")
 
 
-def measured_traffic(pairs):
+def measured_traffic(pairs, summary):
     """DRAM bytes of one full launch, scaled from the committed ncu summary of
     a smaller launch of the same kernel (null once the kernel has changed)."""
     try:
-        kv = dict(line.split(":", 1) for line in open(TRAFFIC_SUMMARY) if ":" in line)
+        kv = dict(line.split(":", 1) for line in open(summary) if ":" in line)
         if kv.get("kernel_source_hash", "").strip() != kernel_hash():
             return None
+        if "dram_bytes_per_launch" in kv:   # traffic that does not grow with the pairs
+            return float(kv["dram_bytes_per_launch"])
         return float(kv["dram_bytes_per_pair"]) * pairs
     except (OSError, ValueError, KeyError):
         return None
