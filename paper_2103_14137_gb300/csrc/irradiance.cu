@@ -226,8 +226,9 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
     int grid = 0;
     int rc = streamed_grid(S, lamp, &grid);
     if (rc != UVC_OK) return rc;
-    // enough (chunk, block) tasks to fill the persistent grid several times over
-    const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
+    // enough (chunk, block) tasks that every warp of the persistent grid gets
+    // some 32 of them: with few, large tasks the last ones leave SMs idle
+    const int64_t want = 32 * (int64_t)grid * kWarpsPerBlock;
     int64_t nsplit = (want + njb - 1) / njb;
     nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (nc + 31) / 32));
     const int64_t cap = (int64_t(1) << 31) / (4 * (int64_t)nvec * S.np);   // partials <= 2 GiB
