@@ -141,9 +141,11 @@ int uvc_free_scene(uvc_scene* scene);
  * source by source with the same segment test; they can differ only where a
  * segment grazes a triangle lying in the patch's own plane.  The setting is
  * read when a call (or uvc_batch_create) converts its lamp.
- * Returns the previous setting (0 or 1), or UVC_E_INVAL for other values.
+ *   enable    0 or 1
+ *   previous  HOST int32, may be NULL: receives the setting before the call
+ * Returns UVC_OK, or UVC_E_INVAL (setting unchanged) for other values of enable.
  */
-int uvc_set_wedge_traversal(int32_t enable);
+int uvc_set_wedge_traversal(int32_t enable, int32_t* previous);
 
 /*
  * uvc_irradiance_matrix - the irradiance matrix (Sec. IV-C, Eq. (4) and (7)):

@@ -90,9 +90,11 @@ int uvc_free_scene(uvc_scene* scene) {
     return uvc::status_from_cuda(e);
 }
 
-int uvc_set_wedge_traversal(int32_t enable) {
+int uvc_set_wedge_traversal(int32_t enable, int32_t* previous) {
     if (enable != 0 && enable != 1) return UVC_E_INVAL;
-    return uvc::g_wedge.exchange(enable);
+    const int prev = uvc::g_wedge.exchange(enable);
+    if (previous) *previous = prev;
+    return UVC_OK;
 }
 
 int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc, const uvc_lamp* lamp, float* A,

@@ -208,7 +208,10 @@ int irradiance_counters(const uvc_scene* sc, const float* cand, int64_t nc, cons
     cudaError_t e = cudaMemsetAsync(dctr, 0, sizeof(unsigned long long) * kNumCounters, stream);
     if (e == cudaSuccess) {
         const int rc = launch_irradiance<true>(S, cand, nc, lamp, A, lda, nullptr, dctr, stream);
-        if (rc != UVC_OK) e = cudaErrorLaunchFailure;
+        if (rc != UVC_OK) {
+            cudaFreeAsync(dctr, stream);
+            return rc;
+        }
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out6, dctr, sizeof(unsigned long long) * kNumCounters, cudaMemcpyDeviceToHost, stream);

@@ -71,7 +71,7 @@ def library():
         "uvc_fluence_streamed_noalloc": [P, P, i64, ctypes.POINTER(_Lamp), P, i32, P, P],
         "uvc_coverage": [P, P, i32, ctypes.c_float, P, P, P],
         "uvc_scene_status": [P, P],
-        "uvc_set_wedge_traversal": [i32],
+        "uvc_set_wedge_traversal": [i32, ctypes.POINTER(i32)],
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "uvc_scene_export_bvh": [P, P, P, P, P],
     }
@@ -251,10 +251,9 @@ def set_wedge_traversal(enable: bool) -> bool:
     """Search a vertical line lamp's sources as one wedge per (candidate,
     patch) (True, the default) or source by source (False); returns the
     previous setting (see uvc_set_wedge_traversal)."""
-    rc = library().uvc_set_wedge_traversal(1 if enable else 0)
-    if rc not in (0, 1):
-        _check(rc, "uvc_set_wedge_traversal")
-    return bool(rc)
+    prev = ctypes.c_int32(0)
+    _check(library().uvc_set_wedge_traversal(1 if enable else 0, ctypes.byref(prev)), "uvc_set_wedge_traversal")
+    return bool(prev.value)
 
 
 def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> dict:

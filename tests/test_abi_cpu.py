@@ -112,7 +112,9 @@ def test_product_never_imports_oracle():
 def test_wedge_switch_is_host_only(lib):
     """uvc_set_wedge_traversal returns the previous setting and rejects other values."""
     import paper_2103_14137_gb300 as uvc
-    assert lib.uvc_set_wedge_traversal(2) == 1          # UVC_E_INVAL
-    prev = uvc.set_wedge_traversal(False)
-    assert prev is True and uvc.set_wedge_traversal(True) is False
-    assert lib.uvc_set_wedge_traversal(1) == 1          # was on
+    prev = ctypes.c_int32(-1)
+    assert lib.uvc_set_wedge_traversal(2, ctypes.byref(prev)) == 1      # UVC_E_INVAL, nothing written
+    assert prev.value == -1
+    assert uvc.set_wedge_traversal(False) is True and uvc.set_wedge_traversal(True) is False
+    assert lib.uvc_set_wedge_traversal(1, ctypes.byref(prev)) == 0 and prev.value == 1
+    assert lib.uvc_set_wedge_traversal(1, None) == 0
