@@ -49,6 +49,7 @@ typedef struct CUstream_st* uvc_stream_t; /* same type as cudaStream_t */
 #define UVC_E_STACK 4    /* traversal stack would overflow (tree deeper than supported) */
 #define UVC_E_TIMEOUT 5  /* a traversal hit its node-visit cap; affected entries are NaN */
 #define UVC_E_SCRATCH 6  /* nvec*np too large for uvc_fluence_streamed_noalloc's fixed scratch */
+#define UVC_E_BOUNDS 7   /* checked build only: a traversal met an index out of range (entries NaN) */
 
 #define UVC_MAX_SOURCES 32
 
@@ -502,6 +503,16 @@ int uvc_mlp_forward(uvc_mlp* model, const float* x, int32_t B, float* logit, uvc
 int uvc_mlp_train_step(uvc_mlp* model, const float* x, const float* y, const float* w, int32_t B, float lr,
                        float* loss, uvc_stream_t stream);
 int uvc_mlp_grads(const uvc_mlp* model, float* host, int64_t n);
+
+/*
+ * uvc_library_flags - how this copy of the library was built: bit
+ * UVC_LIB_CHECKED is set for the checked build (compiled with UVC_CHECKED),
+ * whose traversals test every node, leaf and cached-triangle index before use
+ * and report violations as UVC_E_BOUNDS in the scene's status word (a
+ * stand-in for a memory checker; the normal build has no checks).
+ */
+#define UVC_LIB_CHECKED 1u
+uint32_t uvc_library_flags(void);
 
 /* uvc_status_string - static text for a status code (never NULL). */
 const char* uvc_status_string(int status);

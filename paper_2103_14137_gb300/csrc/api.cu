@@ -236,6 +236,14 @@ int uvc_probe_lost(const float* A, int64_t nc, int64_t lda, int64_t np, const in
     return uvc::probe_lost(A, nc, lda, np, idx, k, area, lost, out, (cudaStream_t)stream);
 }
 
+uint32_t uvc_library_flags(void) {
+#ifdef UVC_CHECKED
+    return UVC_LIB_CHECKED;
+#else
+    return 0u;
+#endif
+}
+
 const char* uvc_status_string(int status) {
     switch (status) {
         case UVC_OK: return "ok";
@@ -244,6 +252,7 @@ const char* uvc_status_string(int status) {
         case UVC_E_CUDA: return "CUDA runtime error";
         case UVC_E_STACK: return "traversal stack overflow";
         case UVC_E_TIMEOUT: return "traversal exceeded its node-visit cap";
+        case UVC_E_BOUNDS: return "traversal index out of range (checked build)";
         case UVC_E_SCRATCH: return "problem too large for the fixed scratch of the allocation-free call";
         default: return "unknown status";
     }

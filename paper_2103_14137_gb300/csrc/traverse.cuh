@@ -27,6 +27,22 @@ constexpr float kFourPi = 12.566370614359172f;
 // of (b - o) * (1/d) (three roundings) with a wide margin.
 constexpr float kFarScale = 1.0f + 9.5367431640625e-07f;
 
+// Checked build (UVC_CHECKED): every node, leaf and cached-triangle index of the
+// traversals is tested against its array before it is used; an index out of
+// range sets UVC_E_BOUNDS in the scene's status word and the access is
+// skipped (the search ends for the lanes concerned, whose entries become NaN).
+// The normal build compiles no checks.
+#ifdef UVC_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+__device__ __forceinline__ bool out_of_range(int* status, int idx, int n) {
+    if (!kChecked || (idx >= 0 && idx < n)) return false;
+    atomicCAS(status, 0, UVC_E_BOUNDS);
+    return true;
+}
+
 struct SceneView {
     const float4* __restrict__ tri;
     const Node4* __restrict__ nodes4;
@@ -198,6 +214,10 @@ __device__ __forceinline__ uint32_t traverse4(const SceneView& S, const Ray& r, 
             if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
             break;
         }
+        if (out_of_range(S.status, node, S.nt - 1)) {
+            failed = alive;
+            break;
+        }
         const Node4* nd = S.nodes4 + node;
         const char* b = reinterpret_cast<const char*>(nd);
         const char *bnx = b + onx, *bfx = b + (8 - onx), *bny = b + 16 + ony, *bfy = b + 16 + (8 - ony);
@@ -221,6 +241,11 @@ __device__ __forceinline__ uint32_t traverse4(const SceneView& S, const Ray& r, 
             const uint32_t m = __ballot_sync(kFull, (nib >> c) & 1u) & alive;
             if (!m) continue;
             const int leaf = ~pick4(rr, c);
+            if (out_of_range(S.status, leaf, S.nt)) {
+                failed = alive;
+                alive = 0;
+                break;
+            }
             if (COUNT) { ++c_leaf; c_tri += __popc(m); }
             const uint32_t h = test_leaf(S, leaf, r, m, lane);
             if ((h >> lane) & 1u) hit_tri = leaf;
@@ -282,6 +307,47 @@ __device__ uint32_t warp_occluded(const SceneView& S, const Ray& r, uint32_t ali
     return traverse4<COUNT>(S, r, alive, stack, lane, failed, ctr, hit_tri);
 }
 
+// One source's terms for the patch point s (normal n): v = o - s as the
+// rounded difference h plus its exact error (TwoSum), <n, v> with an
+// error-free dot product (TwoProduct + TwoSum) rounded once, and |h|^2.  Both
+// traversal paths call this, so their Eq. (7) terms agree bit for bit.
+__device__ __forceinline__ void source_terms(float ox, float oy, float oz, float4 s4, float4 n4, float& hx, float& hy,
+                                             float& hz, float& nv, float& d2) {
+    hx = __fsub_rn(ox, s4.x);
+    hy = __fsub_rn(oy, s4.y);
+    hz = __fsub_rn(oz, s4.z);
+    const float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
+    const float lx = __fadd_rn(__fsub_rn(ox, __fsub_rn(hx, qx)), __fsub_rn(-s4.x, qx));
+    const float ly = __fadd_rn(__fsub_rn(oy, __fsub_rn(hy, qy)), __fsub_rn(-s4.y, qy));
+    const float lz = __fadd_rn(__fsub_rn(oz, __fsub_rn(hz, qz)), __fsub_rn(-s4.z, qz));
+    const float p = __fmul_rn(n4.x, hx);
+    float err = __fmaf_rn(n4.x, hx, -p);
+    err = __fmaf_rn(n4.x, lx, err);
+    float acc = p;
+    {
+        const float p2 = __fmul_rn(n4.y, hy);
+        const float e2 = __fmaf_rn(n4.y, hy, -p2);
+        const float s = __fadd_rn(acc, p2);
+        const float z = __fsub_rn(s, acc);
+        const float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p2, z));
+        acc = s;
+        err = __fadd_rn(err, __fadd_rn(q, e2));
+        err = __fmaf_rn(n4.y, ly, err);
+    }
+    {
+        const float p3 = __fmul_rn(n4.z, hz);
+        const float e3 = __fmaf_rn(n4.z, hz, -p3);
+        const float s = __fadd_rn(acc, p3);
+        const float z = __fsub_rn(s, acc);
+        const float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p3, z));
+        acc = s;
+        err = __fadd_rn(err, __fadd_rn(q, e3));
+        err = __fmaf_rn(n4.z, lz, err);
+    }
+    nv = __fadd_rn(acc, err);
+    d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+}
+
 // The patch of one lane: sample point, normal, excluded triangles.
 struct PatchLane {
     float4 s, n;   // n.w = clearance (metres)
@@ -321,39 +387,8 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
     bool bad = false;
     for (int m = 0; m < L.K; ++m) {
         const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
-        // v = o - s exactly as hi + lo (TwoSum)
-        float hx = __fsub_rn(ox, s4.x), hy = __fsub_rn(oy, s4.y), hz = __fsub_rn(oz, s4.z);
-        float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
-        float lx = __fadd_rn(__fsub_rn(ox, __fsub_rn(hx, qx)), __fsub_rn(-s4.x, qx));
-        float ly = __fadd_rn(__fsub_rn(oy, __fsub_rn(hy, qy)), __fsub_rn(-s4.y, qy));
-        float lz = __fadd_rn(__fsub_rn(oz, __fsub_rn(hz, qz)), __fsub_rn(-s4.z, qz));
-        // <n, v> with TwoProduct / TwoSum (error-free dot product)
-        float p = __fmul_rn(n4.x, hx);
-        float err = __fmaf_rn(n4.x, hx, -p);
-        err = __fmaf_rn(n4.x, lx, err);
-        float acc = p;
-        {
-            float p2 = __fmul_rn(n4.y, hy);
-            float e2 = __fmaf_rn(n4.y, hy, -p2);
-            float s = __fadd_rn(acc, p2);
-            float z = __fsub_rn(s, acc);
-            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p2, z));
-            acc = s;
-            err = __fadd_rn(err, __fadd_rn(q, e2));
-            err = __fmaf_rn(n4.y, ly, err);
-        }
-        {
-            float p3 = __fmul_rn(n4.z, hz);
-            float e3 = __fmaf_rn(n4.z, hz, -p3);
-            float s = __fadd_rn(acc, p3);
-            float z = __fsub_rn(s, acc);
-            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p3, z));
-            acc = s;
-            err = __fadd_rn(err, __fadd_rn(q, e3));
-            err = __fmaf_rn(n4.z, lz, err);
-        }
-        const float nv = __fadd_rn(acc, err);
-        const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+        float hx, hy, hz, nv, d2;
+        source_terms(ox, oy, oz, s4, n4, hx, hy, hz, nv, d2);
         const float d = sqrtf(d2);
         const bool facing = P.valid && nv > 0.f && d2 > 0.f;
         Ray r;
@@ -367,7 +402,7 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
         r.tend = cut > 0.f ? 1.f - cut * __frcp_rn(d) : 1.f;
         const bool settled = facing && r.tend <= 0.f;
         bool cached_hit = false;
-        if (facing && !settled && cache >= 0) {
+        if (facing && !settled && cache >= 0 && !out_of_range(S.status, cache, S.nt)) {
             const float4* t = S.tri + 3 * (size_t)cache;
             cached_hit = seg_tri(r, __ldg(t), __ldg(t + 1), __ldg(t + 2));
         }
@@ -545,10 +580,15 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
     int top = 0, node = 0, visits = 0;
     unsigned long long c_leaf = 0, c_box = 0, c_tri = 0, c_plane = 0;
     const float delta = S.cut_eps;
+    bool oob = false;   // checked build: this lane met an index out of range
     while (true) {
         if (++visits > S.visit_cap) {
             failed = alive;
             if (lane == 0) atomicCAS(S.status, 0, UVC_E_TIMEOUT);
+            break;
+        }
+        if (out_of_range(S.status, node, S.nt - 1)) {
+            failed = alive;
             break;
         }
         const Node4* nd = S.nodes4 + node;
@@ -577,6 +617,12 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
                 const int c = __ffs(mine) - 1;
                 mine &= mine - 1;
                 const int leaf = ~pick4(rr, c);
+                if (out_of_range(S.status, leaf, S.nt)) {
+                    oob = true;
+                    want = 0u;
+                    mine = 0u;
+                    continue;
+                }
                 const float4* t = S.tri + 3 * (size_t)leaf;
                 const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
                 const int id = __float_as_int(ta.w);
@@ -609,6 +655,7 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
                 if (!want) mine = 0u;
             }
         }
+        if (kChecked) failed |= __ballot_sync(kFull, oob);
         alive &= __ballot_sync(kFull, want != 0u);
         if (!alive) break;
         unsigned inner = hit & (unsigned)mm.y;
@@ -665,37 +712,8 @@ __device__ __forceinline__ uint32_t wedge_setup_patch(const SceneView& S, const 
     gy = 0.f;
     for (int m = 0; m < L.K; ++m) {
         const float ox = __fadd_rn(cx, L.ox[m]), oy = __fadd_rn(cy, L.oy[m]), oz = __fadd_rn(cz, L.oz[m]);
-        float hx = __fsub_rn(ox, s4.x), hy = __fsub_rn(oy, s4.y), hz = __fsub_rn(oz, s4.z);
-        float qx = __fsub_rn(hx, ox), qy = __fsub_rn(hy, oy), qz = __fsub_rn(hz, oz);
-        float lx = __fadd_rn(__fsub_rn(ox, __fsub_rn(hx, qx)), __fsub_rn(-s4.x, qx));
-        float ly = __fadd_rn(__fsub_rn(oy, __fsub_rn(hy, qy)), __fsub_rn(-s4.y, qy));
-        float lz = __fadd_rn(__fsub_rn(oz, __fsub_rn(hz, qz)), __fsub_rn(-s4.z, qz));
-        float p = __fmul_rn(n4.x, hx);
-        float err = __fmaf_rn(n4.x, hx, -p);
-        err = __fmaf_rn(n4.x, lx, err);
-        float acc = p;
-        {
-            float p2 = __fmul_rn(n4.y, hy);
-            float e2 = __fmaf_rn(n4.y, hy, -p2);
-            float s = __fadd_rn(acc, p2);
-            float z = __fsub_rn(s, acc);
-            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p2, z));
-            acc = s;
-            err = __fadd_rn(err, __fadd_rn(q, e2));
-            err = __fmaf_rn(n4.y, ly, err);
-        }
-        {
-            float p3 = __fmul_rn(n4.z, hz);
-            float e3 = __fmaf_rn(n4.z, hz, -p3);
-            float s = __fadd_rn(acc, p3);
-            float z = __fsub_rn(s, acc);
-            float q = __fadd_rn(__fsub_rn(acc, __fsub_rn(s, z)), __fsub_rn(p3, z));
-            acc = s;
-            err = __fadd_rn(err, __fadd_rn(q, e3));
-            err = __fmaf_rn(n4.z, lz, err);
-        }
-        const float nv = __fadd_rn(acc, err);
-        const float d2 = __fmaf_rn(hx, hx, __fmaf_rn(hy, hy, __fmul_rn(hz, hz)));
+        float hx, hy, hz, nv, d2;
+        source_terms(ox, oy, oz, s4, n4, hx, hy, hz, nv, d2);
         const float d = sqrtf(d2);
         const bool fac = P.valid && nv > 0.f && d2 > 0.f;
         Ray r;
@@ -760,7 +778,7 @@ __device__ __forceinline__ uint32_t wedge_search(const SceneView& S, const LampD
     w.mz = delta * dmax / gn;
     // the lane's last occluder first, against the searching sources it can reach
     uint32_t occl = 0;
-    if (want && cache >= 0) {
+    if (want && cache >= 0 && !out_of_range(S.status, cache, S.nt)) {
         const float4* t = S.tri + 3 * (size_t)cache;
         const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
         const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));

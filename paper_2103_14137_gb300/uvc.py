@@ -14,10 +14,12 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libuvc.so")
+# UVC_LIB_PATH selects another build of the library (the checked build in its test)
+LIB_PATH = os.environ.get("UVC_LIB_PATH") or os.path.join(_HERE, "libuvc.so")
 MAX_SOURCES = 32
 
-UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT, UVC_E_SCRATCH = range(7)
+UVC_OK, UVC_E_INVAL, UVC_E_NOMEM, UVC_E_CUDA, UVC_E_STACK, UVC_E_TIMEOUT, UVC_E_SCRATCH, UVC_E_BOUNDS = range(8)
+UVC_LIB_CHECKED = 1
 UVC_BUILD_LBVH_ONLY = 1
 
 
@@ -108,10 +110,17 @@ def library():
     lib.uvc_probe_features_work_bytes.restype = ctypes.c_size_t
     lib.uvc_mlp_param_count.argtypes = [P]
     lib.uvc_mlp_param_count.restype = i64
+    lib.uvc_library_flags.argtypes = []
+    lib.uvc_library_flags.restype = ctypes.c_uint32
     lib.uvc_status_string.argtypes = [ctypes.c_int]
     lib.uvc_status_string.restype = ctypes.c_char_p
     _lib = lib
     return lib
+
+
+def library_flags() -> int:
+    """Build flags of the loaded library (UVC_LIB_CHECKED for the checked build)."""
+    return int(library().uvc_library_flags())
 
 
 def status_string(status: int) -> str:

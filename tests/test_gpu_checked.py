@@ -1,0 +1,28 @@
+"""The checked build (UVC_CHECKED): the traversal kernels test every node,
+leaf and cached-triangle index before use and report a violation as
+UVC_E_BOUNDS in the scene's status word.  compute-sanitizer is not available
+here, so this build stands in for it: the irradiance, wedge, batch and
+area-mean GPU suites run against it in a child process and must pass, every
+scene status included (the suites assert scene_status == 0)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+pytestmark = pytest.mark.gpu
+
+
+def test_checked_build_passes_the_traversal_suites():
+    from paper_2103_14137_gb300 import _build
+    so = _build.build(checked=True)
+    env = dict(os.environ, UVC_LIB_PATH=so)
+    flags = subprocess.run([sys.executable, "-c", "import paper_2103_14137_gb300 as u; print(u.uvc.library_flags())"],
+                           cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert flags.returncode == 0 and flags.stdout.strip() == "1", flags.stdout + flags.stderr
+    suites = ["tests/test_gpu_irradiance.py", "tests/test_gpu_wedge.py", "tests/test_gpu_batch.py",
+              "tests/test_gpu_area_mean.py", "tests/test_gpu_fluence.py"]
+    r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-m", "gpu", "-x", "-q", "-p", "no:cacheprovider"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=1800)
+    assert r.returncode == 0, r.stdout[-4000:] + r.stderr[-2000:]
