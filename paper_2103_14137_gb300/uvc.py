@@ -137,6 +137,19 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _matrix_rows(x: torch.Tensor, name, nrows: int):
+    """A float32 CUDA matrix with unit column stride whose rows may be padded
+    (a view of the first columns of a wider buffer): (pointer, row stride)."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float32 CUDA tensor")
+    if x.shape[0] != nrows:
+        raise ValueError(f"{name} must have {nrows} rows, got {x.shape[0]}")
+    if x.numel() and x.stride(1) != 1:
+        raise ValueError(f"{name} must have unit column stride")
+    lda = max(x.stride(0), x.shape[1]) if x.shape[0] > 1 else x.shape[1]
+    return ctypes.c_void_p(x.data_ptr() if x.numel() else 0), lda
+
+
 def _dev(x: torch.Tensor, dtype, name, shape=None):
     if not isinstance(x, torch.Tensor) or not x.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
@@ -245,9 +258,9 @@ def irradiance_matrix(scene: Scene, cand, lamp: Lamp, A=None, vis=None, with_vis
         raise ValueError("A must be (nc, lda)")
     vptr = None if vis is None else _dev(vis, torch.int32, "vis", (lamp.K, nc, (scene.np + 31) // 32))
     L = lamp._c()
+    aptr, lda = _matrix_rows(A, "A", nc)
     rc = library().uvc_irradiance_matrix(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
-                                         ctypes.byref(L), _dev(A, torch.float32, "A"), A.shape[1], vptr,
-                                         _stream(stream))
+                                         ctypes.byref(L), aptr, lda, vptr, _stream(stream))
     _check(rc, "uvc_irradiance_matrix")
     return A, vis
 
@@ -272,9 +285,10 @@ def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> 
         A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
     out = np.zeros(len(COUNTER_NAMES), np.uint64)
     L = lamp._c()
+    aptr, lda = _matrix_rows(A, "A", nc)
     rc = library().uvc_irradiance_counters(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
-                                           ctypes.byref(L), _dev(A, torch.float32, "A"), A.shape[1],
-                                           ctypes.c_void_p(out.ctypes.data), _stream(stream))
+                                           ctypes.byref(L), aptr, lda, ctypes.c_void_p(out.ctypes.data),
+                                           _stream(stream))
     _check(rc, "uvc_irradiance_counters")
     return dict(zip(COUNTER_NAMES, (int(x) for x in out)))
 
@@ -323,12 +337,13 @@ def irradiance_raster(scene: Scene, tri_normal, cand, lamp: Lamp, R: int = 512, 
 
 
 def fluence(scene: Scene, A, t, mu=None, stream=None):
-    """mu (nvec, np) = t (nvec, nc) @ A (nc, np)."""
+    """mu (nvec, np) = t (nvec, nc) @ A (nc, np); A may be a view of the
+    first np columns of a wider buffer (padded rows)."""
     nvec, nc = t.shape
     if mu is None:
         mu = torch.empty((nvec, scene.np), dtype=torch.float32, device=t.device)
-    rc = library().uvc_fluence(scene.handle, _dev(A, torch.float32, "A"), nc, A.shape[1] if A.dim() == 2 else 0,
-                               _dev(t, torch.float32, "t", (nvec, nc)), nvec,
+    aptr, lda = _matrix_rows(A, "A", nc)
+    rc = library().uvc_fluence(scene.handle, aptr, nc, lda, _dev(t, torch.float32, "t", (nvec, nc)), nvec,
                                _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
     _check(rc, "uvc_fluence")
     return mu

@@ -6,7 +6,7 @@ import torch
 import oracle
 import paper_2103_14137_gb300 as uvc
 from synth import dwell_vectors, tiny_room
-from tests.gpu_util import T, build, lamp_of
+from tests.gpu_util import T, build, build_arrays, lamp_of
 
 pytestmark = pytest.mark.gpu
 MU_TOL = 1e-5
@@ -27,6 +27,55 @@ def test_fluence_random_matrix_ragged_sizes():
         t = rng.uniform(0, 60, size=(nvec, nc)).astype(np.float32)
         mu = uvc.fluence(sc, T(A), T(t)).cpu().numpy()
         assert _rel(mu, oracle.fluence(A, t)) <= MU_TOL, (nc, nvec)
+    sc.free()
+
+
+def _rows_of(nc, n, lda):
+    """(nc, n) view of a (nc, lda) buffer (padded rows)."""
+    return torch.empty((nc, lda), dtype=torch.float32, device="cuda")[:, :n]
+
+
+@pytest.mark.parametrize("n", [3, 640, 641, 643, 988])
+def test_fluence_padded_rows_match_unpadded(n):
+    """A given as a view of wider rows (row stride a multiple of 4 floats, so
+    8-byte loads) and with odd or unpadded strides give the same fluence bit
+    for bit and match the oracle, including column tiles with 1-3 leftover
+    columns and fewer than 4 patches."""
+    rng = np.random.default_rng(n)
+    s = tiny_room(n_cand=3)
+    sc = build_arrays(s.verts, s.tris, s.centroid[:n], s.normal[:n], s.area[:n], s.excl[:n])
+    for nc, nvec in ((1, 1), (77, 3), (2000, 16), (301, 37)):
+        A = rng.uniform(0, 10, size=(nc, n)).astype(np.float32)
+        A[rng.uniform(size=A.shape) < 0.3] = 0.0
+        t = rng.uniform(0, 60, size=(nvec, nc)).astype(np.float32)
+        Ab = _rows_of(nc, n, (n + 3) // 4 * 4)
+        Ab.copy_(T(A))
+        Ap = _rows_of(nc, n, n if n % 2 else n + 1)   # odd stride: 4-byte loads
+        Ap.copy_(T(A))
+        mu_b = uvc.fluence(sc, Ab, T(t))
+        mu_p = uvc.fluence(sc, Ap, T(t))
+        torch.cuda.synchronize()
+        assert uvc.scene_status(sc) == 0
+        assert torch.equal(mu_b, mu_p), (n, nc, nvec)
+        assert _rel(mu_b.cpu().numpy(), oracle.fluence(A, t)) <= MU_TOL, (n, nc, nvec)
+    sc.free()
+
+
+def test_fluence_padded_rows_ward_size():
+    """The ward's shape (2,000 x 102,030, 16 vectors, ragged last tile of 14
+    columns) with even and odd row strides: bit-identical."""
+    from synth import ward_room
+    s = ward_room(n_cand=4)
+    sc = build(s)
+    g = torch.Generator(device="cuda").manual_seed(3)
+    Ab = _rows_of(2000, s.np_, (s.np_ + 3) // 4 * 4)
+    Ab.copy_(torch.rand((2000, s.np_), generator=g, device="cuda"))
+    Ap = _rows_of(2000, s.np_, s.np_ + 1)
+    Ap.copy_(Ab)
+    t = torch.rand((16, 2000), generator=g, device="cuda") * 60
+    mu_b, mu_p = uvc.fluence(sc, Ab, t), uvc.fluence(sc, Ap, t)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0 and torch.equal(mu_b, mu_p)
     sc.free()
 
 
