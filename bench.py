@@ -430,11 +430,20 @@ def measured_traffic(pairs, summary):
         return None
 
 
+def _code_only(text: str) -> str:
+    """Source text without comments and whitespace, so that a comment edit does
+    not count as a change of the kernel."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return "".join(text.split())
+
+
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in _KERNEL_FILES:
-        h.update(open(os.path.join(ROOT, "paper_2103_14137_gb300", "csrc", f), "rb").read())
+        h.update(_code_only(open(os.path.join(ROOT, "paper_2103_14137_gb300", "csrc", f)).read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -434,9 +434,11 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
 // source still searching).  One packet traversal of the wedges replaces the K
 // segment traversals: a child box is entered when it meets the lane's wedge,
 // widened by delta, and every triangle reached is tested, with the same
-// watertight segment test, against each source still searching; a source
-// stops at its first hit, a lane when all its sources have stopped, and the
-// wedge narrows as its outer sources stop.
+// watertight segment test, against each source still searching that can meet
+// it: none if the triangle lies entirely on one side of the wedge's vertical
+// plane (farther than delta), else those in its lamp-height interval
+// (lamp_interval).  A source stops at its first hit, a lane when all its
+// sources have stopped, and the wedge narrows as its outer sources stop.
 //
 // Every triangle that a source's own segment traversal would reach is reached
 // here (each segment lies inside the wedge, and delta = 1e-5 D exceeds the
