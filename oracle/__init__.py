@@ -52,6 +52,8 @@ def load_library(path: str):
     lib.uvco_area_mean.argtypes = [P, i64, P, i64, P, P, P, P, P, i64, P, i64, P, P, ctypes.c_int32,
                                    ctypes.c_double, ctypes.c_float, P, i64, ctypes.c_double, P, P, P, ctypes.c_int]
     lib.uvco_area_mean.restype = ctypes.c_int
+    lib.uvco_area_mean_bvh.argtypes = lib.uvco_area_mean.argtypes
+    lib.uvco_area_mean_bvh.restype = ctypes.c_int
     lib.uvco_raster.argtypes = [P, i64, P, i64, P, P, i64, P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_int32,
                                 ctypes.c_double, P, P, ctypes.c_int]
     lib.uvco_raster.restype = ctypes.c_int
@@ -136,10 +138,13 @@ PULL = 1e-3   # check points: patch vertices moved this fraction of the way to t
 
 
 def area_mean(verts, tris, centroid, normal, area, excl, ptri, cand, offsets, weights, power, delta=PULL,
-              pairs=None, eps=None, flags=True, threads=0):
+              pairs=None, eps=None, flags=True, threads=0, bvh=False):
     """FP64 area-mean irradiance (solid-angle closed form where every check
     segment of a source is unoccluded, centroid sample otherwise), see
-    uvco_area_mean.  Returns (E, nclosed, flag) shaped like irradiance()."""
+    uvco_area_mean.  Returns (E, nclosed, flag) shaped like irradiance().
+    bvh=True runs every check segment through the CPU hierarchy
+    (uvco_area_mean_bvh): the same results, fast enough for whole rows of
+    large rooms."""
     lib = _load()
     verts = _c(verts, np.float32).reshape(-1, 3)
     tris = _c(tris, np.int32).reshape(-1, 3)
@@ -165,10 +170,10 @@ def area_mean(verts, tris, centroid, normal, area, excl, ptri, cand, offsets, we
     ncl = np.zeros(npairs, np.uint8)
     flag = np.zeros(npairs, np.uint8) if flags else None
     ptr = lambda a: None if a is None else a.ctypes.data  # noqa: E731
-    rc = lib.uvco_area_mean(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0], ptr(centroid), ptr(normal),
-                            ptr(area), ptr(excl), ptr(ptri), np_, ptr(cand), nc, ptr(offsets), ptr(weights), K,
-                            float(power), float(delta), ptr(pp), npairs, float(eps), ptr(E), ptr(ncl), ptr(flag),
-                            int(threads))
+    fn = lib.uvco_area_mean_bvh if bvh else lib.uvco_area_mean
+    rc = fn(ptr(verts), verts.shape[0], ptr(tris), tris.shape[0], ptr(centroid), ptr(normal), ptr(area), ptr(excl),
+            ptr(ptri), np_, ptr(cand), nc, ptr(offsets), ptr(weights), K, float(power), float(delta), ptr(pp), npairs,
+            float(eps), ptr(E), ptr(ncl), ptr(flag), int(threads))
     if rc != 0:
         raise ValueError(f"oracle: invalid input (rc={rc})")
     return E.reshape(shape), ncl.reshape(shape), None if flag is None else flag.reshape(shape)

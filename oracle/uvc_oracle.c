@@ -537,6 +537,16 @@ static int segment_grazing(const tri64* T, int64_t nt, int32_t ex0, int32_t ex1,
     return bits;
 }
 
+/* Visibility and grazing bits of one segment o -> p, brute force or through the hierarchy. */
+static int seg_visible(const tri64* T, int64_t nt, const bvh64* B, int64_t* stack, int32_t ex0, int32_t ex1, d3 o,
+                       d3 p) {
+    return B ? bvh_visible(B, T, ex0, ex1, o, vsub(p, o), stack) : segment_visible(T, nt, ex0, ex1, o, p);
+}
+static int seg_grazing(const tri64* T, int64_t nt, const bvh64* B, int64_t* stack, int32_t ex0, int32_t ex1, d3 o,
+                       d3 p, double eps) {
+    return B ? bvh_grazing(B, T, ex0, ex1, o, p, eps, stack) : segment_grazing(T, nt, ex0, ex1, o, p, eps);
+}
+
 /*
  * Area-mean irradiance of patches with known geometry (the mean of Eq. (4)
  * over the patch instead of its centroid sample): the flux a triangle
@@ -556,94 +566,145 @@ static int segment_grazing(const tri64* T, int64_t nt, int32_t ex0, int32_t ex1,
  *   nclosed_out[k]   number of sources that used the closed form
  *   flag_out[k]      grazing bits (as above) OR-ed over every check segment
  *                    of the facing sources
+ * With B non-NULL every check segment goes through the hierarchy (same results).
  * Returns 0, or -1 on an index out of range.
  */
+static int area_mean_entries(const tri64* T, int64_t nt, const bvh64* B, const float* centroid, const float* normal,
+                             const float* area, const int32_t* excl, const float* ptri, int64_t np,
+                             const float* cand, const float* offsets, const float* weights, int32_t K,
+                             double power, float delta, const int64_t* pairs, int64_t npairs, double eps,
+                             double* E_out, uint8_t* nclosed_out, uint8_t* flag_out, int nthreads) {
+    const double four_pi = 4.0 * M_PI;
+    int failed = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+#endif
+    {
+        int64_t* stack = B ? (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * B->nnodes + 2)) : NULL;
+        if (B && !stack) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            failed = 1;
+        }
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 8)
+#endif
+        for (int64_t k = 0; k < npairs; ++k) {
+            if (B && !stack) continue;
+            int64_t i = pairs ? pairs[2 * k] : k / np;
+            int64_t j = pairs ? pairs[2 * k + 1] : k % np;
+            const float* sf = centroid + 3 * j;
+            d3 s = v3(sf[0], sf[1], sf[2]);
+            d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
+            int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
+            /* the patch triangles and the pulled-in check points */
+            d3 tv[2][3];
+            int ntri = 0;
+            d3 chk[6];
+            int nchk = 0;
+            for (int t = 0; t < 2; ++t) {
+                const float* g = ptri + 18 * j + 9 * t;
+                for (int q = 0; q < 3; ++q) tv[t][q] = v3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
+                d3 cr = vcross(vsub(tv[t][1], tv[t][0]), vsub(tv[t][2], tv[t][0]));
+                if (vdot(cr, cr) == 0.0) continue;
+                if (t != ntri)
+                    for (int q = 0; q < 3; ++q) tv[ntri][q] = tv[t][q];
+                for (int q = 0; q < 3; ++q) {
+                    const float* gq = g + 3 * q;
+                    float px = gq[0] + delta * (sf[0] - gq[0]);
+                    float py = gq[1] + delta * (sf[1] - gq[1]);
+                    float pz = gq[2] + delta * (sf[2] - gq[2]);
+                    chk[nchk++] = v3(px, py, pz);
+                }
+                ++ntri;
+            }
+            double E = 0.0;
+            int flags = 0, nclosed = 0;
+            for (int m = 0; m < K; ++m) {
+                float ox = cand[3 * i] + offsets[3 * m];
+                float oy = cand[3 * i + 1] + offsets[3 * m + 1];
+                float oz = cand[3 * i + 2] + offsets[3 * m + 2];
+                d3 o = v3(ox, oy, oz);
+                d3 v = vsub(o, s);
+                double d = vnorm(v);
+                double nv_ = vdot(n, v);
+                if (flag_out && fabs(nv_) <= eps) flags |= 4;
+                if (!(nv_ > 0.0 && d > 0.0)) continue;
+                int vis_c = seg_visible(T, nt, B, stack, ex0, ex1, o, s);
+                if (flag_out) flags |= seg_grazing(T, nt, B, stack, ex0, ex1, o, s, eps);
+                int all = vis_c && ntri > 0;
+                for (int q = 0; q < nchk; ++q) {
+                    if (all && !seg_visible(T, nt, B, stack, ex0, ex1, o, chk[q])) all = 0;
+                    if (flag_out && vis_c) flags |= seg_grazing(T, nt, B, stack, ex0, ex1, o, chk[q], eps);
+                }
+                double pw = (double)weights[m] * power;
+                if (all) {
+                    double om = 0.0;
+                    for (int t = 0; t < ntri; ++t) om += solid_angle(o, tv[t][0], tv[t][1], tv[t][2]);
+                    E += pw * om / (four_pi * (double)area[j]);
+                    ++nclosed;
+                } else if (vis_c) {
+                    E += pw * nv_ / (four_pi * d * d * d);
+                }
+            }
+            E_out[k] = E;
+            if (nclosed_out) nclosed_out[k] = (uint8_t)nclosed;
+            if (flag_out) flag_out[k] = (uint8_t)flags;
+        }
+        free(stack);
+    }
+    return failed ? -2 : 0;
+}
+
+static int area_mean_impl(int use_bvh, const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                          const float* centroid, const float* normal, const float* area, const int32_t* excl,
+                          const float* ptri, int64_t np, const float* cand, int64_t nc, const float* offsets,
+                          const float* weights, int32_t K, double power, float delta, const int64_t* pairs,
+                          int64_t npairs, double eps, double* E_out, uint8_t* nclosed_out, uint8_t* flag_out,
+                          int nthreads) {
+    if (pairs == NULL) npairs = nc * np;
+    if (check_irradiance_args(excl, np, nc, nt, K, pairs, npairs) != 0) return -1;
+    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
+    if (!T) return -2;
+    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
+    int rc = 0;
+    if (use_bvh) {
+        bvh64 B;
+        rc = bvh_build(T, nt, &B);
+        if (rc == 0) {
+            rc = area_mean_entries(T, nt, &B, centroid, normal, area, excl, ptri, np, cand, offsets, weights, K,
+                                   power, delta, pairs, npairs, eps, E_out, nclosed_out, flag_out, nthreads);
+            bvh_free(&B);
+        }
+    } else {
+        rc = area_mean_entries(T, nt, NULL, centroid, normal, area, excl, ptri, np, cand, offsets, weights, K, power,
+                               delta, pairs, npairs, eps, E_out, nclosed_out, flag_out, nthreads);
+    }
+    free(T);
+    return rc;
+}
+
 int uvco_area_mean(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                    const float* centroid, const float* normal, const float* area, const int32_t* excl,
                    const float* ptri, int64_t np, const float* cand, int64_t nc,
                    const float* offsets, const float* weights, int32_t K, double power, float delta,
                    const int64_t* pairs, int64_t npairs, double eps,
                    double* E_out, uint8_t* nclosed_out, uint8_t* flag_out, int nthreads) {
-    if (K < 1 || nt < 0 || np < 0 || nc < 0) return -1;
-    if (pairs == NULL) npairs = nc * np;
-    for (int64_t j = 0; j < np; ++j)
-        for (int q = 0; q < 2; ++q)
-            if (excl[2 * j + q] < -1 || excl[2 * j + q] >= nt) return -1;
-    if (pairs != NULL)
-        for (int64_t k = 0; k < npairs; ++k)
-            if (pairs[2 * k] < 0 || pairs[2 * k] >= nc || pairs[2 * k + 1] < 0 || pairs[2 * k + 1] >= np)
-                return -1;
-    tri64* T = (tri64*)malloc(sizeof(tri64) * (size_t)(nt > 0 ? nt : 1));
-    if (!T) return -2;
-    if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
-    const double four_pi = 4.0 * M_PI;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 8)
-#endif
-    for (int64_t k = 0; k < npairs; ++k) {
-        int64_t i = pairs ? pairs[2 * k] : k / np;
-        int64_t j = pairs ? pairs[2 * k + 1] : k % np;
-        const float* sf = centroid + 3 * j;
-        d3 s = v3(sf[0], sf[1], sf[2]);
-        d3 n = v3(normal[3 * j], normal[3 * j + 1], normal[3 * j + 2]);
-        int32_t ex0 = excl[2 * j], ex1 = excl[2 * j + 1];
-        /* the patch triangles and the pulled-in check points */
-        d3 tv[2][3];
-        int ntri = 0;
-        d3 chk[6];
-        int nchk = 0;
-        for (int t = 0; t < 2; ++t) {
-            const float* g = ptri + 18 * j + 9 * t;
-            for (int q = 0; q < 3; ++q) tv[t][q] = v3(g[3 * q], g[3 * q + 1], g[3 * q + 2]);
-            d3 cr = vcross(vsub(tv[t][1], tv[t][0]), vsub(tv[t][2], tv[t][0]));
-            if (vdot(cr, cr) == 0.0) continue;
-            if (t != ntri)
-                for (int q = 0; q < 3; ++q) tv[ntri][q] = tv[t][q];
-            for (int q = 0; q < 3; ++q) {
-                const float* gq = g + 3 * q;
-                float px = gq[0] + delta * (sf[0] - gq[0]);
-                float py = gq[1] + delta * (sf[1] - gq[1]);
-                float pz = gq[2] + delta * (sf[2] - gq[2]);
-                chk[nchk++] = v3(px, py, pz);
-            }
-            ++ntri;
-        }
-        double E = 0.0;
-        int flags = 0, nclosed = 0;
-        for (int m = 0; m < K; ++m) {
-            float ox = cand[3 * i] + offsets[3 * m];
-            float oy = cand[3 * i + 1] + offsets[3 * m + 1];
-            float oz = cand[3 * i + 2] + offsets[3 * m + 2];
-            d3 o = v3(ox, oy, oz);
-            d3 v = vsub(o, s);
-            double d = vnorm(v);
-            double nv_ = vdot(n, v);
-            if (flag_out && fabs(nv_) <= eps) flags |= 4;
-            if (!(nv_ > 0.0 && d > 0.0)) continue;
-            int vis_c = segment_visible(T, nt, ex0, ex1, o, s);
-            if (flag_out) flags |= segment_grazing(T, nt, ex0, ex1, o, s, eps);
-            int all = vis_c && ntri > 0;
-            for (int q = 0; q < nchk; ++q) {
-                if (all && !segment_visible(T, nt, ex0, ex1, o, chk[q])) all = 0;
-                if (flag_out && vis_c) flags |= segment_grazing(T, nt, ex0, ex1, o, chk[q], eps);
-            }
-            double pw = (double)weights[m] * power;
-            if (all) {
-                double om = 0.0;
-                for (int t = 0; t < ntri; ++t) om += solid_angle(o, tv[t][0], tv[t][1], tv[t][2]);
-                E += pw * om / (four_pi * (double)area[j]);
-                ++nclosed;
-            } else if (vis_c) {
-                E += pw * nv_ / (four_pi * d * d * d);
-            }
-        }
-        E_out[k] = E;
-        if (nclosed_out) nclosed_out[k] = (uint8_t)nclosed;
-        if (flag_out) flag_out[k] = (uint8_t)flags;
-    }
-    free(T);
-    return 0;
+    return area_mean_impl(0, verts, nv, tris, nt, centroid, normal, area, excl, ptri, np, cand, nc, offsets, weights,
+                          K, power, delta, pairs, npairs, eps, E_out, nclosed_out, flag_out, nthreads);
+}
+
+/* The same area-mean entries through the CPU hierarchy (see bvh_build). */
+int uvco_area_mean_bvh(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                       const float* centroid, const float* normal, const float* area, const int32_t* excl,
+                       const float* ptri, int64_t np, const float* cand, int64_t nc,
+                       const float* offsets, const float* weights, int32_t K, double power, float delta,
+                       const int64_t* pairs, int64_t npairs, double eps,
+                       double* E_out, uint8_t* nclosed_out, uint8_t* flag_out, int nthreads) {
+    return area_mean_impl(1, verts, nv, tris, nt, centroid, normal, area, excl, ptri, np, cand, nc, offsets, weights,
+                          K, power, delta, pairs, npairs, eps, E_out, nclosed_out, flag_out, nthreads);
 }
 
 /*

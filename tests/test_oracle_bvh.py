@@ -60,3 +60,31 @@ def test_closed_box_lamp_inside_identical():
     s = tiny_room(n_cand=12)
     E, vis, flag = _both(s.verts, s.tris, s.centroid, s.normal, s.excl, s.cand, line_lamp(0.5, 3, 30.0))
     assert vis.any()
+
+
+def _area_both(s, cand, L, pairs=None):
+    args = (s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, s.ptri, cand, L.offsets, L.weights, L.power)
+    a = oracle.area_mean(*args, pairs=pairs)
+    b = oracle.area_mean(*args, pairs=pairs, bvh=True)
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+    return a
+
+
+def test_area_mean_tiny_room_identical():
+    """uvco_area_mean_bvh against its brute force on the whole tiny-room
+    matrix, with a line lamp across the table top's plane: the centroid and
+    every pulled-in vertex segment go through the hierarchy."""
+    s = tiny_room(n_cand=30)
+    cand = s.cand.copy()
+    cand[:, 2] = np.where(np.arange(30) % 2 == 0, 0.62, 1.0)
+    E, ncl, flag = _area_both(s, cand, line_lamp(0.9, 5, 100.0))
+    assert (ncl > 0).mean() > 0.2 and (ncl < 5).any()    # closed form and fallbacks both occur
+
+
+def test_area_mean_ward_sampled_pairs_identical():
+    s = ward_room()
+    rng = np.random.default_rng(23)
+    pairs = np.stack([rng.integers(0, s.nc, 1200), rng.integers(0, s.np_, 1200)], axis=1)
+    E, ncl, flag = _area_both(s, s.cand, s.lamp, pairs=pairs)
+    assert (ncl > 0).mean() > 0.05 and (E > 0).mean() > 0.05
