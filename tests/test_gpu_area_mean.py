@@ -77,6 +77,37 @@ def test_quad_patches_sampled_pairs():
     assert (nco > 0).mean() > 0.2
 
 
+def test_ward_full_rows_against_bvh_oracle():
+    """Whole rows of the full-size ward area-mean matrix (32 candidates spread
+    over all 2,000 x all 102,030 patches, K = 8), launched on every candidate
+    at once, against the oracle's CPU-hierarchy mode (bit-identical to its
+    brute force, tests/test_oracle_bvh.py); the grazing flags are taken only
+    for pairs whose branch or value differs."""
+    s = ward_room()
+    sc = build(s)
+    A, ncl = uvc.irradiance_area_mean(sc, T(s.cand), lamp_of(s.lamp), T(s.ptri), with_closed=True)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    rows = np.linspace(0, s.nc - 1, 32).astype(np.int64)
+    pairs = np.stack([np.repeat(rows, s.np_), np.tile(np.arange(s.np_), rows.size)], axis=1)
+    L = s.lamp
+    args = (s.verts, s.tris, s.centroid, s.normal, s.area, s.excl, s.ptri, s.cand, L.offsets, L.weights, L.power)
+    E, nco, _ = oracle.area_mean(*args, pairs=pairs, bvh=True, flags=False)
+    ri = torch.from_numpy(rows).cuda()
+    Ag = A.index_select(0, ri).cpu().numpy().reshape(-1).astype(np.float64)
+    ng = ncl.index_select(0, ri).cpu().numpy().reshape(-1)
+    flag = np.zeros(pairs.shape[0], np.uint8)
+    rel = np.abs(Ag - E) / np.maximum(np.abs(E), 1e-30)
+    diff = np.flatnonzero((ng != nco) | ((rel > REL_TOL) & ~((E == 0) & (Ag == 0))))
+    if diff.size:
+        _, _, f = oracle.area_mean(*args, pairs=pairs[diff], bvh=True)
+        flag[diff] = f
+    n_flag = compare(Ag, ng, E, nco, flag)
+    assert n_flag <= 1e-4 * E.size
+    assert (nco > 0).mean() > 0.2 and (nco < L.K).any()
+    sc.free()
+
+
 def test_empty_candidates_and_bad_geometry_shape():
     s = tiny_room(n_cand=3)
     sc = build(s)
