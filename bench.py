@@ -681,7 +681,7 @@ def run_learned(args):
     whose check fails are then recomputed on all candidates (inside the timed
     region).  The plain pipeline computes every job's full matrix, fluence and
     coverage job by job.  Scenes, probe scenes, candidates and dwell vectors
-    are resident before timing.  The judged quality (lost coverage, added
+    are resident before timing.  The quality figures (lost coverage, added
     dwell against the plain LP) comes from the scorer's report."""
     import torch
 
@@ -847,7 +847,7 @@ def run_learned(args):
         quality = {k: rep.get(k) for k in ("eval_jobs", "lost_coverage_mean", "lost_coverage_max",
                                            "added_dwell_mean", "added_dwell_max", "fallback_rate",
                                            "support_recall_mean")}
-        quality["source"] = "paper_2103_14137_gb300/data/scorer_report.json (train_scorer judge)"
+        quality["source"] = "paper_2103_14137_gb300/data/scorer_report.json (train_scorer evaluation)"
     out = {
         "metric": METRIC, "value": round(n / (ms_learned * 1e-3), 4), "unit": "rooms/s", "n_gpus": 1, "steps": 1,
         "warmup": 1, "ms_per_step": round(ms_learned, 3), "higher_is_better": True, "scaling": "weak",

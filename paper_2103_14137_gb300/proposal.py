@@ -14,7 +14,7 @@ patch that at most a fraction RARE_FRAC of the candidates light (uvc_mark_best).
 
 The scorer learns which candidates the relaxed LP of Sec. IV-D (Eq. (9))
 gives a non-zero dwell time; the plain method - every candidate, exact matrix,
-the same LP - stays the fallback and the judge.  Training and the judge are
+the same LP - stays the fallback and the referee.  Training and the evaluation are
 host orchestration of library calls plus the host LP (lp.py).
 """
 from __future__ import annotations

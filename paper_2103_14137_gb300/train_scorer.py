@@ -1,5 +1,5 @@
 """Train the candidate scorer on LP dwell-time labels from seeded procedural
-rooms, then judge the proposal against the plain method on held-out rooms.
+rooms, then evaluate the proposal against the plain method on held-out rooms.
 
 Run from the repository root (it uses the seeded room generator in synth/):
     python -m paper_2103_14137_gb300.train_scorer --rooms 48 --eval-rooms 8 \
@@ -9,7 +9,7 @@ Training jobs: rooms 10000 + r of the uneven-room generator, three random
 lamp designs each, at most --cap candidates; targets from the relaxed LP (Eq. (9))
 over every patch, solved by row generation: the efficiency of each candidate
 at the LP's dual prices (label_of).
-Judge: rooms 100 + r (the batched benchmark's rooms), designs 1, 5 and 9, all
+Evaluation: rooms 100 + r (the batched benchmark's rooms), designs 1, 5 and 9, all
 their candidates.  For each job the plain LP (all candidates) and the reduced
 LP (the kept candidates) give dwell times whose coverage at MU_MIN is
 measured over every patch with the exact matrix; lost coverage is the drop,
@@ -95,7 +95,7 @@ def training_data(n_rooms, cap, dev, workers, log, chunk=12):
     return feats, ys, lp_s, etas, sups
 
 
-def judge(scorer, n_rooms, dev, workers, log, design_ids=(1, 5, 9), mark=True):
+def evaluate(scorer, n_rooms, dev, workers, log, design_ids=(1, 5, 9), mark=True):
     batched_room, design_candidates, designs, line_lamp, POWER = _synth()
     D = designs()
     jobs, scenes, meta = [], [], []
@@ -115,12 +115,12 @@ def judge(scorer, n_rooms, dev, workers, log, design_ids=(1, 5, 9), mark=True):
             meta.append({"room": seed, "design": d, "nc": int(cand.shape[0]), "np": int(room.np_),
                          "kept": int(keep.size), "probe_lost": lost, "fallback": bool(lost > LOST_MAX),
                          "_keep": keep})
-        log(f"judge room {r}: nt={room.nt} np={room.np_}")
+        log(f"evaluation room {r}: nt={room.nt} np={room.np_}")
     full = [dict(j, rows=None) for j in jobs]
     red = [dict(j, rows=m["_keep"]) for j, m in zip(jobs, meta)]
     t0 = time.perf_counter()
     sols = dwell_rowgen(full + red, workers, log=log)
-    log(f"judge LPs {time.perf_counter() - t0:.1f} s")
+    log(f"evaluation LPs {time.perf_counter() - t0:.1f} s")
     n = len(jobs)
     for k, (j, m) in enumerate(zip(jobs, meta)):
         t_full, mu_full, s_full, r_full, rows_full, eta_full = sols[k]
@@ -155,7 +155,7 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--workers", type=int, default=max(1, (os.cpu_count() or 2) - 1))
     ap.add_argument("--out", default=None)
-    ap.add_argument("--load", default=None, help="judge these weights instead of training")
+    ap.add_argument("--load", default=None, help="evaluate these weights instead of training")
     ap.add_argument("--report", default=None)
     ap.add_argument("--save-data", default=None, help="write the training features and labels (.npz)")
     ap.add_argument("--no-mark", action="store_true", help="select by score alone (no best-source marking)")
@@ -182,7 +182,7 @@ def main(argv=None):
         if a.out:
             save(a.out, flat, rooms=a.rooms, steps=a.steps)
         scorer = Scorer(flat)
-    jobs = judge(scorer, a.eval_rooms, dev, a.workers, log, mark=not a.no_mark)
+    jobs = evaluate(scorer, a.eval_rooms, dev, a.workers, log, mark=not a.no_mark)
     report["mark_best"] = not a.no_mark
     lost = np.array([j["lost_coverage"] for j in jobs])
     added = np.array([j["added_dwell"] for j in jobs])
