@@ -68,7 +68,8 @@ def parse():
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
-    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target CPU time of the oracle sample (per step in --impl reference)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -514,7 +515,7 @@ def run_reference(args):
     oracle.build()
     threads = os.cpu_count() or 1
     # size each step so that warmup + steps end within a few minutes
-    per_step_s = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    per_step_s = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     dt = _oracle_rate(s, 64, 7, threads)
     n = int(min(max(64, 64 * per_step_s / max(dt, 1e-6)), 2_000_000))
     for k in range(args.warmup):
