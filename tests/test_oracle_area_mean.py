@@ -94,6 +94,16 @@ def test_blocked_vertex_falls_back_to_the_centroid_sample():
     assert ncl2 == 1 and math.isclose(E2, 3.0 * omega / (4 * math.pi * 4.0), rel_tol=1e-9)
 
 
+def test_off_axis_fallback_keeps_the_cosine():
+    """A source off the patch's axis with only one check segment blocked: the
+    centroid sample P cos / (4 pi d^2), cos = h / d."""
+    src = np.array([0.625, -0.375, 2.0])                                   # exact in binary32
+    occ = np.array([[0.76, 0.26, 1.0], [0.86, 0.26, 1.0], [0.81, 0.36, 1.0]])   # halfway to vertex (1, 1, 0)
+    E, ncl, _ = one_patch(square(2.0), [0, 0, 1], 4.0, occluders=[occ], source=src, power=3.0)
+    d = float(np.linalg.norm(src))
+    assert ncl == 0 and math.isclose(E, 3.0 * (2.0 / d) / (4 * math.pi * d * d), rel_tol=1e-12)
+
+
 def test_source_behind_the_patch_gives_zero():
     E, ncl, _ = one_patch(square(1.0), [0, 0, 1], 1.0, source=(0.1, 0.2, -1.0))
     assert E == 0.0 and ncl == 0
@@ -109,3 +119,59 @@ def test_closed_form_tends_to_the_centroid_sample():
     # second-order convergence: halving the patch divides the error by ~4
     for e0, e1 in zip(errs, errs[1:]):
         assert 3.0 < e0 / e1 < 5.0, errs
+
+
+def closed_box(size, n):
+    """The inside of an axis-aligned box [0, size]: every face an n x n grid of
+    quad patches (two triangles each, normals into the box)."""
+    size = np.asarray(size, np.float64)
+    centre = size / 2
+    verts, quads = [], []
+    for ax in range(3):
+        u, v = [k for k in range(3) if k != ax]
+        for side in (0.0, size[ax]):
+            for i in range(n):
+                for j in range(n):
+                    q = np.zeros((4, 3))
+                    for c, (di, dj) in enumerate(((0, 0), (1, 0), (1, 1), (0, 1))):
+                        q[c, ax] = side
+                        q[c, u] = size[u] * (i + di) / n
+                        q[c, v] = size[v] * (j + dj) / n
+                    t0, t1 = q[[0, 1, 2]], q[[0, 2, 3]]
+                    nrm = np.cross(t0[1] - t0[0], t0[2] - t0[0])
+                    if nrm @ (centre - t0[0]) < 0:          # wind both triangles towards the inside
+                        t0, t1 = t0[[0, 2, 1]], t1[[0, 2, 1]]
+                    quads.append((t0, t1))
+    nq = len(quads)
+    tri = np.array([t for q in quads for t in q], np.float32)
+    verts = tri.reshape(-1, 3)
+    T = np.arange(verts.shape[0], dtype=np.int32).reshape(-1, 3)
+    ptri = tri.reshape(nq, 2, 3, 3)
+    p64 = ptri.astype(np.float64)
+    cr = np.cross(p64[:, 0, 1] - p64[:, 0, 0], p64[:, 0, 2] - p64[:, 0, 0])
+    normal = (cr / np.linalg.norm(cr, axis=1, keepdims=True)).astype(np.float32)
+    area = (0.5 * (np.linalg.norm(cr, axis=1)
+                   + np.linalg.norm(np.cross(p64[:, 1, 1] - p64[:, 1, 0], p64[:, 1, 2] - p64[:, 1, 0]), axis=1))
+            ).astype(np.float32)
+    cen = p64.reshape(nq, 6, 3).mean(axis=1).astype(np.float32)
+    excl = np.stack([2 * np.arange(nq), 2 * np.arange(nq) + 1], axis=1).astype(np.int32)
+    return verts, T, cen, normal, area, excl, ptri
+
+
+def test_closed_box_receives_all_the_power():
+    """A source inside a closed box sees every patch whole, and the patches'
+    solid angles add up to the full sphere: sum_j E_j a_j = P exactly (up to
+    FP64 rounding) for a point lamp and for a line lamp, every source using the
+    closed form.  A wrong normalisation, solid-angle factor or a dropped
+    second patch triangle would miss P."""
+    verts, T, cen, nrm, area, excl, ptri = closed_box((4.0, 3.0, 2.5), 5)
+    lamps = [([[0.0, 0.0, 0.0]], [1.0]),
+             ([[0.0, 0.0, 0.2 + 0.4 * m] for m in range(4)], [0.25] * 4)]
+    for off, w in lamps:
+        E, ncl, flag = oracle.area_mean(verts, T, cen, nrm, area, excl, ptri, [[1.3, 1.1, 0.55]], off, w, 60.0)
+        assert np.all(ncl == len(w))
+        flux = float(np.sum(E[0] * area.astype(np.float64)))
+        assert math.isclose(flux, 60.0, rel_tol=1e-10), flux
+        # the centroid sample alone does not conserve the flux on these coarse patches
+        Ec, _, _ = oracle.irradiance(verts, T, cen, nrm, excl, [[1.3, 1.1, 0.55]], off, w, 60.0, flags=False)
+        assert abs(float(np.sum(Ec[0] * area)) - 60.0) > 1e-3 * 60.0

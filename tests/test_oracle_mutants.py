@@ -52,3 +52,38 @@ def test_mutant_is_caught(name, tmp_path):
         except AssertionError:
             caught.append(pin.__name__)
     assert caught, f"mutant {name} passed every pin"
+
+
+# Mistakes in the area-mean oracle (uvco_area_mean), each of which one of the
+# area-mean pins (tests/test_oracle_area_mean.py) must catch.
+AREA_MUTANTS = {
+    "solid_angle_halved": ("return 2.0 * atan2(num, den);", "return atan2(num, den);"),
+    "solid_angle_den_sign": ("+ vdot(R2, R3) * r1;", "- vdot(R2, R3) * r1;"),
+    "area_not_divided": ("E += pw * om / (four_pi * (double)area[j]);", "E += pw * om / four_pi;"),
+    "second_triangle_dropped": ("for (int t = 0; t < ntri; ++t) om += solid_angle",
+                                "for (int t = 0; t < 1; ++t) om += solid_angle"),
+    "vertex_checks_skipped": ("if (all && !seg_visible(T, nt, B, stack, ex0, ex1, o, chk[q])) all = 0;", ";"),
+    "closed_form_unweighted": ("double pw = (double)weights[m] * power;", "double pw = power;"),
+    "fallback_without_cosine": ("E += pw * nv_ / (four_pi * d * d * d);", "E += pw / (four_pi * d * d);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(AREA_MUTANTS))
+def test_area_mean_mutant_is_caught(name, tmp_path, monkeypatch):
+    from tests import test_oracle_area_mean as pins
+    old, new = AREA_MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    mutated = tmp_path / "mut.c"
+    mutated.write_text(src.replace(old, new, 1))
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                           str(mutated), "-o", str(so), "-lm"])
+    monkeypatch.setattr(oracle, "_lib", oracle.load_library(str(so)))
+    caught = []
+    for fn in sorted(n for n in dir(pins) if n.startswith("test_")):
+        try:
+            getattr(pins, fn)()
+        except AssertionError:
+            caught.append(fn)
+    assert caught, f"mutant {name} passed every area-mean pin"
