@@ -1,6 +1,9 @@
 """Each plausible mistake planted in a copy of the C oracle must be caught by
 at least one pin: evidence that the pins constrain every term of Eq. (7), the
-visibility rule, the source layout and the grazing flags.  Runs on the CPU."""
+visibility rule, the source layout and the grazing flags, and likewise the
+area-mean closed form (solid angles, area normalisation, vertex checks,
+fallback) and the visibility-cube estimator (pixel solid angles and powers,
+nearest hit, front faces, pixel centres).  Runs on the CPU."""
 import os
 import subprocess
 
@@ -30,17 +33,35 @@ MUTANTS = {
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_mutant_is_caught(name, tmp_path):
-    old, new = MUTANTS[name]
+def _mutant_lib(old, new, tmp_path, unique=False):
+    """A copy of the C oracle with `old` replaced by `new` (first occurrence),
+    compiled and loaded."""
     src = open(SRC).read()
-    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    if unique:
+        assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    else:
+        assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
     mutated = tmp_path / "mut.c"
     mutated.write_text(src.replace(old, new, 1))
     so = tmp_path / "libmut.so"
     subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
                            str(mutated), "-o", str(so), "-lm"])
-    lib = oracle.load_library(str(so))
+    return oracle.load_library(str(so))
+
+
+def _caught_by(pins_module):
+    caught = []
+    for fn in sorted(n for n in dir(pins_module) if n.startswith("test_")):
+        try:
+            getattr(pins_module, fn)()
+        except AssertionError:
+            caught.append(fn)
+    return caught
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    lib = _mutant_lib(*MUTANTS[name], tmp_path)
 
     def irr(*a, **kw):
         return oracle.irradiance(*a, lib=lib, **kw)
@@ -71,19 +92,28 @@ AREA_MUTANTS = {
 @pytest.mark.parametrize("name", sorted(AREA_MUTANTS))
 def test_area_mean_mutant_is_caught(name, tmp_path, monkeypatch):
     from tests import test_oracle_area_mean as pins
-    old, new = AREA_MUTANTS[name]
-    src = open(SRC).read()
-    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
-    mutated = tmp_path / "mut.c"
-    mutated.write_text(src.replace(old, new, 1))
-    so = tmp_path / "libmut.so"
-    subprocess.check_call(["gcc", "-std=gnu11", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
-                           str(mutated), "-o", str(so), "-lm"])
-    monkeypatch.setattr(oracle, "_lib", oracle.load_library(str(so)))
-    caught = []
-    for fn in sorted(n for n in dir(pins) if n.startswith("test_")):
-        try:
-            getattr(pins, fn)()
-        except AssertionError:
-            caught.append(fn)
-    assert caught, f"mutant {name} passed every area-mean pin"
+    monkeypatch.setattr(oracle, "_lib", _mutant_lib(*AREA_MUTANTS[name], tmp_path, unique=True))
+    assert _caught_by(pins), f"mutant {name} passed every area-mean pin"
+
+
+# Mistakes in the visibility-cube oracle (uvco_raster), each of which one of
+# the raster pins (tests/test_oracle_raster.py) must catch.
+RASTER_MUTANTS = {
+    "pixel_power_without_4pi": ("double pw = (double)weights[m] * power / (4.0 * M_PI);",
+                                "double pw = (double)weights[m] * power;"),
+    "pixel_solid_angle_sign": ("pixel_G(u1, v1) - pixel_G(u0, v1) - pixel_G(u1, v0) + pixel_G(u0, v0)",
+                               "pixel_G(u1, v1) - pixel_G(u0, v1) + pixel_G(u1, v0) + pixel_G(u0, v0)"),
+    "farthest_hit_wins": ("if (inside && tt < tbest)", "if (inside && (best < 0 || tt > tbest))"),
+    "back_faces_receive": ("if (dn < 0.0) {", "if (dn != 0.0) {"),
+    "ray_through_pixel_corner": ("float uf = (float)(2 * px + 1) / (float)R - 1.0f;",
+                                 "float uf = (float)(2 * px) / (float)R - 1.0f;"),
+    "barycentric_bound": ("int inside = uu >= 0.0 && ww >= 0.0 && uu + ww <= 1.0;",
+                          "int inside = uu >= 0.0 && ww >= 0.0 && uu + ww <= 1.5;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(RASTER_MUTANTS))
+def test_raster_mutant_is_caught(name, tmp_path, monkeypatch):
+    from tests import test_oracle_raster as pins
+    monkeypatch.setattr(oracle, "_lib", _mutant_lib(*RASTER_MUTANTS[name], tmp_path, unique=True))
+    assert _caught_by(pins), f"mutant {name} passed every raster pin"
