@@ -525,6 +525,20 @@ const char* uvc_status_string(int status);
 int uvc_scene_status(const uvc_scene* scene, uvc_stream_t stream);
 
 /*
+ * uvc_scene_set_limits - lower the scene's traversal limits, for tests of the
+ * failure handling (a stand-in for a tree too deep for the stack, or a search
+ * that does not end).  max_stack: stack entries per warp (the built-in bound
+ * is 3 per level of the four-wide tree, plus 4); max_visits: node visits per
+ * search (built in: nt + 64); 0 restores the built-in bound, and values above
+ * it have no effect.  A search that would exceed a limit stops: its entries
+ * become NaN and the status word records UVC_E_STACK or UVC_E_TIMEOUT (first
+ * error wins); the other entries are unchanged.  Applies to calls made after
+ * it (a batch keeps the limits of its creation); host-only, no device work.
+ * Not in the paper.  Errors: UVC_E_INVAL (NULL scene, negative limit).
+ */
+int uvc_scene_set_limits(uvc_scene* scene, int32_t max_stack, int32_t max_visits);
+
+/*
  * uvc_scene_info - host-side facts about a built scene: triangle and patch
  * counts, depth of the hierarchy (edges from the root to the deepest leaf).
  * Any output pointer may be NULL.

@@ -268,6 +268,13 @@ int uvc_scene_status(const uvc_scene* scene, uvc_stream_t stream) {
     return v;
 }
 
+int uvc_scene_set_limits(uvc_scene* scene, int32_t max_stack, int32_t max_visits) {
+    if (!scene || max_stack < 0 || max_visits < 0) return UVC_E_INVAL;
+    scene->limit_stack = max_stack;   // host fields: read when a later call builds its launch
+    scene->limit_visits = max_visits;
+    return UVC_OK;
+}
+
 int uvc_scene_info(const uvc_scene* scene, int64_t* nt, int64_t* np, int32_t* depth) {
     if (!scene) return UVC_E_INVAL;
     if (nt) *nt = scene->nt;

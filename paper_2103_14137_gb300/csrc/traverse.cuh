@@ -66,6 +66,8 @@ SceneView view_of(const uvc_scene* sc) {
     v.root = sc->root;
     v.stack_cap = 3 * (sc->depth4 + 1) + 1;   // at most 3 pushes per four-wide level
     v.visit_cap = (int)sc->nt + 64;
+    if (sc->limit_stack > 0 && sc->limit_stack < v.stack_cap) v.stack_cap = sc->limit_stack;
+    if (sc->limit_visits > 0 && sc->limit_visits < v.visit_cap) v.visit_cap = sc->limit_visits;
     v.cut_eps = 1e-5f * sc->diameter;
     v.status = sc->status;
     return v;

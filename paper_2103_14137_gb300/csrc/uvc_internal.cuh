@@ -81,6 +81,9 @@ struct uvc_scene {
     float* area_total = nullptr;  // [1]
     int* status = nullptr;        // [1] device status word (0 = ok)
     cudaStream_t build_stream = nullptr;
+    // lowered traversal limits (uvc_scene_set_limits); 0 = the built-in bound
+    int32_t limit_stack = 0;
+    int32_t limit_visits = 0;
 };
 
 namespace uvc {

@@ -75,6 +75,7 @@ def library():
         "uvc_scene_status": [P, P],
         "uvc_set_wedge_traversal": [i32, ctypes.POINTER(i32)],
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
+        "uvc_scene_set_limits": [P, i32, i32],
         "uvc_scene_export_bvh": [P, P, P, P, P],
     }
     sig.update({
@@ -574,6 +575,13 @@ class Mlp:
 
 def scene_status(scene: Scene, stream=None) -> int:
     return int(library().uvc_scene_status(scene.handle, _stream(stream)))
+
+
+def scene_set_limits(scene: Scene, max_stack: int = 0, max_visits: int = 0) -> None:
+    """Lower the scene's traversal stack depth and node-visit cap for later
+    calls (0 = the built-in bound), to exercise the failure handling (see
+    uvc_scene_set_limits)."""
+    _check(library().uvc_scene_set_limits(scene.handle, int(max_stack), int(max_visits)), "uvc_scene_set_limits")
 
 
 def scene_export_bvh(scene: Scene) -> dict:

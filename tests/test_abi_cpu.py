@@ -56,6 +56,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.uvc_fluence(None, None, 0, 0, None, 1, None, None) == 1
     assert lib.uvc_coverage(None, None, 1, 1.0, None, None, None) == 1
     assert lib.uvc_scene_status(None, None) == 1
+    assert lib.uvc_scene_set_limits(None, 0, 0) == 1
     assert lib.uvc_free_scene(None) == 0
     assert lib.uvc_candidate_features(None, None, 0, None, 66, None) == 1
     assert lib.uvc_probe_features(None, 1, 10, 10, None, None, None, 47, None) == 1      # ldf < 48
