@@ -7,8 +7,9 @@ fluence as uvc_fluence_streamed, within the fluence tolerance of the other
 tests, on consecutive calls (the fixed scratch array keeps the previous call's
 contents), and must refuse problems larger than its fixed scratch.
 
-This file is collected last so that a run stopping at the first failure has
-already run every other test; it also passes alone in a fresh process.
+This file is collected after the traversal, fluence and proposal suites, so
+that a run stopping at the first failure has already run them; it also passes
+alone in a fresh process.
 """
 import numpy as np
 import pytest
