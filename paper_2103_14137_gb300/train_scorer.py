@@ -62,11 +62,77 @@ def _job(sc, T, room, cand, lamp, seed):
             "check": (Ap[:, half:], ap[half:]), "sketch": Ap[:, :half]}
 
 
-def training_data(n_rooms, cap, dev, workers, log, chunk=12):
+def _label_settings(cap):
+    """Everything a chunk's features and labels depend on besides its rooms:
+    the settings, and the source of the room generator, the proposal and the
+    LP (any edit there invalidates the cache)."""
+    import hashlib
+    from . import proposal as prop
+    from .lp import T_MAX
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    h = hashlib.sha256()
+    for rel in ("synth/batched.py", "synth/mesh.py", "synth/scenes.py", "paper_2103_14137_gb300/proposal.py",
+                "paper_2103_14137_gb300/lp.py"):
+        with open(os.path.join(root, rel), "rb") as f:
+            h.update(f.read())
+    return {"cap": int(cap), "probe": prop.PROBE, "lp_patches": prop.LP_PATCHES, "lp_add": prop.LP_ADD,
+            "lp_rounds": prop.LP_ROUNDS, "mu_min": MU_MIN, "t_max": T_MAX, "features": int(uvc.FEATURES),
+            "probe_features": int(uvc.PROBE_FEATURES), "code": h.hexdigest()[:16]}
+
+
+def _chunk_path(cache, r0, r1):
+    return os.path.join(cache, f"train_rooms_{10000 + r0}-{10000 + r1 - 1}.npz")
+
+
+def save_chunk(cache, r0, r1, cap, feats, ys, etas, sups, lp_s):
+    """Write one chunk of solved training jobs (rooms r0..r1-1) to the cache
+    directory, atomically, with the settings they were made under."""
+    os.makedirs(cache, exist_ok=True)
+    n = np.array([len(f) for f in feats], np.int64)
+    path = _chunk_path(cache, r0, r1)
+    tmp = f"{path}.{os.getpid()}.tmp.npz"
+    np.savez_compressed(tmp, settings=json.dumps(_label_settings(cap)), n=n,
+                        feat=np.concatenate(feats).astype(np.float32), y=np.concatenate(ys).astype(np.float32),
+                        eta=np.concatenate(etas).astype(np.float32), support=np.concatenate(sups).astype(bool),
+                        lp_s=np.asarray(lp_s, np.float64))
+    os.replace(tmp, path)
+
+
+def load_chunk(cache, r0, r1, cap):
+    """The cached chunk of rooms r0..r1-1 as per-job lists, or None when it is
+    missing or was made under other settings."""
+    path = _chunk_path(cache, r0, r1) if cache else None
+    if not path or not os.path.exists(path):
+        return None
+    z = np.load(path)
+    if json.loads(str(z["settings"])) != _label_settings(cap):
+        return None
+    cut = np.cumsum(z["n"])[:-1]
+    split = lambda a: list(np.split(a, cut))  # noqa: E731
+    return split(z["feat"]), split(z["y"]), split(z["eta"]), split(z["support"]), list(z["lp_s"])
+
+
+def training_data(n_rooms, cap, dev, workers, log, chunk=12, cache=None):
+    """Features and LP labels of the training jobs, chunk by chunk of rooms.
+    With `cache` (a directory) every solved chunk is written there and a
+    chunk found there under the same settings is read instead of solved, so an
+    interrupted run resumes at its first unsolved chunk."""
     batched_room, design_candidates, designs, line_lamp, POWER = _synth()
     D = designs()
     feats, ys, lp_s, etas, sups = [], [], [], [], []
     for c0 in range(0, n_rooms, chunk):
+        c1 = min(n_rooms, c0 + chunk)
+        hit = load_chunk(cache, c0, c1, cap)
+        if hit is not None:
+            f, y, e, sp, ls = hit
+            feats += f
+            ys += y
+            etas += e
+            sups += sp
+            lp_s += ls
+            log(f"training rooms {c0}..{c1 - 1}: {len(f)} jobs read from {cache}")
+            continue
+        n_before = len(feats)
         jobs, scenes = [], []
         for r in range(c0, min(n_rooms, c0 + chunk)):
             seed = 10000 + r
@@ -88,6 +154,9 @@ def training_data(n_rooms, cap, dev, workers, log, chunk=12):
             lp_s.append(secs)
         log(f"training rooms {c0}..{c0 + len(scenes) - 1}: {len(jobs)} jobs, LPs {time.perf_counter() - t0:.1f} s, "
             f"rows {np.mean([x[4] for x in sols]):.0f} mean")
+        if cache:
+            save_chunk(cache, c0, c1, cap, feats[n_before:], ys[n_before:], etas[n_before:], sups[n_before:],
+                       lp_s[n_before:])
         del jobs, sols
         for sc in scenes:
             sc.free()
@@ -159,6 +228,8 @@ def main(argv=None):
     ap.add_argument("--report", default=None)
     ap.add_argument("--save-data", default=None, help="write the training features and labels (.npz)")
     ap.add_argument("--no-mark", action="store_true", help="select by score alone (no best-source marking)")
+    ap.add_argument("--cache", default=None,
+                    help="directory for solved training chunks (written as they finish, reused on a rerun)")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     _build.build()
@@ -168,7 +239,7 @@ def main(argv=None):
     if a.load:
         scorer = Scorer.load(a.load)
     else:
-        feats, ys, lp_s, etas, sups = training_data(a.rooms, a.cap, dev, a.workers, log)
+        feats, ys, lp_s, etas, sups = training_data(a.rooms, a.cap, dev, a.workers, log, cache=a.cache)
         X, y = np.concatenate(feats), np.concatenate(ys)
         if a.save_data:
             np.savez_compressed(a.save_data, X=X.astype(np.float32), y=y, eta=np.concatenate(etas),
