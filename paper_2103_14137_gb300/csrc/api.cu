@@ -34,7 +34,7 @@ std::atomic<int> g_wedge{1};
 
 }  // namespace
 
-int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound) {
     if (!lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES) return UVC_E_INVAL;
     if (!std::isfinite(lamp->power) || lamp->power < 0.f) return UVC_E_INVAL;
     std::memset(out, 0, sizeof(*out));
@@ -57,6 +57,15 @@ int lamp_to_device(const uvc_lamp* lamp, LampDev* out) {
         const double z0 = out->oz[0], dz = ((double)out->oz[K - 1] - z0) / (K - 1);
         bool even = dz > 0.0 && std::isfinite(1.0 / dz);
         for (int m = 0; m < K && even; ++m) even = std::fabs((double)out->oz[m] - (z0 + m * dz)) <= dz / 64.0;
+        // The closed-form index range of the wedge search leaves 1/64 of a
+        // step for FP32 rounding: the source heights fl32(c.z + off) and the
+        // interval ends carry errors of about 2^-24 of the coordinates, so the
+        // step must be at least 2^-16 of them.  Candidates are taken to lie
+        // within 16 times the scene's coordinate bound; closer sources take
+        // the source-by-source height test (exact at any spacing).
+        double offmax = 0.0;
+        for (int m = 0; m < K; ++m) offmax = std::max(offmax, std::fabs((double)out->oz[m]));
+        if (even && !(dz >= std::ldexp(16.0 * (double)coord_bound + 3.0 * offmax, -16))) even = false;
         out->wuniform = even ? 1 : 0;
         out->wz0 = (float)z0;
         out->wrdz = even ? (float)(1.0 / dz) : 0.f;
@@ -101,7 +110,7 @@ int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc,
                           int64_t lda, uint32_t* vis, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc)) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc == 0 || scene->np == 0) return UVC_OK;
@@ -113,7 +122,7 @@ int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t n
                             float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || !counters) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc > 0 && scene->np > 0 && (!cand || !A)) return UVC_E_INVAL;
@@ -125,7 +134,7 @@ int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t 
                              const float* ptri, float* A, int64_t lda, uint8_t* nclosed, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc > 0 && scene->np > 0 && (!cand || !A || !ptri)) return UVC_E_INVAL;
@@ -143,7 +152,7 @@ int uvc_irradiance_raster(const uvc_scene* scene, const float* tri_normal, const
                           uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX || R < 1 || R > 4096) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (lda < scene->nt) return UVC_E_INVAL;
     if (nc > 0 && scene->nt > 0 && (!cand || !A || !tri_normal || !workspace)) return UVC_E_INVAL;
@@ -162,7 +171,7 @@ int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, 
                          const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (scene->np == 0) return UVC_OK;
     if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;
@@ -173,7 +182,7 @@ int uvc_fluence_streamed_noalloc(const uvc_scene* scene, const float* cand, int6
                                  const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
     if (rc != UVC_OK) return rc;
     if (scene->np == 0) return UVC_OK;
     if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;

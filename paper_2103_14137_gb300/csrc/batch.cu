@@ -189,9 +189,12 @@ int uvc_batch_create(const uvc_job* jobs, int32_t njobs, const uvc_lamp* lamps, 
     b->njobs = njobs;
     b->nlamps = nlamps;
     b->host_lamps.resize(nlamps);
+    float coord_bound = 0.f;   // over every job's scene (a lamp may serve several)
+    for (int q = 0; q < njobs; ++q)
+        if (jobs[q].scene) coord_bound = std::max(coord_bound, jobs[q].scene->coord_bound);
     for (int l = 0; l < nlamps; ++l) {
         uvc::LampDev& D = b->host_lamps[l];
-        if (uvc::lamp_to_device(&lamps[l], &D) != UVC_OK) { delete b; return UVC_E_INVAL; }
+        if (uvc::lamp_to_device(&lamps[l], &D, coord_bound) != UVC_OK) { delete b; return UVC_E_INVAL; }
         if (D.wedge) b->wedge_k = std::max(b->wedge_k, D.K);
     }
     int nwedge = 0;

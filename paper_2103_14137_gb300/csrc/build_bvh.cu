@@ -985,7 +985,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     sc->depth4 = (sc->depth + 1) / 2;
     float diam = 0.f;
     if (n > 0) {
-        double d2 = 0.0;
+        double d2 = 0.0, cmax = 0.0;
         for (int k = 0; k < 3; ++k) {
             const unsigned int lo_u = host_bounds[6 + k], hi_u = host_bounds[9 + k];
             float lo_f, hi_f;
@@ -995,8 +995,10 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
             std::memcpy(&hi_f, &b, 4);
             const double ext = (double)hi_f - (double)lo_f;
             if (std::isfinite(ext)) d2 += ext * ext;
+            if (std::isfinite(ext)) cmax = std::max(cmax, std::max(std::fabs((double)lo_f), std::fabs((double)hi_f)));
         }
         diam = (float)std::sqrt(d2);
+        sc->coord_bound = (float)cmax;
     }
     sc->diameter = diam;
     if (np > 0) {

@@ -56,8 +56,9 @@ struct LampDev {
     float pw[UVC_MAX_SOURCES];
 };
 
-// Host: validate a lamp and convert it (api.cu).
-int lamp_to_device(const uvc_lamp* lamp, LampDev* out);
+// Host: validate a lamp and convert it (api.cu); coord_bound is the largest
+// coordinate magnitude of the scene(s) it will be used with.
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound);
 
 }  // namespace uvc
 
@@ -67,6 +68,7 @@ struct uvc_scene {
     int32_t depth = 0;     // edges from the root to the deepest leaf
     int32_t root = 0;      // root reference (0, or ~0 for a single triangle)
     float diameter = 0.f;  // diagonal of the triangles' bounding box
+    float coord_bound = 0.f;  // largest |coordinate| of that box
     // device buffers, carved out of one allocation
     void* block = nullptr;
     float4* tri = nullptr;        // [nt][3]: (v0, id bits), (v1, 0), (v2, 0) in sorted order

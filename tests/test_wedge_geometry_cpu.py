@@ -13,6 +13,8 @@ the per-source search and the oracle in tests/test_gpu_wedge.py).
    vertical plane.  No source whose segment meets the triangle lies outside
    that interval.
 """
+import math
+
 import numpy as np
 
 
@@ -128,3 +130,53 @@ def test_lamp_height_interval_contains_every_blocked_source():
         tested += K
     assert hits > 5000
     assert kept / tested < 0.5                                 # the filter does remove most sources
+
+
+def _uniform_range(z0, z1, cz, wz0, wrdz, K):
+    """The closed-form source index range of an evenly spaced lamp, in the
+    kernel's FP32 operations."""
+    f = np.float32
+    t0 = min(max(f(f(f(f(z0) - f(cz)) - f(wz0)) * f(wrdz)), f(-4)), f(40))
+    t1 = min(max(f(f(f(f(z1) - f(cz)) - f(wz0)) * f(wrdz)), f(-4)), f(40))
+    return max(0, int(math.ceil(f(t0 - f(0.03125))))), min(K - 1, int(math.floor(f(t1 + f(0.03125)))))
+
+
+def _violations(rng, spacing_factor, trials=20000):
+    """Sources whose FP32 height lies in [z0, z1] but outside the closed-form
+    range, for lamps whose step is spacing_factor times the smallest step the
+    library lets take the closed form (2^-16 (16 B + 3 max|off|), B the scene's
+    coordinate bound, candidates within 16 B)."""
+    bad = 0
+    for _ in range(trials):
+        B = 10.0 ** rng.uniform(0, 3)
+        K = int(rng.integers(2, 17))
+        z0off = rng.uniform(-1, 1)
+        cz = rng.uniform(-16 * B, 16 * B)
+        span = rng.uniform(0.01, 2.0)
+        dz_min = 2.0 ** -16 * (16 * B + 3 * (abs(z0off) + span))
+        dz = dz_min * spacing_factor
+        ideal = z0off + dz * np.arange(K)
+        off = (ideal + rng.uniform(-dz / 64, dz / 64, K)).astype(np.float32)
+        off[0] = np.float32(z0off)
+        d_host = (float(off[-1]) - float(off[0])) / (K - 1)
+        if not (d_host > 0 and np.all(np.abs(off.astype(np.float64) - (float(off[0]) + np.arange(K) * d_host))
+                                      <= d_host / 64)):
+            continue                                            # the host would not take the closed form
+        oz = (np.float32(cz) + off).astype(np.float32)          # fl32(c.z + off)
+        q = int(rng.integers(0, K))
+        z_lo = float(oz[q]) - abs(rng.normal(0, dz)) * rng.integers(0, 2)
+        z_hi = float(oz[q]) + abs(rng.normal(0, dz)) * rng.integers(0, 2)
+        qlo, qhi = _uniform_range(z_lo, z_hi, cz, float(off[0]), 1.0 / d_host, K)
+        inside = np.flatnonzero((oz >= np.float32(z_lo)) & (oz <= np.float32(z_hi)))
+        bad += int(np.sum((inside < qlo) | (inside > qhi)))
+    return bad
+
+
+def test_closed_form_source_range_keeps_every_source_at_the_allowed_spacing():
+    """At the smallest step the library allows for the closed form, no source
+    whose FP32 height lies in the lamp-height interval falls outside the
+    closed-form index range; at a thousandth of it some would (which is why
+    closer sources take the per-source height test)."""
+    rng = np.random.default_rng(5)
+    assert _violations(rng, 1.0) == 0
+    assert _violations(np.random.default_rng(6), 1e-3, trials=2000) > 0
