@@ -101,6 +101,13 @@ typedef struct uvc_scene uvc_scene; /* opaque; owns its device buffers */
  *   patches, np         see uvc_patches; excl entries in [-1, nt)
  *   out                 receives the new scene (freed with uvc_free_scene)
  *
+ * All geometry is FP32, and the tolerances of the searches scale with the
+ * scene's size D (the diagonal of its bounding box: box widening 1e-5 D,
+ * grazing band 1e-7 D): they assume coordinates of the order of D, where FP32
+ * resolves 2^-24 |x|.  A scene far from the origin (|x| >> D) should be
+ * translated near it, with its candidates, before upload; the library does
+ * not move it.
+ *
  * nt may be 0 (nothing occludes).  Returns UVC_E_INVAL for NULL pointers,
  * counts out of range, an index out of range or a non-finite coordinate
  * (checked on the device, then reported after one stream synchronisation),
