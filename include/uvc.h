@@ -102,9 +102,9 @@ typedef struct uvc_scene uvc_scene; /* opaque; owns its device buffers */
  *   out                 receives the new scene (freed with uvc_free_scene)
  *
  * All geometry is FP32, and the tolerances of the searches scale with the
- * scene's size D (the diagonal of its bounding box: box widening 1e-5 D,
- * grazing band 1e-7 D): they assume coordinates of the order of D, where FP32
- * resolves 2^-24 |x|.  A scene far from the origin (|x| >> D) should be
+ * scene's size D (the diagonal of its bounding box: box widening and
+ * clearance slack 1e-5 D, coplanar margin 2^-14 D): they assume coordinates of
+ * the order of D, where FP32 resolves 2^-24 |x|.  A scene far from the origin (|x| >> D) should be
  * translated near it, with its candidates, before upload; the library does
  * not move it.
  *
