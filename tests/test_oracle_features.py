@@ -29,6 +29,9 @@ def test_point_triangle_distance():
     assert np.isclose(d([-1.0, -1.0, 0.0]), np.sqrt(2))            # nearest to vertex a
     assert np.isclose(d([1.0, -2.0, 0.0]), 2.0)                    # nearest to edge ab
     assert np.isclose(d([2.0, 2.0, 0.0]), np.sqrt(2))              # nearest to edge bc (x+y=2)
+    assert np.isclose(d([3.0, -1.0, 0.0]), np.sqrt(2))             # nearest to vertex b
+    assert np.isclose(d([-1.0, 3.0, 1.0]), np.sqrt(3))             # nearest to vertex c
+    assert np.isclose(d([-2.0, 1.0, 0.0]), 2.0)                    # nearest to edge ca (x = 0)
     rng = np.random.default_rng(0)
     uv = rng.uniform(size=(20000, 2))
     uv = np.where(uv.sum(1, keepdims=True) > 1, 1 - uv, uv)

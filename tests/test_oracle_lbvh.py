@@ -26,6 +26,14 @@ def test_morton_hand_values():
     assert [int(x) for x in k] == want
 
 
+def test_reference_point_is_the_box_centre():
+    """The key of a triangle is taken at the centre of its bounding box
+    (worked by hand: boxes [0,2]x[0,4]x[0,6] and [-1,3]x[1,5]x[-2,4])."""
+    v = np.array([[0, 0, 0], [2, 0, 0], [0, 4, 6], [1, 5, -2], [3, 1, 0], [-1, 2, 4]], np.float32)
+    t = np.arange(6, dtype=np.int32).reshape(2, 3)
+    assert np.array_equal(lbvh.reference_points(v, t), np.array([[1, 2, 3], [1, 3, 1]], np.float32))
+
+
 def test_stable_sort_keeps_triangle_order_on_ties():
     keys = np.array([5, 3, 5, 3, 1, 5], np.uint64)
     sk, order = lbvh.sort_keys(keys)
