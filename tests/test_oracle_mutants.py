@@ -2,8 +2,11 @@
 at least one pin: evidence that the pins constrain every term of Eq. (7), the
 visibility rule, the source layout and the grazing flags, and likewise the
 area-mean closed form (solid angles, area normalisation, vertex checks,
-fallback) and the visibility-cube estimator (pixel solid angles and powers,
-nearest hit, front faces, pixel centres).  Runs on the CPU."""
+fallback), the visibility-cube estimator (pixel solid angles and powers,
+nearest hit, front faces, pixel centres) and the CPU hierarchy (child boxes,
+box padding, slab clipping, leaf loops), whose results must then differ from
+the brute force.  Runs on the CPU."""
+import inspect
 import os
 import subprocess
 
@@ -49,13 +52,28 @@ def _mutant_lib(old, new, tmp_path, unique=False):
     return oracle.load_library(str(so))
 
 
+def _calls(fn):
+    """The argument tuples a pin runs with: () for a plain test, each value of
+    a one-name parametrize mark; pins taking fixtures are left out."""
+    params = inspect.signature(fn).parameters
+    if not params:
+        return [()]
+    marks = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+    if len(marks) == 1 and len(params) == 1 and marks[0].args[0] == next(iter(params)):
+        return [(v,) for v in marks[0].args[1]]
+    return []
+
+
 def _caught_by(pins_module):
     caught = []
-    for fn in sorted(n for n in dir(pins_module) if n.startswith("test_")):
-        try:
-            getattr(pins_module, fn)()
-        except AssertionError:
-            caught.append(fn)
+    for name in sorted(n for n in dir(pins_module) if n.startswith("test_")):
+        fn = getattr(pins_module, name)
+        for args in _calls(fn):
+            try:
+                fn(*args)
+            except AssertionError:
+                caught.append(name)
+                break
     return caught
 
 
@@ -117,3 +135,33 @@ def test_raster_mutant_is_caught(name, tmp_path, monkeypatch):
     from tests import test_oracle_raster as pins
     monkeypatch.setattr(oracle, "_lib", _mutant_lib(*RASTER_MUTANTS[name], tmp_path, unique=True))
     assert _caught_by(pins), f"mutant {name} passed every raster pin"
+
+
+# Mistakes in the oracle's CPU hierarchy (bvh_build, the box tests, the
+# hierarchical visibility and grazing searches), each of which must make its
+# results differ from the brute force somewhere in tests/test_oracle_bvh.py.
+BVH_MUTANTS = {
+    "right_box_misses_its_last_triangle": ("box_of(T, B->order, R->first, R->count, R->lo, R->hi);",
+                                           "box_of(T, B->order, R->first, R->count - 1, R->lo, R->hi);"),
+    "boxes_shrunk_for_visibility": ("const double pad = 1e-9 * B->diag + 1e-300;",
+                                    "const double pad = -1e-3 * B->diag;"),
+    "grazing_boxes_without_the_band": ("const double pad = eps + 1e-9 * B->diag + 1e-300;",
+                                       "const double pad = -1e-3 * B->diag;"),
+    "slab_exit_from_the_entry": ("if (tb < t1) t1 = tb;", "if (tb < t1) t1 = ta;"),
+    "visibility_leaf_skips_its_last": (
+        "for (int64_t q = nd->first; q < nd->first + nd->count; ++q) {\n"
+        "                const int64_t t = B->order[q];\n"
+        "                if (t == ex0 || t == ex1) continue;\n"
+        "                if (segment_meets_triangle",
+        "for (int64_t q = nd->first; q < nd->first + nd->count - 1; ++q) {\n"
+        "                const int64_t t = B->order[q];\n"
+        "                if (t == ex0 || t == ex1) continue;\n"
+        "                if (segment_meets_triangle"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BVH_MUTANTS))
+def test_bvh_mutant_is_caught(name, tmp_path, monkeypatch):
+    from tests import test_oracle_bvh as pins
+    monkeypatch.setattr(oracle, "_lib", _mutant_lib(*BVH_MUTANTS[name], tmp_path, unique=True))
+    assert _caught_by(pins), f"mutant {name} passed every hierarchy pin"
