@@ -126,6 +126,8 @@ __global__ void k_feat_clear(const Node* __restrict__ nodes, const float4* __res
         const Node nd = nodes[ref];
         const float dL = box_d2(p, nd.x.x, nd.y.x, nd.z.x, nd.x.z, nd.y.z, nd.z.z);
         const float dR = box_d2(p, nd.x.y, nd.y.y, nd.z.y, nd.x.w, nd.y.w, nd.z.w);
+        // never taken: the stack holds at most one pending sibling per level, and
+        // the radix tree over 64-bit keys and 32-bit positions is at most 96 deep
         if (top + 2 > 128) break;
         const bool lfirst = dL <= dR;
         if ((lfirst ? dR : dL) < best) stack[top++] = lfirst ? nd.r.y : nd.r.x;
