@@ -391,7 +391,9 @@ int uvc_batch_free(uvc_batch* batch);
  *   cand  float[nc][3] device;  feat  float rows of ldf >= 66 floats, device
  *   (caller-owned; columns 66..ldf-1 untouched).
  * FP32 arithmetic with fixed-order sums (deterministic).  Errors: UVC_E_INVAL
- * (NULL scene, nc out of range, NULL buffer with nc > 0), UVC_E_CUDA.
+ * (NULL scene, nc out of range, NULL buffer with nc > 0), UVC_E_STACK (a
+ * hierarchy deeper than 126 levels, beyond the nearest-triangle search's
+ * fixed stack), UVC_E_CUDA.
  */
 int uvc_candidate_features(const uvc_scene* scene, const float* cand, int64_t nc, float* feat, int64_t ldf,
                            uvc_stream_t stream);

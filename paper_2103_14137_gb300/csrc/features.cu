@@ -126,8 +126,9 @@ __global__ void k_feat_clear(const Node* __restrict__ nodes, const float4* __res
         const Node nd = nodes[ref];
         const float dL = box_d2(p, nd.x.x, nd.y.x, nd.z.x, nd.x.z, nd.y.z, nd.z.z);
         const float dR = box_d2(p, nd.x.y, nd.y.y, nd.z.y, nd.x.w, nd.y.w, nd.z.w);
-        // never taken: the stack holds at most one pending sibling per level, and
-        // the radix tree over 64-bit keys and 32-bit positions is at most 96 deep
+        // never taken: the stack holds at most one pending sibling per level plus
+        // the two children just pushed, and candidate_features refuses trees
+        // deeper than 126
         if (top + 2 > 128) break;
         const bool lfirst = dL <= dR;
         if ((lfirst ? dR : dL) < best) stack[top++] = lfirst ? nd.r.y : nd.r.x;
@@ -487,6 +488,7 @@ int select_top(const float* score, int64_t n, int64_t k, const float* cand, floa
 int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, int64_t ldf,
                        cudaStream_t stream) {
     if (nc == 0) return UVC_OK;
+    if (sc->depth > 126) return UVC_E_STACK;   // k_feat_clear's fixed stack of 128 entries
     Edges E;
     for (int b = 1; b < kBins; ++b) {
         const double e = 0.1 * std::pow(250.0, (double)b / kBins);
