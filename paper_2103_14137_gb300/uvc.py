@@ -138,16 +138,33 @@ def _stream(stream):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def _matrix_rows(x: torch.Tensor, name, nrows: int):
-    """A float32 CUDA matrix with unit column stride whose rows may be padded
-    (a view of the first columns of a wider buffer): (pointer, row stride)."""
-    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or x.dim() != 2:
-        raise TypeError(f"{name} must be a 2-D float32 CUDA tensor")
-    if x.shape[0] != nrows:
-        raise ValueError(f"{name} must have {nrows} rows, got {x.shape[0]}")
-    if x.numel() and x.stride(1) != 1:
+def _row_layout(shape, strides, name, nrows: int, ncols: int) -> int:
+    """Row stride (lda) of an (nrows, >= ncols) matrix with unit column stride
+    whose rows may be padded; rejects every layout the library would read or
+    write outside of (too few rows or columns, overlapping rows)."""
+    if len(shape) != 2:
+        raise TypeError(f"{name} must be 2-D")
+    rows, cols = shape
+    if rows != nrows:
+        raise ValueError(f"{name} must have {nrows} rows, got {rows}")
+    if cols < ncols:
+        raise ValueError(f"{name} must have at least {ncols} columns, got {cols}")
+    if rows * cols == 0:
+        return cols
+    if strides[1] != 1:
         raise ValueError(f"{name} must have unit column stride")
-    lda = max(x.stride(0), x.shape[1]) if x.shape[0] > 1 else x.shape[1]
+    if rows > 1 and strides[0] < cols:
+        raise ValueError(f"{name} has overlapping rows (row stride {strides[0]} < {cols} columns)")
+    return strides[0] if rows > 1 else cols
+
+
+def _matrix_rows(x: torch.Tensor, name, nrows: int, ncols: int):
+    """A float32 CUDA matrix of nrows rows and at least ncols columns, unit
+    column stride, rows possibly padded (a view of the first columns of a
+    wider buffer): (pointer, row stride)."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32:
+        raise TypeError(f"{name} must be a float32 CUDA tensor")
+    lda = _row_layout(tuple(x.shape), tuple(x.stride()), name, nrows, ncols)
     return ctypes.c_void_p(x.data_ptr() if x.numel() else 0), lda
 
 
@@ -259,7 +276,7 @@ def irradiance_matrix(scene: Scene, cand, lamp: Lamp, A=None, vis=None, with_vis
         raise ValueError("A must be (nc, lda)")
     vptr = None if vis is None else _dev(vis, torch.int32, "vis", (lamp.K, nc, (scene.np + 31) // 32))
     L = lamp._c()
-    aptr, lda = _matrix_rows(A, "A", nc)
+    aptr, lda = _matrix_rows(A, "A", nc, scene.np)
     rc = library().uvc_irradiance_matrix(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
                                          ctypes.byref(L), aptr, lda, vptr, _stream(stream))
     _check(rc, "uvc_irradiance_matrix")
@@ -286,7 +303,7 @@ def irradiance_counters(scene: Scene, cand, lamp: Lamp, A=None, stream=None) -> 
         A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
     out = np.zeros(len(COUNTER_NAMES), np.uint64)
     L = lamp._c()
-    aptr, lda = _matrix_rows(A, "A", nc)
+    aptr, lda = _matrix_rows(A, "A", nc, scene.np)
     rc = library().uvc_irradiance_counters(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
                                            ctypes.byref(L), aptr, lda, ctypes.c_void_p(out.ctypes.data),
                                            _stream(stream))
@@ -303,10 +320,10 @@ def irradiance_area_mean(scene: Scene, cand, lamp: Lamp, ptri, A=None, with_clos
         A = torch.empty((nc, scene.np), dtype=torch.float32, device=cand.device)
     ncl = torch.empty((nc, scene.np), dtype=torch.uint8, device=cand.device) if with_closed else None
     L = lamp._c()
+    aptr, lda = _matrix_rows(A, "A", nc, scene.np)
     rc = library().uvc_irradiance_area_mean(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
                                             ctypes.byref(L), _dev(ptri, torch.float32, "ptri", (scene.np, 2, 3, 3)),
-                                            _dev(A, torch.float32, "A"), A.shape[1] if A.dim() == 2 else 0,
-                                            None if ncl is None else _dev(ncl, torch.uint8, "nclosed"),
+                                            aptr, lda, None if ncl is None else _dev(ncl, torch.uint8, "nclosed"),
                                             _stream(stream))
     _check(rc, "uvc_irradiance_area_mean")
     return A, ncl
@@ -329,10 +346,11 @@ def irradiance_raster(scene: Scene, tri_normal, cand, lamp: Lamp, R: int = 512, 
     if workspace is None:
         workspace = raster_workspace(scene, lamp, R, max(1, min(cand_per_batch, nc)), cand.device)
     L = lamp._c()
+    aptr, lda = _matrix_rows(A, "A", nc, scene.nt)
     rc = library().uvc_irradiance_raster(scene.handle, _dev(tri_normal, torch.float32, "tri_normal", (scene.nt, 3)),
                                          _dev(cand, torch.float32, "cand", (nc, 3)), nc, ctypes.byref(L), int(R),
-                                         _dev(A, torch.float32, "A"), A.shape[1] if A.dim() == 2 else 0,
-                                         ctypes.c_void_p(workspace.data_ptr()), workspace.numel(), _stream(stream))
+                                         aptr, lda, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
+                                         _stream(stream))
     _check(rc, "uvc_irradiance_raster")
     return A
 
@@ -343,7 +361,7 @@ def fluence(scene: Scene, A, t, mu=None, stream=None):
     nvec, nc = t.shape
     if mu is None:
         mu = torch.empty((nvec, scene.np), dtype=torch.float32, device=t.device)
-    aptr, lda = _matrix_rows(A, "A", nc)
+    aptr, lda = _matrix_rows(A, "A", nc, scene.np)
     rc = library().uvc_fluence(scene.handle, aptr, nc, lda, _dev(t, torch.float32, "t", (nvec, nc)), nvec,
                                _dev(mu, torch.float32, "mu", (nvec, scene.np)), _stream(stream))
     _check(rc, "uvc_fluence")

@@ -119,3 +119,22 @@ def test_wedge_switch_is_host_only(lib):
     assert uvc.set_wedge_traversal(False) is True and uvc.set_wedge_traversal(True) is False
     assert lib.uvc_set_wedge_traversal(1, ctypes.byref(prev)) == 0 and prev.value == 1
     assert lib.uvc_set_wedge_traversal(1, None) == 0
+
+
+def test_matrix_row_layouts():
+    """The binding passes the library a row stride only for layouts it can
+    read and write in bounds: padded rows are fine, too few rows or columns
+    and overlapping rows are refused (host logic, no GPU)."""
+    from paper_2103_14137_gb300.uvc import _row_layout
+    assert _row_layout((4, 10), (10, 1), "A", 4, 10) == 10            # contiguous
+    assert _row_layout((4, 10), (16, 1), "A", 4, 10) == 16            # view of a wider buffer
+    assert _row_layout((4, 12), (12, 1), "A", 4, 10) == 12            # more columns than written
+    assert _row_layout((1, 10), (99, 1), "A", 1, 10) == 10            # one row: its stride is unused
+    assert _row_layout((0, 10), (10, 1), "A", 0, 10) == 10            # no rows
+    for shape, strides, exc in (((3, 10), (10, 1), ValueError),        # wrong row count
+                                ((4, 9), (16, 1), ValueError),         # narrower view than the columns written
+                                ((4, 10), (1, 4), ValueError),         # transposed (column stride 4)
+                                ((4, 10), (5, 1), ValueError),         # overlapping rows
+                                ((4,), (1,), TypeError)):
+        with pytest.raises(exc):
+            _row_layout(shape, strides, "A", 4, 10)
