@@ -349,8 +349,8 @@ def irradiance_raster(scene: Scene, tri_normal, cand, lamp: Lamp, R: int = 512, 
     aptr, lda = _matrix_rows(A, "A", nc, scene.nt)
     rc = library().uvc_irradiance_raster(scene.handle, _dev(tri_normal, torch.float32, "tri_normal", (scene.nt, 3)),
                                          _dev(cand, torch.float32, "cand", (nc, 3)), nc, ctypes.byref(L), int(R),
-                                         aptr, lda, ctypes.c_void_p(workspace.data_ptr()), workspace.numel(),
-                                         _stream(stream))
+                                         aptr, lda, _scratch(workspace, 0, "workspace"),
+                                         workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "uvc_irradiance_raster")
     return A
 
@@ -439,22 +439,29 @@ def probe_features_work(np_: int, device="cuda"):
     return torch.empty((n + 3) // 4, dtype=torch.float32, device=device)
 
 
-def probe_features(A, area, feat=None, work=None, lda=None, stream=None):
+def _scratch(buf, nbytes: int, name):
+    """Device pointer of a caller-supplied scratch buffer of at least nbytes."""
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    if buf.numel() * buf.element_size() < nbytes:
+        raise ValueError(f"{name} holds {buf.numel() * buf.element_size()} bytes, {nbytes} needed")
+    return ctypes.c_void_p(buf.data_ptr())
+
+
+def probe_features(A, area, feat=None, work=None, stream=None):
     """(nc, 48) visibility sketch from the probe irradiance A (nc, np): area of
     the lit probe patches by hardness and efficiency bin (uvc_probe_features).
     A may be a column slice (unit column stride) of a wider matrix."""
     nc, np_ = A.shape
-    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
-        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
-    lda = max(A.stride(0), np_) if lda is None else lda
+    aptr, lda = _matrix_rows(A, "A", nc, np_)
     if feat is None:
         feat = torch.empty((nc, PROBE_FEATURES), dtype=torch.float32, device=A.device)
     if work is None:
         work = probe_features_work(np_, A.device)
+    wptr = _scratch(work, int(library().uvc_probe_features_work_bytes(int(np_))), "work")
     fp, ld = _rows(feat, nc, PROBE_FEATURES, "feat")
-    rc = library().uvc_probe_features(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, lda, np_,
-                                      _dev(area, torch.float32, "area", (np_,)),
-                                      ctypes.c_void_p(work.data_ptr()), fp, ld, _stream(stream))
+    rc = library().uvc_probe_features(aptr, nc, lda, np_, _dev(area, torch.float32, "area", (np_,)), wptr, fp, ld,
+                                      _stream(stream))
     _check(rc, "uvc_probe_features")
     return feat
 
@@ -488,10 +495,9 @@ def mark_best(A, score, value=float("inf"), rare: int = 0, stream=None):
     """score[argmax_i A[i, j]] = value for every lit column j of A (nc, np);
     with rare > 0 also every candidate lighting a column lit by <= rare rows."""
     nc, np_ = A.shape
-    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
-        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
-    rc = library().uvc_mark_best(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, max(A.stride(0), np_), np_,
-                                 _dev(score, torch.float32, "score", (nc,)), float(value), int(rare), _stream(stream))
+    aptr, lda = _matrix_rows(A, "A", nc, np_)
+    rc = library().uvc_mark_best(aptr, nc, lda, np_, _dev(score, torch.float32, "score", (nc,)), float(value),
+                                 int(rare), _stream(stream))
     _check(rc, "uvc_mark_best")
     return score
 
@@ -505,10 +511,8 @@ def probe_lost(A, idx, area, out=None, lost=None, stream=None):
         out = torch.empty(1, dtype=torch.float32, device=A.device)
     if lost is None:
         lost = torch.empty(np_, dtype=torch.float32, device=A.device)
-    if A.dtype != torch.float32 or not A.is_cuda or (np_ > 0 and A.stride(1) != 1):
-        raise TypeError("A must be a float32 CUDA matrix with unit column stride")
-    lda = max(A.stride(0), np_)
-    rc = library().uvc_probe_lost(ctypes.c_void_p(A.data_ptr() if A.numel() else 0), nc, lda, np_,
+    aptr, lda = _matrix_rows(A, "A", nc, np_)
+    rc = library().uvc_probe_lost(aptr, nc, lda, np_,
                                   _dev(idx, torch.int32, "idx", (k,)), k,
                                   _dev(area, torch.float32, "area", (np_,)), _dev(lost, torch.float32, "lost", (np_,)),
                                   _dev(out, torch.float32, "out", (1,)), _stream(stream))
