@@ -635,15 +635,15 @@ class Batch:
         self._keep = []
         for q, (scene, cand, lamp, A, vis) in enumerate(jobs):
             nc = cand.shape[0]
+            if not 0 <= int(lamp) < len(lamps):
+                raise ValueError(f"job {q}: lamp index {lamp} out of range")
             cj[q].scene = scene.handle
             cj[q].cand = _dev(cand, torch.float32, "cand", (nc, 3))
             cj[q].nc = nc
             cj[q].lamp = int(lamp)
-            cj[q].A = _dev(A, torch.float32, "A")
-            cj[q].lda = A.shape[1]
-            if A.dim() != 2 or A.shape[0] != nc:
-                raise ValueError("A must be (nc, lda)")
-            cj[q].vis = None if vis is None else _dev(vis, torch.int32, "vis")
+            cj[q].A, cj[q].lda = _matrix_rows(A, "A", nc, scene.np)
+            cj[q].vis = None if vis is None else _dev(vis, torch.int32, "vis",
+                                                      (lamps[int(lamp)].K, nc, (scene.np + 31) // 32))
             self._keep.append((scene, cand, A, vis))
         cl = (_Lamp * len(lamps))(*[L._c() for L in lamps])
         nbytes = lib.uvc_batch_workspace_bytes(len(jobs), len(lamps))
