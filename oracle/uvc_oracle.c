@@ -731,6 +731,36 @@ int uvco_area_mean_bvh(const float* verts, int64_t nv, const int32_t* tris, int6
  */
 static double pixel_G(double u, double v) { return atan(u * v / sqrt(1.0 + u * u + v * v)); }
 
+/* Could the pixel ray o + t dir (t > 0, |dir| = dl) reach triangle T within
+ * the rounding an FP32 rasteriser may make?  tmax: the farthest parameter a
+ * receiver may have (just beyond the nearest robust hit, or past the whole
+ * scene when there is none).  A triangle the ray's line crosses is near when
+ * the crossing point, at parameter tt in (0, tmax], lies within rel * tt * dl
+ * of it; a triangle met edge-on (the ray parallel to its plane, det = 0) is
+ * near when the stretch of the ray from o to parameter tmax passes within
+ * rel * tmax * dl of it (distance of that segment from the triangle's edges
+ * and of its end points from the triangle). */
+static int raster_receiver(const tri64* T, d3 o, d3 dir, double dl, double tmax, double rel) {
+    d3 e1 = vsub(T->b, T->a), e2 = vsub(T->c, T->a);
+    d3 p = vcross(dir, e2);
+    double det = vdot(e1, p);
+    if (det == 0.0) {
+        d3 q = vadd(o, vmul(dir, tmax));
+        double dist = fmin(point_triangle_distance(o, T->a, T->b, T->c),
+                           point_triangle_distance(q, T->a, T->b, T->c));
+        dist = fmin(dist, segment_segment_distance(o, q, T->a, T->b));
+        dist = fmin(dist, segment_segment_distance(o, q, T->b, T->c));
+        dist = fmin(dist, segment_segment_distance(o, q, T->c, T->a));
+        return dist <= rel * tmax * dl;
+    }
+    d3 r = vsub(o, T->a);
+    d3 qq = vcross(r, e1);
+    double tt = vdot(e2, qq) / det;
+    if (!(tt > 0.0) || tt > tmax) return 0;
+    d3 h = vadd(o, vmul(dir, tt));
+    return point_triangle_distance(h, T->a, T->b, T->c) <= rel * tt * dl;
+}
+
 int uvco_raster(const float* verts, int64_t nv, const int32_t* tris, int64_t nt, const float* tri_normal,
                 const float* cand, int64_t nc, const float* offsets, const float* weights, int32_t K, double power,
                 int32_t R, double rel, double* F_out, double* amb_out, int nthreads) {
@@ -740,6 +770,19 @@ int uvco_raster(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     if (build_tris(verts, nv, tris, nt, T) != 0) { free(T); return -1; }
     for (int64_t k = 0; k < nc * nt; ++k) { F_out[k] = 0.0; if (amb_out) amb_out[k] = 0.0; }
     const int64_t npix = 6 * (int64_t)R * R;
+    /* bounding box of the triangles: a ray that meets nothing robustly is
+     * followed to the far side of the scene when looking for receivers */
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < nt; ++t) {
+        const d3 w[3] = {T[t].a, T[t].b, T[t].c};
+        for (int k = 0; k < 3; ++k) {
+            lo[0] = fmin(lo[0], w[k].x); hi[0] = fmax(hi[0], w[k].x);
+            lo[1] = fmin(lo[1], w[k].y); hi[1] = fmax(hi[1], w[k].y);
+            lo[2] = fmin(lo[2], w[k].z); hi[2] = fmax(hi[2], w[k].z);
+        }
+    }
+    const d3 mid = v3(0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2]));
+    const double radius = nt > 0 ? 0.5 * vnorm(v3(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2])) : 0.0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -808,31 +851,21 @@ int uvco_raster(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     }
                 }
                 if (!amb_out) continue;
-                /* receivers: inside or near, and not behind the nearest robust hit */
-                int64_t rec[16];
+                /* receivers: inside or near, and not behind the nearest robust
+                 * hit; every one of them gets the pixel's power when there are
+                 * at least two (a first pass counts them, a second adds) */
+                const double tmax = isfinite(trob) ? trob * (1.0 + rel) : (vnorm(vsub(o, mid)) + radius) / dl;
                 int nrec = 0;
-                for (int64_t t = 0; t < nt && nrec < 16; ++t) {
-                    d3 e1 = vsub(T[t].b, T[t].a), e2 = vsub(T[t].c, T[t].a);
-                    d3 p = vcross(dir, e2);
-                    double det = vdot(e1, p);
-                    d3 r = vsub(o, T[t].a);
-                    if (det == 0.0) {
-                        /* edge-on: near if the ray passes within rel of the triangle */
-                        continue;
-                    }
-                    d3 qq = vcross(r, e1);
-                    double tt = vdot(e2, qq) / det;
-                    if (!(tt > 0.0) || tt > trob * (1.0 + rel)) continue;
-                    d3 h = vadd(o, vmul(dir, tt));
-                    if (point_triangle_distance(h, T[t].a, T[t].b, T[t].c) <= rel * tt * dl) rec[nrec++] = t;
-                }
+                for (int64_t t = 0; t < nt && nrec < 2; ++t)
+                    if (raster_receiver(&T[t], o, dir, dl, tmax, rel)) ++nrec;
                 if (nrec >= 2)
-                    for (int k = 0; k < nrec; ++k) {
+                    for (int64_t t = 0; t < nt; ++t)
+                        if (raster_receiver(&T[t], o, dir, dl, tmax, rel)) {
 #ifdef _OPENMP
 #pragma omp atomic
 #endif
-                        amb_out[i * nt + rec[k]] += e;
-                    }
+                            amb_out[i * nt + t] += e;
+                        }
             }
         }
     free(T);

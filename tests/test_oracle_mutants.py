@@ -127,6 +127,8 @@ RASTER_MUTANTS = {
                                  "float uf = (float)(2 * px) / (float)R - 1.0f;"),
     "barycentric_bound": ("int inside = uu >= 0.0 && ww >= 0.0 && uu + ww <= 1.0;",
                           "int inside = uu >= 0.0 && ww >= 0.0 && uu + ww <= 1.5;"),
+    "edge_on_receivers_skipped": ("    if (det == 0.0) {\n        d3 q = vadd(o, vmul(dir, tmax));",
+                                  "    if (det == 0.0) {\n        return 0;\n        d3 q = vadd(o, vmul(dir, tmax));"),
 }
 
 

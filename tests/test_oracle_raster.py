@@ -100,3 +100,35 @@ def test_back_facing_wall_absorbs():
 def test_pixel_solid_angles_cover_the_sphere():
     for R in (1, 7, 64):
         assert math.isclose(6 * oracle.pixel_solid_angles(R).sum(), 4 * math.pi, rel_tol=1e-12)
+
+
+def test_edge_on_triangle_is_an_ambiguous_receiver():
+    """A triangle in the plane y = 1 through the source (1, 1, 1) is met
+    edge-on by the rays of the middle pixel row of the +z face (odd R, so that
+    row's rays have no y component): an FP32 rasteriser may give those pixels
+    to it or to the ceiling behind it, so the oracle marks their power
+    ambiguous on both, although neither the exact ray cast nor the FP32 one
+    hits the edge-on triangle."""
+    v, t, n = cube_room()
+    R = 9
+    edge = np.array([[0.7, 1.0, 1.6], [1.3, 1.0, 1.6], [1.0, 1.0, 1.9]], np.float32)
+    v2 = np.concatenate([v, edge])
+    t2 = np.concatenate([t, np.array([[8, 9, 10]], np.int32)])
+    n2 = np.concatenate([n, np.array([[0, 1, 0]], np.float32)])
+    F, amb = run(v2, t2, n2, (1.0, 1.0, 1.0), R)
+    assert F[0, 12] == 0.0                              # edge-on: no exact hit
+    # pixels of the middle row of the +z face (face 4) whose ray passes through
+    # the triangle's interior: u = (2 px + 1)/R - 1 with |u| < 0.5 (at z = 1.6
+    # the triangle spans x in [0.7, 1.3]; at its apex it narrows, but the ray at
+    # u reaches z = 1.6 inside it)
+    om = oracle.pixel_solid_angles(R)                  # [py, px]
+    py = (R - 1) // 2
+    u = (2 * np.arange(R) + 1) / R - 1
+    inside = np.abs(u) < 0.5
+    want = 6.0 / (4 * math.pi) * om[py, inside].sum()
+    assert want > 0
+    assert amb[0, 12] >= want * (1 - 1e-12)
+    # the same power is marked on the ceiling triangles that lie behind it
+    assert amb[0, 2:4].sum() >= want * (1 - 1e-12)
+    # the other pixels of the face stay unambiguous for the edge-on triangle
+    assert amb[0, 12] <= 6.0 / (4 * math.pi) * om[py].sum() * (1 + 1e-12)
