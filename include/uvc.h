@@ -297,8 +297,10 @@ int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, 
  *   Limit: 4 * nvec * np must not exceed 64 MiB (67,108,864 bytes), else
  *   UVC_E_SCRATCH and nothing is launched.
  *   The first call on a device looks up the array's device address for that
- *   device (cudaGetSymbolAddress) and caches it; make that first call before
- *   any stream capture.  All calls share the one array, which keeps the last
+ *   device (cudaGetSymbolAddress) and caches it, keyed on the device and its
+ *   current context (after a cudaDeviceReset the first call in the new
+ *   context looks it up again); make that first call before any stream
+ *   capture.  All calls share the one array, which keeps the last
  *   call's contents (each call writes every partial before reading it), so
  *   calls whose work overlaps on the GPU (e.g. on two streams at once) race
  *   and corrupt each other: serialise them.
@@ -529,7 +531,8 @@ const char* uvc_status_string(int status);
 /*
  * uvc_scene_status - synchronise `stream`, then return and clear the scene's
  * device status word: UVC_OK, or the first device-side error recorded since
- * the last call (UVC_E_TIMEOUT, UVC_E_STACK).
+ * the last call (UVC_E_TIMEOUT, UVC_E_STACK; in the checked build also
+ * UVC_E_BOUNDS, see uvc_library_flags).
  */
 int uvc_scene_status(const uvc_scene* scene, uvc_stream_t stream);
 

@@ -164,13 +164,23 @@ def _matrix_rows(x: torch.Tensor, name, nrows: int, ncols: int):
     wider buffer): (pointer, row stride)."""
     if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32:
         raise TypeError(f"{name} must be a float32 CUDA tensor")
+    _on_current_device(x, name)
     lda = _row_layout(tuple(x.shape), tuple(x.stride()), name, nrows, ncols)
     return ctypes.c_void_p(x.data_ptr() if x.numel() else 0), lda
+
+
+def _on_current_device(x: torch.Tensor, name):
+    """The library runs on the calling thread's current device; a tensor on
+    another GPU would hand its kernels pointers into another device's memory."""
+    cur = torch.cuda.current_device()
+    if x.device.index != cur:
+        raise ValueError(f"{name} is on cuda:{x.device.index}, the current device is cuda:{cur}")
 
 
 def _dev(x: torch.Tensor, dtype, name, shape=None):
     if not isinstance(x, torch.Tensor) or not x.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
+    _on_current_device(x, name)
     if x.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
     if not x.is_contiguous():
@@ -210,20 +220,14 @@ def point_lamp(power: float) -> Lamp:
     return Lamp(np.zeros((1, 3)), np.ones(1), power)
 
 
-def line_lamp(length: float, K: int, power: float) -> Lamp:
-    """Vertical tube from the candidate point up to +length: K equal-power
-    sources at the midpoints of K equal pieces."""
-    z = length * (np.arange(K, dtype=np.float64) + 0.5) / K
-    off = np.zeros((K, 3))
-    off[:, 2] = z
-    return Lamp(off, np.full(K, 1.0 / K), power)
-
-
 class Scene:
-    """A built scene (uvc_build_scene); owns device memory until free()."""
+    """A built scene (uvc_build_scene); owns device memory until free().  It
+    lives on the device that was current when it was built and is used only
+    while that device is current."""
 
     def __init__(self, handle, keepalive=()):
         self._h = handle
+        self.device = torch.cuda.current_device()
         nt, np_, depth = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
         _check(library().uvc_scene_info(handle, ctypes.byref(nt), ctypes.byref(np_), ctypes.byref(depth)),
                "uvc_scene_info")
@@ -233,6 +237,9 @@ class Scene:
     def handle(self):
         if self._h is None:
             raise RuntimeError("scene already freed")
+        cur = torch.cuda.current_device()
+        if cur != self.device:
+            raise ValueError(f"scene was built on cuda:{self.device}, the current device is cuda:{cur}")
         return self._h
 
     def free(self):
@@ -414,6 +421,7 @@ PROBE_FEATURES = 48
 def _rows(feat, nc, min_cols, name):
     if not isinstance(feat, torch.Tensor) or not feat.is_cuda or feat.dtype != torch.float32:
         raise TypeError(f"{name} must be a float32 CUDA tensor")
+    _on_current_device(feat, name)
     if feat.dim() != 2 or feat.shape[0] != nc or feat.shape[1] < min_cols or feat.stride(1) != 1 \
             or (nc > 1 and feat.stride(0) < min_cols):
         raise ValueError(f"{name} must be ({nc}, >= {min_cols}) with unit column stride")
@@ -443,6 +451,7 @@ def _scratch(buf, nbytes: int, name):
     """Device pointer of a caller-supplied scratch buffer of at least nbytes."""
     if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
         raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    _on_current_device(buf, name)
     if buf.numel() * buf.element_size() < nbytes:
         raise ValueError(f"{name} holds {buf.numel() * buf.element_size()} bytes, {nbytes} needed")
     return ctypes.c_void_p(buf.data_ptr())

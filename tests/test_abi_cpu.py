@@ -72,22 +72,14 @@ def test_null_arguments_rejected_without_gpu(lib):
 
 
 def test_lamp_struct_layout():
-    from paper_2103_14137_gb300.uvc import _Lamp, line_lamp
+    from paper_2103_14137_gb300.uvc import Lamp, _Lamp
+    from synth import line_lamp
     assert ctypes.sizeof(_Lamp) == 4 + 4 + 32 * 3 * 4 + 32 * 4
-    L = line_lamp(1.2, 8, 120.0)
-    c = L._c()
+    g = line_lamp(1.2, 8, 120.0)
+    c = Lamp(g.offsets, g.weights, g.power)._c()
     assert c.K == 8 and abs(c.power - 120.0) < 1e-6
     assert np.allclose([c.offsets[m][2] for m in range(8)], 1.2 * (np.arange(8) + 0.5) / 8)
     assert np.isclose(sum(c.weight[m] for m in range(8)), 1.0)
-
-
-def test_product_line_lamp_matches_generator():
-    """The binding's line lamp and the input generator's are written separately;
-    they must describe the same sources."""
-    from paper_2103_14137_gb300.uvc import line_lamp
-    from synth import line_lamp as gen_line_lamp
-    a, b = line_lamp(1.8, 12, 80.0), gen_line_lamp(1.8, 12, 80.0)
-    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.weights, b.weights)
 
 
 def test_vis_unpacking():

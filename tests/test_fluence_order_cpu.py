@@ -15,8 +15,29 @@ GROUPS, CHUNK, BLOCK = 4, 128, 32
 
 
 def _fma32(a, b, c):
-    """fl32(a * b + c): the product of two binary32 numbers is exact in binary64."""
-    return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
+    """fl32(a * b + c) rounded once, as a fused multiply-add does.
+
+    The product of two binary32 numbers is exact in binary64; the binary64 sum
+    s = fl64(p + c) carries an error e (p + c = s + e exactly, TwoSum).  Since
+    |e| is below half a binary64 unit of s, rounding s to binary32 gives the
+    correctly rounded p + c except when s lies exactly halfway between two
+    binary32 numbers: then the sign of e decides (rounding s alone would
+    round twice)."""
+    p = a.astype(np.float64) * b.astype(np.float64)
+    c64 = c.astype(np.float64)
+    s = p + c64
+    z = s - p
+    e = (p - (s - z)) + (c64 - z)
+    r = s.astype(np.float32)
+    r64 = r.astype(np.float64)
+    up = np.nextafter(r, np.float32(np.inf))
+    dn = np.nextafter(r, np.float32(-np.inf))
+    # s halfway between r and a neighbour (nearest-even chose r): the exact
+    # value lies on e's side of the midpoint, so it rounds to the neighbour
+    # when e points away from r
+    tie_up = (s > r64) & (s - r64 == up.astype(np.float64) - s) & (e > 0)
+    tie_dn = (s < r64) & (r64 - s == s - dn.astype(np.float64)) & (e < 0)
+    return np.where(tie_up, up, np.where(tie_dn, dn, r))
 
 
 def _kahan(s, c, x):
@@ -87,3 +108,18 @@ def test_plain_running_sum_would_not():
     want = _exact(A, t)[0]
     assert abs(float(s) - want) / want > 40 * U
     assert abs(float(kernel_order(A, t)[0]) - want) / want <= 40 * U
+
+
+def test_fma_emulation_rounds_once():
+    """A case where rounding a*b + c first to binary64 and then to binary32
+    lands on the wrong neighbour: a*b = 2^-4 - 2^-40 exactly, c = 2^20 + 2^-3;
+    the binary64 sum is the binary32 midpoint 2^20 + 2^-3 + 2^-4, the exact
+    value lies just below it, so a fused multiply-add gives 2^20 + 2^-3."""
+    a = np.array([(1 + 2.0 ** -18) * 0.25], np.float32)
+    b = np.array([(1 - 2.0 ** -18) * 0.25], np.float32)
+    c = np.array([2.0 ** 20 + 2.0 ** -3], np.float32)
+    assert float(a[0]) * float(b[0]) == 2.0 ** -4 - 2.0 ** -40
+    twice = (a.astype(np.float64) * b + c.astype(np.float64)).astype(np.float32)
+    assert twice[0] == np.float32(2.0 ** 20 + 2.0 ** -2)
+    assert _fma32(a, b, c)[0] == c[0]
+    assert _fma32(-a, b, -c)[0] == -c[0]
