@@ -23,7 +23,6 @@
 //               the edge functions evaluated without contraction, and a
 //               conservatively widened slab test for the boxes.
 #include <algorithm>
-#include <atomic>
 #include <cmath>
 #include <mutex>
 
@@ -271,12 +270,47 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
 
-// Device address of g_noalloc_scratch per device ordinal, resolved once per
-// device (the host-side name of the array is only a stand-in, not a device
-// address).
+// Device address of g_noalloc_scratch, resolved once per device and context
+// (the host-side name of the array is only a stand-in, not a device address).
+// The address belongs to the context the module was loaded into: after a
+// cudaDeviceReset a later call runs in a new context, where the module is
+// loaded again and the array may sit elsewhere, so the cached address is keyed
+// on the context's unique id as well as on the device ordinal.
 constexpr int kMaxDevices = 64;
-std::atomic<float*> g_noalloc_ptr[kMaxDevices];
+struct NoallocSlot {
+    unsigned long long ctx_id = 0;
+    float* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slot[kMaxDevices];
 std::mutex g_noalloc_mutex;
+
+// Unique id of the calling thread's current context (cuCtxGetCurrent,
+// cuCtxGetId through the runtime's driver entry points, so that the library
+// does not link the driver library itself); 0 when there is no current
+// context yet or the driver lacks the calls.
+typedef int (*CtxGetCurrentFn)(void** ctx);
+typedef int (*CtxGetIdFn)(void* ctx, unsigned long long* id);
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    void* ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+    return id;
+}
 
 int noalloc_scratch(float** out) {
     int dev = 0;
@@ -284,22 +318,21 @@ int noalloc_scratch(float** out) {
         cudaGetLastError();
         return UVC_E_CUDA;
     }
-    float* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
-    if (!p) {
-        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
-        if (!p) {
-            void* addr = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
-            if (e != cudaSuccess || !addr) {
-                cudaGetLastError();
-                return UVC_E_CUDA;
-            }
-            p = static_cast<float*>(addr);
-            g_noalloc_ptr[dev].store(p, std::memory_order_release);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocSlot& slot = g_noalloc_slot[dev];
+    unsigned long long ctx = current_context_id();
+    if (!slot.ptr || ctx == 0 || ctx != slot.ctx_id) {
+        void* addr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+        if (e != cudaSuccess || !addr) {
+            cudaGetLastError();
+            return UVC_E_CUDA;
         }
+        if (ctx == 0) ctx = current_context_id();   // the lookup made the primary context current
+        slot.ptr = static_cast<float*>(addr);
+        slot.ctx_id = ctx;
     }
-    *out = p;
+    *out = slot.ptr;
     return UVC_OK;
 }
 

@@ -125,3 +125,81 @@ def test_batch_path_modes_match_single_calls(which):
     _check(jobs, ref)
     b.free()
     sc.free()
+
+
+def _oracle_jobs():
+    """Uneven rooms (12,346 to 190,386 triangles, 5,899 to 12,526 patches)
+    crossed with the robot-design sweep: lamp-bottom heights 0.3-1.1 m x line
+    lamps of K = 4, 8, 12 sources, an uneven number of candidates per job."""
+    from synth.batched import designs
+    rooms = [batched_room(103), batched_room(106), batched_room(113)]
+    scenes = [build(r) for r in rooms]
+    sweep = designs()
+    lamps_g = [line_lamp(L, K, 120.0) for (_, L, K) in sweep]
+    jobs, host = [], []
+    for r, (room, sc) in enumerate(zip(rooms, scenes)):
+        ds = range(len(sweep)) if r != 1 else (0, 5, 10)        # the 190k-triangle room: three designs
+        for d in ds:
+            h, L, K = sweep[d]
+            cand = design_candidates(room, h, L, 9 + 5 * d + 3 * r, seed=1000 + 16 * r + d)
+            A = torch.full((cand.shape[0], sc.np), -1.0, device="cuda")
+            vis = torch.zeros((K, cand.shape[0], (sc.np + 31) // 32), dtype=torch.int32, device="cuda")
+            jobs.append((sc, T(cand), d, A, vis))
+            host.append((room, cand, d))
+    return rooms, scenes, lamps_g, jobs, host
+
+
+def _check_against_oracle(jobs, host, lamps_g, cache):
+    """Every job's whole matrix against the oracle's CPU-BVH mode (the same
+    entries as its brute force, computed once per job into `cache`); pairs
+    whose visibility differs get the brute force's grazing flags."""
+    import oracle
+    from tests._compare import compare_irradiance
+    torch.cuda.synchronize()
+    excused = 0
+    for q, ((sc, _, d, A, vis), (room, cand, _)) in enumerate(zip(jobs, host)):
+        L = lamps_g[d]
+        if q not in cache:
+            cache[q] = oracle.irradiance(room.verts, room.tris, room.centroid, room.normal, room.excl, cand,
+                                         L.offsets, L.weights, L.power, bvh=True, flags=False)[:2]
+        E, ovis = cache[q]
+        visg = uvc.vis_to_bool(vis, sc.np)
+        flag = np.zeros(E.shape, np.uint8)
+        diff = np.argwhere((visg != ovis.astype(bool)).any(axis=-1))
+        if diff.size:
+            _, _, f = oracle.irradiance(room.verts, room.tris, room.centroid, room.normal, room.excl, cand,
+                                        L.offsets, L.weights, L.power, pairs=diff)
+            flag[diff[:, 0], diff[:, 1]] = f
+        st = compare_irradiance(A.cpu().numpy(), visg, E, ovis, flag)
+        excused += st["excused_bits"]
+        assert torch.all(torch.isfinite(A))
+    return excused
+
+
+def test_batch_of_uneven_rooms_and_designs_against_oracle():
+    """One persistent launch over 27 (room, design) jobs of uneven size, and
+    the same launch replayed from a captured CUDA graph, both against the
+    FP64 oracle: visibility bit-exact except on grazing pairs (within the
+    cap of each job), entries within 1e-5."""
+    rooms, scenes, lamps_g, jobs, host = _oracle_jobs()
+    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for L in lamps_g]
+    b = uvc.Batch(jobs, lamps)
+    b.autotune(0.2)
+    b.launch()
+    cache = {}
+    _check_against_oracle(jobs, host, lamps_g, cache)
+    for sc in scenes:
+        assert uvc.scene_status(sc) == 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        b.launch()
+    for _, _, _, A, vis in jobs:
+        A.fill_(-1.0)
+        vis.zero_()
+    g.replay()
+    _check_against_oracle(jobs, host, lamps_g, cache)
+    for sc in scenes:
+        assert uvc.scene_status(sc) == 0
+    b.free()
+    for sc in scenes:
+        sc.free()

@@ -2,6 +2,9 @@
 full matrices on small scenes (several warp tiles plus a ragged tail), sampled
 entries on the full-size ward workload in the benchmark's launch
 configuration, and the degenerate cases."""
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -135,31 +138,42 @@ def test_ward_full_rows_against_bvh_oracle():
 def test_ward_full_matrix_against_bvh_oracle():
     """The whole full-size ward matrix (2,000 x 102,030 pairs, K = 8: 1.6 G
     source bits) against the oracle's CPU-BVH mode, block by block of 125
-    candidates; pairs whose visibility differs get the brute force's grazing
-    flags.  Each block meets the parity bar on its own (at most
-    floor(1e-6 pairs K) excused bits per block)."""
+    candidates, with the grazing flags of every pair (the hierarchy's flag
+    search gives the brute force's bits).  Each block meets the parity bar on
+    its own (at most floor(1e-6 pairs K) excused bits per block); the number
+    of flagged pairs over the whole matrix is counted (and, when
+    UVC_PARITY_REPORT names a file, appended to it as one JSON line)."""
     s = ward_room()
     sc = build(s)
     A, vis = uvc.irradiance_matrix(sc, T(s.cand), lamp_of(s.lamp), with_vis=True)
     torch.cuda.synchronize()
     assert uvc.scene_status(sc) == 0
     Ah = A.cpu().numpy()
-    excused = flagged = 0
+    excused = flagged = mismatched = 0
     for r0 in range(0, s.nc, 125):
         rows = np.arange(r0, min(s.nc, r0 + 125), dtype=np.int64)
         pairs = np.stack([np.repeat(rows, s.np_), np.tile(np.arange(s.np_), rows.size)], axis=1)
-        E, ovis, _ = oracle.irradiance_scene(s, pairs=pairs, bvh=True, flags=False)
+        E, ovis, flag = oracle.irradiance_scene(s, pairs=pairs, bvh=True, flags=True)
         visg = uvc.vis_to_bool(vis[:, r0:r0 + rows.size].contiguous(), s.np_).reshape(-1, s.lamp.K)
-        flag = np.zeros(pairs.shape[0], np.uint8)
-        diff = np.flatnonzero((visg != ovis.astype(bool)).any(axis=1))
-        if diff.size:
-            _, _, f = oracle.irradiance_scene(s, pairs=pairs[diff])
-            flag[diff] = f
         st = compare_irradiance(Ah[rows].reshape(-1), visg, E, ovis, flag)
         excused += st["excused_bits"]
-        flagged += int(diff.size)
-    assert excused <= 1e-6 * s.nc * s.np_ * s.lamp.K
+        flagged += st["flagged"]
+        mismatched += int((visg != ovis.astype(bool)).any(axis=1).sum())
+    pairs_total = s.nc * s.np_
+    assert excused <= 1e-6 * pairs_total * s.lamp.K
+    assert flagged < 1e-2 * pairs_total
+    _report("ward_full_matrix", pairs=pairs_total, source_bits=pairs_total * s.lamp.K, flagged_pairs=flagged,
+            mismatched_pairs=mismatched, excused_bits=excused, cap_bits=int(1e-6 * pairs_total * s.lamp.K))
     sc.free()
+
+
+def _report(name, **stats):
+    """Append the statistics of a parity run to the file UVC_PARITY_REPORT
+    names (nothing when it is unset)."""
+    path = os.environ.get("UVC_PARITY_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps({"test": name, **stats}) + "\n")
 
 
 def test_lda_larger_than_np_leaves_padding_untouched():

@@ -4,10 +4,7 @@ would on a tree too deep for the stack or on a search that does not end.  The
 call must return normally, the status word must name the limit
 (UVC_E_STACK / UVC_E_TIMEOUT) and be cleared by reading it, the stopped
 entries must be NaN, every other entry and visibility bit must be the
-unlimited run's, and restoring the limits must restore the result exactly.
-
-This file is collected last, so that a run stopping at the first failure has
-run every other test first."""
+unlimited run's, and restoring the limits must restore the result exactly."""
 import numpy as np
 import pytest
 import torch

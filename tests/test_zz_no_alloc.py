@@ -43,6 +43,30 @@ def test_noalloc_matches_streamed_on_two_calls_in_a_row():
     sc.free()
 
 
+@pytest.mark.parametrize("nvec", [100, 60])
+def test_noalloc_with_few_chunks_and_a_line_lamp(nvec):
+    """The ward's 102,030 patches with 100 dwell vectors (40.8 MB of partial
+    sums per chunk: the fixed scratch holds one chunk) and 60 (24.5 MB: two
+    chunks), 64 candidates and the K = 8 vertical line lamp (the wedge
+    search): fewer, longer chunks than uvc_fluence_streamed picks, so another
+    summation order, still within the fluence tolerance, on two calls in a
+    row."""
+    from synth import ward_room
+    s = ward_room()
+    sc = build(s)
+    rows = np.linspace(0, s.nc - 1, 64).astype(np.int64)
+    cand, lamp = T(s.cand[rows]), lamp_of(s.lamp)
+    assert 32 * 2 ** 20 < 4 * 100 * s.np_ <= 64 * 2 ** 20 and 4 * 60 * s.np_ <= 32 * 2 ** 20
+    for seed in (31, 32):
+        t = T(dwell_vectors(nvec, rows.size, seed=seed))
+        want = uvc.fluence_streamed(sc, cand, lamp, t).cpu().numpy()
+        mu = torch.full((nvec, s.np_), float("nan"), device="cuda")
+        got = uvc.fluence_streamed_noalloc(sc, cand, lamp, t, mu).cpu().numpy()
+        assert uvc.scene_status(sc) == 0
+        assert _rel(got, want) <= MU_TOL, (nvec, seed)
+    sc.free()
+
+
 def test_noalloc_rejects_problems_beyond_its_scratch():
     s = tiny_room(n_cand=4)
     sc = build(s)
