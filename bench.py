@@ -184,6 +184,60 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def lamp_is_vertical(off) -> bool:
+    off = np.asarray(off)
+    return off.shape[0] >= 2 and bool(np.all(off[:, :2] == 0))
+
+
+def l2_read_peak(uvc, nbytes=32 * 2 ** 20, passes=40, reps=10) -> dict:
+    """The L2 read bandwidth of this GPU: uvc_probe_l2_read over a 32 MiB
+    buffer (well inside the 129 MB L2) read 40 times per launch with L2-only
+    16-byte loads; after one warm-up launch, the best of 10 launches timed with
+    CUDA events on the launching stream."""
+    import torch
+    buf = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda")
+    sink = torch.zeros(4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    uvc.probe_l2_read(buf, passes, sink)
+    best = float("inf")
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        uvc.probe_l2_read(buf, passes, sink)
+        b.record(stream)
+        b.synchronize()
+        best = min(best, a.elapsed_time(b) * 1e-3)
+    return {"gbs": nbytes * passes / best / 1e9, "buffer_bytes": nbytes, "passes": passes,
+            "method": "uvc_probe_l2_read: 32 MiB resident buffer, 40 passes of ld.global.cg 16-byte loads per "
+                      "launch, 4 x 512 threads per SM, best of 10 launches (CUDA events)"}
+
+
+def memory_roofline(uvc, sc, s, irr_s, pairs, pk, ntask=3000, seed=11) -> dict:
+    """Bytes per pair of the wedge traversal from the counting replay
+    (replay/, the same hierarchy and visit order on the CPU, over a seeded
+    sample of warp tasks) against the measured L2 and HBM read bandwidths."""
+    import replay
+    ex = uvc.scene_export_traversal(sc)
+    tasks = replay.sample_tasks(s.nc, s.np_, ntask, seed)
+    c = replay.replay(ex, s.cand, s.lamp.offsets, tasks)
+    bpp = replay.bytes_per_pair(c, s.lamp.K)
+    l2 = l2_read_peak(uvc)
+    hbm = float(pk.get("hbm_gbs", 6800.0))
+    ach_w = bpp["per_warp"] * pairs / irr_s / 1e9
+    ach_l = bpp["per_lane"] * pairs / irr_s / 1e9
+    return {"bytes_per_pair": {"per_warp": round(bpp["per_warp"], 2), "per_lane": round(bpp["per_lane"], 2),
+                               "output": bpp["output"]},
+            "achieved_GBs": round(ach_w, 1), "achieved_GBs_per_lane": round(ach_l, 1),
+            "peak_l2_GBs": round(l2["gbs"], 1), "peak_hbm_GBs": round(hbm, 1),
+            "frac_l2": round(ach_w / l2["gbs"], 4), "frac_hbm": round(ach_w / hbm, 4),
+            "frac_l2_per_lane": round(ach_l / l2["gbs"], 4),
+            "peak_l2_method": l2["method"],
+            "peak_hbm_source": "hbm_gbs of MEASURED_PEAKS.json (copy kernel)" if "hbm_gbs" in pk else "fallback",
+            "leaf_step_lane_occupancy": round(bpp["leaf_step_lane_occupancy"], 3),
+            "sample": f"{tasks.shape[0]} seeded warp tasks (32 patches x 4 candidates) replayed on the CPU, "
+                      f"{c['pairs']} pairs"}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -333,6 +387,8 @@ def run_ours(args):
                 "traffic": traffic, "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
                 "ops_per_launch": ops, "launch_ms": round(irr_s * 1e3, 3),
                 "counters": cnt}
+        if lamp_is_vertical(s.lamp.offsets):
+            roof["memory"] = memory_roofline(uvc, sc, s, irr_s, pairs, pk)
     sc.free()
 
     out = {

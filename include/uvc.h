@@ -558,6 +558,44 @@ int uvc_scene_set_limits(uvc_scene* scene, int32_t max_stack, int32_t max_visits
 int uvc_scene_info(const uvc_scene* scene, int64_t* nt, int64_t* np, int32_t* depth);
 
 /*
+ * uvc_probe_l2_read - bandwidth probe (not in the paper): read the device
+ * buffer `buf` (`bytes` bytes, 16-byte aligned, a multiple of 16) `passes`
+ * times with 16-byte loads that are cached in L2 only (ld.global.cg), from 4
+ * blocks of 512 threads per SM, and write nothing unless the XOR of all words
+ * hits one magic value (then one word to `sink`, a device pointer).  Timed by
+ * the caller (CUDA events around the call) on a buffer that fits in L2, it
+ * gives the L2 read bandwidth that the traversal's bytes are compared with.
+ * Asynchronous on `stream`.  Errors: UVC_E_INVAL (NULL pointers, size or
+ * alignment, passes < 1), UVC_E_CUDA.
+ */
+int uvc_probe_l2_read(const void* buf, size_t bytes, int32_t passes, uint32_t* sink, uvc_stream_t stream);
+
+/*
+ * uvc_scene_export_traversal - copy the arrays the traversal kernels read to
+ * HOST buffers, as they lie in device memory (synchronises the scene's build
+ * stream), for inspection and for counting tools that replay the kernels'
+ * visit order on the CPU.  Not in the paper.  Any pointer may be NULL.
+ *   nodes4     (nt-1) x 128 bytes: the four-wide nodes (valid at the indices
+ *              the traversal reaches from the root), each
+ *              float q[6][4] (per child pair the x, y, z records
+ *              (c0.lo, c1.lo, c0.hi, c1.hi)), int32 r[4] (child refs: >= 0
+ *              node, < 0 leaf ~k, 0x7fffffff empty), int32 m[4] (leaf mask,
+ *              node mask, 0, 0)
+ *   tri        float[nt][3][4]: vertices (x, y, z, w) in sorted order, w of
+ *              the first vertex the triangle's input index (int32 bits)
+ *   patch_s    float[np][4]: sample point and area
+ *   patch_n    float[np][4]: normal and clearance (metres)
+ *   patch_excl int32[np][2]: excluded triangles (input indices, -1 = none)
+ *   root       the root reference (0, or ~0 for a single triangle)
+ *   diameter   diagonal of the triangles' bounding box
+ *   coord_bound largest coordinate magnitude of that box
+ * Errors: UVC_E_INVAL (NULL scene), UVC_E_CUDA.
+ */
+int uvc_scene_export_traversal(const uvc_scene* scene, void* nodes4, float* tri, float* patch_s, float* patch_n,
+                               int32_t* patch_excl, int32_t* root, float* diameter,
+                               float* coord_bound);
+
+/*
  * uvc_scene_export_bvh - copy the hierarchy to HOST buffers for inspection
  * and testing (synchronises the scene's build stream).  Any pointer may be
  * NULL to skip that array.  For nt >= 2 there are nt-1 internal nodes:

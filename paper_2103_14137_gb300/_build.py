@@ -8,7 +8,7 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libuvc.so")
-SOURCES = ["build_bvh.cu", "irradiance.cu", "batch.cu", "fluence.cu", "solid_angle.cu", "raster.cu", "features.cu", "mlp.cu", "api.cu"]
+SOURCES = ["build_bvh.cu", "irradiance.cu", "batch.cu", "fluence.cu", "solid_angle.cu", "raster.cu", "features.cu", "mlp.cu", "probe.cu", "api.cu"]
 HEADERS = ["uvc_internal.cuh", "traverse.cuh"]
 INCLUDE = os.path.join(HERE, "..", "include")
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

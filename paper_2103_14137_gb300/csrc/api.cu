@@ -292,6 +292,33 @@ int uvc_scene_info(const uvc_scene* scene, int64_t* nt, int64_t* np, int32_t* de
     return UVC_OK;
 }
 
+int uvc_probe_l2_read(const void* buf, size_t bytes, int32_t passes, uint32_t* sink, uvc_stream_t stream) {
+    if (!buf || !sink || bytes < 16 || bytes % 16 != 0 || reinterpret_cast<uintptr_t>(buf) % 16 != 0 || passes < 1)
+        return UVC_E_INVAL;
+    return uvc::probe_l2_read(buf, bytes, passes, sink, (cudaStream_t)stream);
+}
+
+int uvc_scene_export_traversal(const uvc_scene* scene, void* nodes4, float* tri, float* patch_s, float* patch_n,
+                               int32_t* patch_excl, int32_t* root, float* diameter,
+                               float* coord_bound) {
+    if (!scene) return UVC_E_INVAL;
+    const int64_t n = scene->nt, ni = n > 1 ? n - 1 : 0, np = scene->np;
+    cudaError_t e = cudaStreamSynchronize(scene->build_stream);
+    if (e == cudaSuccess && nodes4 && ni)
+        e = cudaMemcpy(nodes4, scene->nodes4, sizeof(uvc::Node4) * ni, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && tri && n) e = cudaMemcpy(tri, scene->tri, sizeof(float4) * 3 * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && patch_s && np)
+        e = cudaMemcpy(patch_s, scene->patch_s, sizeof(float4) * np, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && patch_n && np)
+        e = cudaMemcpy(patch_n, scene->patch_n, sizeof(float4) * np, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && patch_excl && np)
+        e = cudaMemcpy(patch_excl, scene->patch_excl, sizeof(int2) * np, cudaMemcpyDeviceToHost);
+    if (root) *root = scene->root;
+    if (diameter) *diameter = scene->diameter;
+    if (coord_bound) *coord_bound = scene->coord_bound;
+    return uvc::status_from_cuda(e);
+}
+
 int uvc_scene_export_bvh(const uvc_scene* scene, uint64_t* keys, int32_t* order, int32_t* children, float* boxes) {
     if (!scene) return UVC_E_INVAL;
     const int64_t n = scene->nt, ni = n > 1 ? n - 1 : 0;

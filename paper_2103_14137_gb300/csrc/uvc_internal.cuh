@@ -126,6 +126,9 @@ int coverage(const uvc_scene* sc, const float* mu, int32_t nvec, float mu_min, f
              float* cov_count, cudaStream_t stream);
 void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream_t stream);
 
+// bandwidth probe (probe.cu)
+int probe_l2_read(const void* buf, size_t bytes, int32_t passes, uint32_t* sink, cudaStream_t stream);
+
 // learned-proposal features (features.cu)
 int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, int64_t ldf,
                        cudaStream_t stream);

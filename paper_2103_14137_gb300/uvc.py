@@ -77,6 +77,9 @@ def library():
         "uvc_scene_info": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32)],
         "uvc_scene_set_limits": [P, i32, i32],
         "uvc_scene_export_bvh": [P, P, P, P, P],
+        "uvc_probe_l2_read": [P, ctypes.c_size_t, i32, P, P],
+        "uvc_scene_export_traversal": [P, P, P, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_float)],
     }
     sig.update({
         "uvc_batch_create": [ctypes.POINTER(_Job), i32, ctypes.POINTER(_Lamp), i32, P, ctypes.c_size_t, P,
@@ -627,6 +630,35 @@ def scene_export_bvh(scene: Scene) -> dict:
     _check(library().uvc_scene_export_bvh(scene.handle, ptr(keys), ptr(order), ptr(children), ptr(boxes)),
            "uvc_scene_export_bvh")
     return dict(keys=keys, order=order, children=children, boxes=boxes)
+
+
+def probe_l2_read(buf: torch.Tensor, passes: int, sink: torch.Tensor, stream=None):
+    """uvc_probe_l2_read over the bytes of `buf` (a contiguous CUDA tensor);
+    `sink` a CUDA tensor of at least one 32-bit word."""
+    if not buf.is_contiguous():
+        raise ValueError("buf must be contiguous")
+    nbytes = buf.numel() * buf.element_size() // 16 * 16
+    _check(library().uvc_probe_l2_read(_scratch(buf, nbytes, "buf"), nbytes, int(passes),
+                                       _scratch(sink, 4, "sink"), _stream(stream)), "uvc_probe_l2_read")
+
+
+def scene_export_traversal(scene: Scene) -> dict:
+    """Host copies of what the traversal kernels read (uvc_scene_export_traversal):
+    nodes4 (nt-1, 32) as raw 32-bit words, tri (nt, 3, 4) float32, patch_s and
+    patch_n (np, 4) float32, patch_excl (np, 2) int32, root, diameter, coord_bound."""
+    n, np_ = scene.nt, scene.np
+    nodes4 = np.zeros((max(n - 1, 0), 32), np.uint32)
+    tri = np.zeros((n, 3, 4), np.float32)
+    ps = np.zeros((np_, 4), np.float32)
+    pn = np.zeros((np_, 4), np.float32)
+    pe = np.zeros((np_, 2), np.int32)
+    root, diam, cb = ctypes.c_int32(), ctypes.c_float(), ctypes.c_float()
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a.size else None  # noqa: E731
+    _check(library().uvc_scene_export_traversal(scene.handle, ptr(nodes4), ptr(tri), ptr(ps), ptr(pn), ptr(pe),
+                                                ctypes.byref(root), ctypes.byref(diam), ctypes.byref(cb)),
+           "uvc_scene_export_traversal")
+    return dict(nodes4=nodes4, tri=tri, patch_s=ps, patch_n=pn, patch_excl=pe, root=root.value,
+                diameter=diam.value, coord_bound=cb.value)
 
 
 class Batch:
