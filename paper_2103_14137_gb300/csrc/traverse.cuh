@@ -507,18 +507,18 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // far above the rounding of the segment test and of this projection.  A
 // triangle reaching lambda >= 1 - 2^-10 (next to s or beyond) keeps every
 // source, as does a degenerate g (NaN comparisons fail).
-__device__ __forceinline__ uint32_t lamp_interval(const WedgeLane& w, uint32_t want, float4 a, float4 b, float4 c,
+__device__ __forceinline__ uint32_t lamp_interval(float ig2, float mz, uint32_t want, float4 a, float4 b, float4 c,
                                                   float cx, float cy, float cz, float sz, float gx, float gy,
                                                   const LampDev& L) {
-    const float la = __fmul_rn(__fmaf_rn(__fsub_rn(a.x, cx), gx, __fmul_rn(__fsub_rn(a.y, cy), gy)), w.ig2);
-    const float lb = __fmul_rn(__fmaf_rn(__fsub_rn(b.x, cx), gx, __fmul_rn(__fsub_rn(b.y, cy), gy)), w.ig2);
-    const float lc = __fmul_rn(__fmaf_rn(__fsub_rn(c.x, cx), gx, __fmul_rn(__fsub_rn(c.y, cy), gy)), w.ig2);
+    const float la = __fmul_rn(__fmaf_rn(__fsub_rn(a.x, cx), gx, __fmul_rn(__fsub_rn(a.y, cy), gy)), ig2);
+    const float lb = __fmul_rn(__fmaf_rn(__fsub_rn(b.x, cx), gx, __fmul_rn(__fsub_rn(b.y, cy), gy)), ig2);
+    const float lc = __fmul_rn(__fmaf_rn(__fsub_rn(c.x, cx), gx, __fmul_rn(__fsub_rn(c.y, cy), gy)), ig2);
     const float lmax = max3f(la, lb, lc);
     if (!(lmax < 0.9990234375f)) return want;
     const float za = __fmaf_rn(__fsub_rn(a.z, sz), rcp_approx(__fsub_rn(1.f, la)), sz);
     const float zb = __fmaf_rn(__fsub_rn(b.z, sz), rcp_approx(__fsub_rn(1.f, lb)), sz);
     const float zc = __fmaf_rn(__fsub_rn(c.z, sz), rcp_approx(__fsub_rn(1.f, lc)), sz);
-    const float m = __fmul_rn(w.mz, rcp_approx(__fsub_rn(1.f, lmax)));
+    const float m = __fmul_rn(mz, rcp_approx(__fsub_rn(1.f, lmax)));
     const float z0 = __fsub_rn(min3f(za, zb, zc), m), z1 = __fadd_rn(max3f(za, zb, zc), m);
     if (L.wuniform) {
         // source q sits at fl32(cz + off_q), off_q within dz/64 of wz0 + q dz:
@@ -552,10 +552,27 @@ __device__ __forceinline__ void wedge_pair_hits(const WedgeLane& w, float2 nx, f
 
 // Per (source, lane) data of the wedge path, in shared memory (one warp's
 // slice): shear constants and axis permutation of the source's segment, and
-// its Eq. (7) term w_m P <n, v> / (4 pi |v|^3).
+// its Eq. (7) term w_m P <n, v> / (4 pi |v|^3); and the warp's queue of leaf
+// tests (see wedge_traverse): a ring of (leaf, lane) items, and per lane the
+// sources found occluded by the last batch and the leaf that did it.
+// The queue is worked off, up to 32 items at a time, once kLeafFlush items
+// wait (a tuning constant: fewer waiting items stop lanes sooner, more keep
+// the batches fuller; on the ward 16: 76.7, 24: 75.9, 32: 77.1, 48: 80.4 ms
+// per matrix).
+#ifndef UVC_LEAF_FLUSH
+#define UVC_LEAF_FLUSH 24
+#endif
+constexpr int kLeafQueue = 256;       // ring entries per warp (a node adds at most 4 x 32)
+constexpr int kLeafBatch = 32;        // items per batch: one per lane
+constexpr int kLeafFlush = UVC_LEAF_FLUSH;
+constexpr uint32_t kOobBit = 0x80000000u;   // checked build: a leaf index out of range (sources use bits 0..15)
 struct WedgeSmem {
-    float4* shear;   // [K][32]: (sx, sy, sz, kx | ky << 2 | kz << 4)
-    float* term;     // [K][32]
+    float4* shear;            // [K][32]: (sx, sy, sz, kx | ky << 2 | kz << 4)
+    float* term;              // [K][32]
+    int* qleaf;               // [kLeafQueue]
+    unsigned char* qlane;     // [kLeafQueue]
+    uint32_t* occ;            // [32]
+    int* qhit;                // [32]
 };
 
 // Shared memory of a block of the traversal kernels: the warps' stacks
@@ -564,27 +581,132 @@ struct WedgeSmem {
 __host__ __device__ inline size_t stack_smem_bytes(int stack_cap) {
     return ((size_t)kWarpsPerBlock * stack_cap * sizeof(int) + 15) & ~size_t(15);
 }
-inline size_t wedge_smem_bytes(int K) { return (size_t)kWarpsPerBlock * K * 32 * (sizeof(float4) + sizeof(float)); }
+constexpr size_t kWedgeQueueBytes = kLeafQueue * (sizeof(int) + 1) + 32 * (sizeof(uint32_t) + sizeof(int));
+inline size_t wedge_smem_bytes(int K) {
+    return (size_t)kWarpsPerBlock * (K * 32 * (sizeof(float4) + sizeof(float)) + kWedgeQueueBytes);
+}
 
 __device__ __forceinline__ WedgeSmem wedge_smem(char* base, int K, int warp) {
     WedgeSmem w;
+    const size_t per_src = (size_t)kWarpsPerBlock * K * 32;
     w.shear = reinterpret_cast<float4*>(base) + (size_t)warp * K * 32;
-    w.term = reinterpret_cast<float*>(base + (size_t)kWarpsPerBlock * K * 32 * sizeof(float4)) + (size_t)warp * K * 32;
+    w.term = reinterpret_cast<float*>(base + per_src * sizeof(float4)) + (size_t)warp * K * 32;
+    char* q = base + per_src * (sizeof(float4) + sizeof(float));   // 4-byte aligned
+    w.qleaf = reinterpret_cast<int*>(q) + (size_t)warp * kLeafQueue;
+    q += (size_t)kWarpsPerBlock * kLeafQueue * sizeof(int);
+    w.occ = reinterpret_cast<uint32_t*>(q) + (size_t)warp * 32;
+    q += (size_t)kWarpsPerBlock * 32 * sizeof(uint32_t);
+    w.qhit = reinterpret_cast<int*>(q) + (size_t)warp * 32;
+    q += (size_t)kWarpsPerBlock * 32 * sizeof(int);
+    w.qlane = reinterpret_cast<unsigned char*>(q) + (size_t)warp * kLeafQueue;
     return w;
+}
+
+// One batch of queued leaf tests: lane k of the warp takes item head + k
+// (k < n), a leaf wanted by some lane `own` of the warp, and tests it with
+// own's wedge (the plane and lamp-height filters) and own's searching
+// sources (the watertight segment test with own's shear constants), as own
+// would have done itself; the sources found occluded are OR-ed into own's
+// word, which own folds into `want` after the batch (narrowing its wedge).
+// Items whose lane has stopped are skipped.  Every lane of the warp calls it.
+template <bool COUNT>
+__device__ __forceinline__ void wedge_leaf_batch(const SceneView& S, const LampDev& L, WedgeLane& w, uint32_t& want,
+                                                 int lane, const WedgeSmem& ws, int head, int n, float cx, float cy,
+                                                 float cz, float sz, float gx, float gy, float mh, int ex0, int ex1,
+                                                 unsigned& c_leaf, unsigned& c_tri, int& hit_tri, bool& oob) {
+    const bool has = lane < n;
+    const int slot = (head + lane) & (kLeafQueue - 1);
+    const int own = has ? (int)ws.qlane[slot] : lane;
+    const int leaf = has ? ws.qleaf[slot] : 0;
+    const uint32_t owant = __shfl_sync(kFull, want, own);
+    const float osz = __shfl_sync(kFull, sz, own);
+    const float ogx = __shfl_sync(kFull, gx, own);
+    const float ogy = __shfl_sync(kFull, gy, own);
+    const float omh = __shfl_sync(kFull, mh, own);
+    const float oig2 = __shfl_sync(kFull, w.ig2, own);
+    const float omz = __shfl_sync(kFull, w.mz, own);
+    const int oex0 = __shfl_sync(kFull, ex0, own);
+    const int oex1 = __shfl_sync(kFull, ex1, own);
+    if (has && owant) {
+        uint32_t occl = 0;
+        if (out_of_range(S.status, leaf, S.nt)) {
+            occl = kOobBit;
+        } else {
+            const float4* t = S.tri + 3 * (size_t)leaf;
+            const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
+            const int id = __float_as_int(ta.w);
+            if (COUNT) ++c_leaf;
+            if (id != oex0 && id != oex1) {
+                // triangle entirely on one side of the wedge's vertical plane,
+                // farther than delta: no segment of the lane can meet it
+                const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -ogy, __fmul_rn(__fsub_rn(ta.y, cy), ogx));
+                const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -ogy, __fmul_rn(__fsub_rn(tb.y, cy), ogx));
+                const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -ogy, __fmul_rn(__fsub_rn(tc.y, cy), ogx));
+                const bool beside = (qa > omh && qb > omh && qc > omh) || (qa < -omh && qb < -omh && qc < -omh);
+                if (!beside) {
+                    const uint32_t test = owant & lamp_interval(oig2, omz, owant, ta, tb, tc, cx, cy, cz, osz, ogx,
+                                                                ogy, L);
+                    for (uint32_t bits = test; bits; bits &= bits - 1) {
+                        const int q = __ffs(bits) - 1;
+                        const float4 sh = ws.shear[q * 32 + own];
+                        const int kb = __float_as_int(sh.w);
+                        if (COUNT) ++c_tri;
+                        if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), kb & 3, (kb >> 2) & 3, (kb >> 4) & 3, sh.x,
+                                      sh.y, sh.z, ta, tb, tc))
+                            occl |= 1u << q;
+                    }
+                }
+            }
+        }
+        if (occl) {
+            atomicOr(&ws.occ[own], occl);
+            atomicMax(&ws.qhit[own], leaf);   // the lane caches the highest such leaf (deterministic)
+        }
+    }
+    __syncwarp();
+    const uint32_t o = ws.occ[lane];
+    if (o) {
+        ws.occ[lane] = 0u;
+        if (kChecked && (o & kOobBit)) {
+            oob = true;
+            want = 0u;
+        }
+        const uint32_t nw = want & ~o;
+        if (nw != want) {
+            want = nw;
+            hit_tri = ws.qhit[lane];
+            if (want) wedge_z(w, want, cz, L, sz, S.cut_eps);
+        }
+        ws.qhit[lane] = -1;
+    }
+    __syncwarp();
 }
 
 // Lane-level wedge search.  `want` holds the lane's searching sources and
 // loses the bit of each source found occluded; `hit_tri` gets the last
 // occluding leaf.
+//
+// The leaf children a lane's wedge enters are not tested at once: they go to
+// the warp's queue (shared memory), and whenever 32 items wait the whole warp
+// works off 32 of them, one per lane, whichever lane wanted them.  Lanes want
+// leaves unevenly (a few lanes near dense geometry, the rest none), so testing
+// them where they arise would leave most lanes idle; the queue keeps the leaf
+// tests nearly fully occupied at the price of narrowing a lane's wedge (and
+// stopping it) up to a batch later.  The sources a lane finds occluded are
+// those of its own search: every leaf its wedge enters while a source is
+// still searching is tested against that source.
 template <bool COUNT>
 __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev& L, WedgeLane& w, uint32_t& want,
                                                uint32_t alive, int* stack, int lane, const WedgeSmem& ws, float cx,
                                                float cy, float cz, float sz, float gx, float gy, float mh, int ex0,
                                                int ex1, uint32_t& failed, unsigned long long* ctr, int& hit_tri) {
-    int top = 0, node = 0, visits = 0;
-    unsigned long long c_leaf = 0, c_box = 0, c_tri = 0, c_plane = 0;
-    const float delta = S.cut_eps;
+    int top = 0, node = 0, visits = 0, head = 0, tail = 0;
+    unsigned long long c_box = 0;
+    unsigned c_leaf = 0, c_tri = 0;
     bool oob = false;   // checked build: this lane met an index out of range
+    ws.occ[lane] = 0u;
+    ws.qhit[lane] = -1;
+    __syncwarp();
     while (true) {
         if (++visits > S.visit_cap) {
             failed = alive;
@@ -612,56 +734,32 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
                                                           ((unsigned)h3 << 3)
                                                     : 0u;
         const unsigned hit = __reduce_or_sync(kFull, nib);
-        // leaf children: each lane works through the leaves it wants itself
-        // (the warp iterates as often as the busiest lane, not once per leaf
-        // any lane wants)
-        unsigned mine = ((alive >> lane) & 1u) ? (nib & (unsigned)mm.x) : 0u;
-        while (__any_sync(kFull, mine != 0u)) {
-            if (mine) {
-                const int c = __ffs(mine) - 1;
-                mine &= mine - 1;
-                const int leaf = ~pick4(rr, c);
-                if (out_of_range(S.status, leaf, S.nt)) {
-                    oob = true;
-                    want = 0u;
-                    mine = 0u;
-                    continue;
-                }
-                const float4* t = S.tri + 3 * (size_t)leaf;
-                const float4 ta = __ldg(t), tb = __ldg(t + 1), tc = __ldg(t + 2);
-                const int id = __float_as_int(ta.w);
-                if (COUNT) { ++c_leaf; ++c_plane; }
-                if (id != ex0 && id != ex1) {
-                    // triangle entirely on one side of the wedge's vertical plane,
-                    // farther than delta: no segment of the lane can meet it
-                    const float qa = __fmaf_rn(__fsub_rn(ta.x, cx), -gy, __fmul_rn(__fsub_rn(ta.y, cy), gx));
-                    const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
-                    const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
-                    const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
-                    if (!beside) {
-                        const uint32_t before = want;
-                        const uint32_t test = want & lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
-                        for (uint32_t bits = test; bits; bits &= bits - 1) {
-                            const int q = __ffs(bits) - 1;
-                            const float4 sh = ws.shear[q * 32 + lane];
-                            const int kb = __float_as_int(sh.w);
-                            if (COUNT) ++c_tri;
-                            if (seg_tri_k(cx, cy, __fadd_rn(cz, L.oz[q]), kb & 3, (kb >> 2) & 3, (kb >> 4) & 3, sh.x,
-                                          sh.y, sh.z, ta, tb, tc))
-                                want &= ~(1u << q);
-                        }
-                        if (want != before) {
-                            hit_tri = leaf;
-                            if (want) wedge_z(w, want, cz, L, sz, delta);
-                        }
-                    }
-                }
-                if (!want) mine = 0u;
+        if (hit & (unsigned)mm.x) {
+            // queue the lane's leaf children (prefix sum of the counts, at most 4 each)
+            const unsigned mine = nib & (unsigned)mm.x;
+            const unsigned cnt = __popc(mine), lt = (1u << lane) - 1u;
+            const unsigned b0 = __ballot_sync(kFull, cnt & 1u), b1 = __ballot_sync(kFull, cnt & 2u),
+                           b2 = __ballot_sync(kFull, cnt & 4u);
+            int pos = tail + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
+            tail += __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+            for (unsigned m = mine; m; m &= m - 1) {
+                ws.qleaf[pos & (kLeafQueue - 1)] = ~pick4(rr, __ffs(m) - 1);
+                ws.qlane[pos & (kLeafQueue - 1)] = (unsigned char)lane;
+                ++pos;
+            }
+            __syncwarp();
+            if (tail - head >= kLeafFlush) {
+                do {
+                    const int n = min(kLeafBatch, tail - head);
+                    wedge_leaf_batch<COUNT>(S, L, w, want, lane, ws, head, n, cx, cy, cz, sz, gx, gy, mh, ex0, ex1,
+                                            c_leaf, c_tri, hit_tri, oob);
+                    head += n;
+                } while (tail - head >= kLeafFlush);
+                if (kChecked) failed |= __ballot_sync(kFull, oob);
+                alive &= __ballot_sync(kFull, want != 0u);
+                if (!alive) break;
             }
         }
-        if (kChecked) failed |= __ballot_sync(kFull, oob);
-        alive &= __ballot_sync(kFull, want != 0u);
-        if (!alive) break;
         unsigned inner = hit & (unsigned)mm.y;
         if (inner) {
             const int first = __ffs(inner) - 1;
@@ -680,18 +778,22 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
             node = stack[--top];
         }
     }
+    if (tail > head) {   // the leaves still queued when the traversal ends
+        wedge_leaf_batch<COUNT>(S, L, w, want, lane, ws, head, tail - head, cx, cy, cz, sz, gx, gy, mh, ex0, ex1,
+                                c_leaf, c_tri, hit_tri, oob);
+        if (kChecked) failed |= __ballot_sync(kFull, oob);
+    }
     if (COUNT && lane == 0) {
         atomicAdd(&ctr[0], (unsigned long long)visits);
         atomicAdd(&ctr[2], 1ull);
         atomicAdd(&ctr[6], c_box);
     }
-    if (COUNT) {   // leaf loads, plane tests and triangle tests are per lane
-        const unsigned nleaf = __reduce_add_sync(kFull, (unsigned)c_leaf);
-        const unsigned nplane = __reduce_add_sync(kFull, (unsigned)c_plane);
-        const unsigned ntri = __reduce_add_sync(kFull, (unsigned)c_tri);
+    if (COUNT) {   // leaf loads (each with its plane test) and triangle tests, by the lanes that made them
+        const unsigned nleaf = __reduce_add_sync(kFull, c_leaf);
+        const unsigned ntri = __reduce_add_sync(kFull, c_tri);
         if (lane == 0) {
             atomicAdd(&ctr[1], (unsigned long long)nleaf);
-            atomicAdd(&ctr[7], (unsigned long long)nplane);
+            atomicAdd(&ctr[7], (unsigned long long)nleaf);
             atomicAdd(&ctr[4], (unsigned long long)ntri);
         }
     }
@@ -789,7 +891,7 @@ __device__ __forceinline__ uint32_t wedge_search(const SceneView& S, const LampD
         const float qb = __fmaf_rn(__fsub_rn(tb.x, cx), -gy, __fmul_rn(__fsub_rn(tb.y, cy), gx));
         const float qc = __fmaf_rn(__fsub_rn(tc.x, cx), -gy, __fmul_rn(__fsub_rn(tc.y, cy), gx));
         const bool beside = (qa > mh && qb > mh && qc > mh) || (qa < -mh && qb < -mh && qc < -mh);
-        const uint32_t test = beside ? 0u : lamp_interval(w, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
+        const uint32_t test = beside ? 0u : lamp_interval(w.ig2, w.mz, want, ta, tb, tc, cx, cy, cz, sz, gx, gy, L);
         for (uint32_t bits = test; bits; bits &= bits - 1) {
             const int q = __ffs(bits) - 1;
             const float4 sh = ws.shear[q * 32 + lane];

@@ -24,10 +24,15 @@
  * Work unit (as in the kernels): a task is 32 consecutive patches (one per
  * lane) and a chunk of consecutive candidates; the lanes keep their patch
  * and their last occluder over the chunk.  Per candidate the K sources of
- * the vertical lamp are searched together: a wedge box test per child, a
- * plane test and a lamp-height interval per leaf, and the watertight
- * segment test per remaining source.  The arithmetic follows the kernels
- * operation by operation (binary32, fused multiply-adds where they fuse);
+ * the vertical lamp are searched together: a wedge box test per child; the
+ * leaf children a lane's wedge enters go to the warp's queue in lane order,
+ * and every time 32 items wait the warp works off 32 of them (each with the
+ * wanting lane's sources as they stood when the batch began: a plane test, a
+ * lamp-height interval and the watertight segment test per remaining
+ * source), then each lane drops the sources found occluded and narrows its
+ * wedge; the items left when the traversal ends form a last batch.  The
+ * arithmetic follows the kernels operation by operation (binary32, fused
+ * multiply-adds where they fuse);
  * the approximate reciprocal of the height interval is taken exactly here,
  * so a source lying within rounding of an interval end may be counted
  * differently (the counts are compared with the kernels' own instrumented
@@ -266,6 +271,73 @@ typedef struct {
     wedge_t w;
 } lane_t;
 
+#define QCAP 256
+#define QBATCH 32
+#ifndef QFLUSH
+#define QFLUSH 24   /* the kernels' kLeafFlush */
+#endif
+
+/* one queued leaf test for lane P with its sources `snap`: the sources found
+ * occluded */
+static uint32_t leaf_item(const scene_t* S, const lamp_t* L, const lane_t* P, int leaf, float cx, float cy, float cz,
+                          uint32_t snap, uint64_t* C) {
+    const f4* t = S->tri + 3 * (size_t)leaf;
+    int32_t id;
+    memcpy(&id, &t[0].w, 4);
+    C[C_LEAF_LOADS]++;
+    C[C_PLANE_TESTS]++;
+    uint32_t occl = 0;
+    if (id != P->ex0 && id != P->ex1 && !lane_beside(&t[0], &t[1], &t[2], cx, cy, P->gx, P->gy, P->mh)) {
+        const uint32_t test = snap & lamp_interval(&P->w, snap, &t[0], &t[1], &t[2], cx, cy, cz, P->s.z, P->gx,
+                                                   P->gy, L);
+        for (uint32_t bits = test; bits; bits &= bits - 1) {
+            const int q = __builtin_ctz(bits);
+            C[C_TRI_TESTS]++;
+            if (seg_tri(cx, cy, cz + L->oz[q], &P->sh[q], &t[0], &t[1], &t[2])) occl |= 1u << q;
+        }
+    }
+    return occl;
+}
+
+/* one batch of n <= 32 queued items from the ring position head */
+static void leaf_batch(const scene_t* S, const lamp_t* L, lane_t* ln, const int* qlane, const int* qleaf, int head,
+                       int n, float cx, float cy, float cz, uint64_t* C) {
+    uint32_t snap[32], occ[32];
+    int hit[32];
+    for (int l = 0; l < 32; ++l) {
+        snap[l] = ln[l].want;
+        occ[l] = 0;
+        hit[l] = -1;
+    }
+    int nl = 0, uniq = 0;
+    int seen_leaf[QBATCH];
+    for (int k = 0; k < n; ++k) {
+        const int slot = (head + k) & (QCAP - 1), own = qlane[slot], leaf = qleaf[slot];
+        if (!snap[own]) continue;   /* the lane has stopped: the item is skipped */
+        int seen = 0;
+        for (int b = 0; b < nl && !seen; ++b) seen = seen_leaf[b] == leaf;
+        seen_leaf[nl++] = leaf;
+        uniq += !seen;
+        const uint32_t o = leaf_item(S, L, &ln[own], leaf, cx, cy, cz, snap[own], C);
+        if (o) {
+            occ[own] |= o;
+            if (leaf > hit[own]) hit[own] = leaf;
+        }
+    }
+    for (int l = 0; l < 32; ++l) {
+        lane_t* P = &ln[l];
+        const uint32_t nw = P->want & ~occ[l];
+        if (nw != P->want) {
+            P->want = nw;
+            P->cache = hit[l];
+            if (P->want) wedge_z(&P->w, P->want, cz, L, P->s.z, S->cut_eps);
+        }
+    }
+    C[C_LEAF_STEPS]++;
+    C[C_LEAF_STEP_LANES] += (uint64_t)nl;
+    C[C_LEAF_STEP_UNIQUE] += (uint64_t)uniq;
+}
+
 /* one candidate (cx, cy, cz) for the 32 lanes of a task */
 static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float cy, float cz, lane_t* ln,
                              uint64_t* C) {
@@ -342,6 +414,7 @@ static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float 
     }
     /* the packet traversal */
     int32_t stack[STACK];
+    int qlane[QCAP], qleaf[QCAP], head = 0, tail = 0;
     int top = 0, node = 0;
     uint64_t visits = 0;
     C[C_TRAVERSALS]++;
@@ -360,57 +433,18 @@ static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float 
             nib[l] = (unsigned)h0 | ((unsigned)h1 << 1) | ((unsigned)h2 << 2) | ((unsigned)h3 << 3);
             hit |= nib[l];
         }
-        unsigned mine[32];
-        int any = 0;
-        for (int l = 0; l < 32; ++l) {
-            mine[l] = ((alive >> l) & 1u) ? (nib[l] & (unsigned)nd->m[0]) : 0u;
-            any |= mine[l] != 0;
-        }
-        while (any) {
-            /* one step of the leaf loop: every lane with a wanted leaf takes its next one */
-            int leaves_now[32], nl = 0;
-            for (int l = 0; l < 32; ++l) {
-                if (!mine[l]) continue;
-                lane_t* P = &ln[l];
-                const int c = __builtin_ctz(mine[l]);
-                mine[l] &= mine[l] - 1;
-                const int leaf = ~nd->r[c];
-                leaves_now[nl++] = leaf;
-                const f4* t = S->tri + 3 * (size_t)leaf;
-                int32_t id;
-                memcpy(&id, &t[0].w, 4);
-                C[C_LEAF_LOADS]++;
-                C[C_PLANE_TESTS]++;
-                if (id != P->ex0 && id != P->ex1 &&
-                    !lane_beside(&t[0], &t[1], &t[2], cx, cy, P->gx, P->gy, P->mh)) {
-                    const uint32_t before = P->want;
-                    const uint32_t test =
-                        P->want & lamp_interval(&P->w, P->want, &t[0], &t[1], &t[2], cx, cy, cz, P->s.z, P->gx,
-                                                P->gy, L);
-                    for (uint32_t bits = test; bits; bits &= bits - 1) {
-                        const int q = __builtin_ctz(bits);
-                        C[C_TRI_TESTS]++;
-                        if (seg_tri(cx, cy, cz + L->oz[q], &P->sh[q], &t[0], &t[1], &t[2])) P->want &= ~(1u << q);
-                    }
-                    if (P->want != before) {
-                        P->cache = leaf;
-                        if (P->want) wedge_z(&P->w, P->want, cz, L, P->s.z, delta);
-                    }
+        if (hit & (unsigned)nd->m[0]) {
+            for (int l = 0; l < 32; ++l)
+                for (unsigned b = nib[l] & (unsigned)nd->m[0]; b; b &= b - 1) {
+                    qlane[tail & (QCAP - 1)] = l;
+                    qleaf[tail & (QCAP - 1)] = ~nd->r[__builtin_ctz(b)];
+                    ++tail;
                 }
-                if (!P->want) mine[l] = 0u;
+            while (tail - head >= QFLUSH) {
+                const int n = tail - head < QBATCH ? tail - head : QBATCH;
+                leaf_batch(S, L, ln, qlane, qleaf, head, n, cx, cy, cz, C);
+                head += n;
             }
-            C[C_LEAF_STEPS]++;
-            C[C_LEAF_STEP_LANES] += (uint64_t)nl;
-            /* distinct triangles loaded in this step */
-            int uniq = 0;
-            for (int a = 0; a < nl; ++a) {
-                int seen = 0;
-                for (int b = 0; b < a && !seen; ++b) seen = leaves_now[b] == leaves_now[a];
-                uniq += !seen;
-            }
-            C[C_LEAF_STEP_UNIQUE] += (uint64_t)uniq;
-            any = 0;
-            for (int l = 0; l < 32; ++l) any |= mine[l] != 0;
         }
         uint32_t still = 0;
         for (int l = 0; l < 32; ++l)
@@ -431,6 +465,7 @@ static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float 
             node = stack[--top];
         }
     }
+    if (tail > head) leaf_batch(S, L, ln, qlane, qleaf, head, tail - head, cx, cy, cz, C);
     C[C_NODE_VISITS] += visits;
 }
 
