@@ -6,7 +6,11 @@ upload/build the scene hierarchy (uvc_build_scene), the occlusion-tested
 irradiance matrix with per-source visibility bits (uvc_irradiance_matrix),
 the fluence A^T t for 16 dwell vectors (uvc_fluence) and the covered-area
 fraction (uvc_coverage).  The metric is occlusion-tested (candidate, patch)
-pairs per second, in Gpairs/s, for the whole job.
+pairs per second, in Gpairs/s, for the whole job.  The same line carries the
+second half of the metric, rooms per second: the plain method, the batched
+engine and the batched + learned proposal timed on 16 seeded rooms of uneven
+size x 12 lamp designs (3 timed steps each), with the proposal's lost
+coverage and added dwell time measured on a seeded subset of the timed jobs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload ward|tiny|large]
@@ -37,6 +41,8 @@ METRIC = "irradiance-matrix Gpairs/s (occlusion-tested) and % roofline; rooms/se
 UNIT = "Gpairs/s"
 MU_MIN = 100.0          # 10 mJ/cm^2
 NVEC = 16
+BL_STEPS = 3            # timed steps of each pipeline in the rooms-per-second block
+BL_QUALITY_JOBS = 8     # timed jobs (seeded subset) whose proposal quality is measured
 L2_BYTES = 129 * 2 ** 20
 # ALU work per operation of the traversal (FP32 arithmetic, min/max, compare
 # and predicate-combining instructions of the kernels, per lane):
@@ -70,6 +76,9 @@ def parse():
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle sample (per step in --impl reference)")
+    p.add_argument("--bl-rooms", type=int, default=16,
+                   help="ward workload: rooms (x 12 designs) of the batched/learned/plain rooms-per-second block "
+                        "(0 = leave it out)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
@@ -407,6 +416,10 @@ def run_ours(args):
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(args, s, host, lamp, streamed, nvec, world, dist if world > 1 else None)
+    if world == 1 and args.workload == "ward" and args.bl_rooms > 0 and not args.candidates:
+        A = vis = None
+        torch.cuda.empty_cache()
+        out["batched_learned"] = batched_learned(uvc, dev, args.bl_rooms, BL_STEPS, args.pool_gb, BL_QUALITY_JOBS)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(s, args.cpu_seconds)
         out["cpu_baseline_bvh"] = cpu_baseline_bvh(s, args.cpu_seconds)
@@ -593,153 +606,11 @@ def run_reference(args):
 # batched rooms x designs (one persistent launch per wave, CUDA graph)
 # ---------------------------------------------------------------------------
 
-def run_batched(args):
-    """Rooms of uneven size x 12 lamp designs: all matrices A plus the fluence
-    (16 dwell vectors) and coverage of every (room, design) job.  The batched
-    pipeline replays, per wave of rooms, one captured CUDA graph holding the
-    persistent batch launch and every job's fluence and coverage; the plain
-    pipeline makes the same calls job by job.  Scenes, candidates and dwell
-    vectors are resident before timing; A lives in a fixed pool reused by the
-    waves.  Metric: rooms per second (and the pair rate)."""
-    import torch
-
-    import paper_2103_14137_gb300 as uvc
-    from synth import dwell_vectors
-    from synth.batched import batch, designs
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    uvc.build()
-    t_gen = time.perf_counter()
-    data = batch(args.rooms, base_seed=100 + 1000 * rank)
-    t_gen = time.perf_counter() - t_gen
-    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for _, L, _ in data[0][1]]   # the 12 designs' lamps
-    Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
-    rooms = []
-    for room, jobs in data:
-        sc = uvc.build_scene(Td(room.verts), Td(room.tris), Td(room.centroid), Td(room.normal), Td(room.area),
-                             Td(room.excl))
-        js = [(Td(cand), d, Td(dwell_vectors(NVEC, cand.shape[0], seed=d))) for cand, _, d in jobs]
-        rooms.append((sc, js))
-    # waves of whole rooms under the A pool
-    pool_floats = int(args.pool_gb * 2 ** 30 / 4)
-    waves, cur, used = [], [], 0
-    for r, (sc, js) in enumerate(rooms):
-        need = sum(c.shape[0] * sc.np for c, _, _ in js)
-        if cur and used + need > pool_floats:
-            waves.append(cur)
-            cur, used = [], 0
-        cur.append(r)
-        used += need
-    waves.append(cur)
-    biggest = max(sum(sum(c.shape[0] * rooms[r][0].np for c, _, _ in rooms[r][1]) for r in w) for w in waves)
-    pool = torch.empty(biggest, dtype=torch.float32, device=dev)
-
-    def wave_views(w):
-        views, off = [], 0
-        for r in w:
-            sc, js = rooms[r]
-            for cand, d, t in js:
-                n = cand.shape[0] * sc.np
-                views.append((sc, cand, d, t, pool[off:off + n].view(cand.shape[0], sc.np)))
-                off += n
-        return views
-
-    def post(sc, A, t, mus):
-        mu = uvc.fluence(sc, A, t, mu=mus)
-        uvc.coverage(sc, mu, MU_MIN)
-
-    # batched: one batch, one graph per wave (captured before timing)
-    graphs, batches, keep = [], [], []
-    tuned = None
-    for w in waves:
-        views = wave_views(w)
-        b = uvc.Batch([(sc, cand, d, A, None) for sc, cand, d, t, A in views], lamps)
-        if tuned is None:
-            tuned = b.autotune(0.02)
-        else:
-            b.set_config(*tuned)
-        mus = [torch.empty((NVEC, sc.np), device=dev) for sc, _, _, _, _ in views]
-        b.launch()
-        for (sc, cand, d, t, A), mu in zip(views, mus):
-            post(sc, A, t, mu)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            b.launch()
-            for (sc, cand, d, t, A), mu in zip(views, mus):
-                post(sc, A, t, mu)
-        graphs.append(g)
-        batches.append(b)
-        keep.append((views, mus))
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    a, bb = ev(), ev()
-    a.record()
-    for g in graphs:
-        g.replay()
-    bb.record()
-    torch.cuda.synchronize()
-    ms_batched = a.elapsed_time(bb)
-    clk = clocks.stop()
-    # plain: the same work, job by job
-    for w in waves[:1]:                        # warm the plain path
-        for sc, cand, d, t, A in wave_views(w)[:2]:
-            uvc.irradiance_matrix(sc, cand, lamps[d], A=A)
-            post(sc, A, t, None)
-    torch.cuda.synchronize()
-    a, bb = ev(), ev()
-    a.record()
-    for w in waves:
-        for sc, cand, d, t, A in wave_views(w):
-            uvc.irradiance_matrix(sc, cand, lamps[d], A=A)
-            post(sc, A, t, None)
-    bb.record()
-    torch.cuda.synchronize()
-    ms_plain = a.elapsed_time(bb)
-    pairs = sum(c.shape[0] * sc.np for sc, js in rooms for c, _, _ in js)
-    n = args.rooms
-    out = {
-        "metric": METRIC, "value": round(n / (ms_batched * 1e-3), 4), "unit": "rooms/s", "n_gpus": 1, "steps": 1,
-        "warmup": 1, "ms_per_step": round(ms_batched, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batched: {n} seeded rooms of uneven size (10k-200k triangles, 5k-300k patches, "
-                               "500-5,000 candidates, log-uniform) x 12 designs (lamp-bottom heights 0.3/0.5/0.8/1.1 m "
-                               "x line lamps 0.6/1.2/1.8 m, K = 4/8/12); all A plus fluence (16 vectors) and coverage",
-                   "rooms": n, "jobs": n * 12, "pairs": pairs, "waves": len(waves), "pool_gib": args.pool_gb,
-                   "tuned": {"cand_per_task": tuned[0], "blocks_per_sm": tuned[1]}},
-        "batched": {"rooms_per_s": round(n / (ms_batched * 1e-3), 4), "ms": round(ms_batched, 1),
-                    "gpairs_per_s": round(pairs / (ms_batched * 1e-3) / 1e9, 4)},
-        "plain": {"rooms_per_s": round(n / (ms_plain * 1e-3), 4), "ms": round(ms_plain, 1),
-                  "gpairs_per_s": round(pairs / (ms_plain * 1e-3) / 1e9, 4)},
-        "batched_over_plain": round(ms_plain / ms_batched, 4),
-        "clocks": clk, "generation_s": round(t_gen, 1),
-    }
-    for b in batches:
-        b.free()
-    for sc, _ in rooms:
-        sc.free()
-    print(json.dumps(out), flush=True)
-
-
-def run_learned(args):
-    """Batched + learned proposal against the plain method, in rooms/s.
-
-    Per (room, design) job the learned pipeline computes the irradiance of all
-    candidates on a probe of 1% of the patches (one batched launch), the
-    scorer features, one scorer pass over all jobs, keeps the best source of
-    every sketch patch plus the best-scoring candidates (20% in all), checks
-    the other probe half for lit area lost, and computes the exact matrix of
-    the kept candidates (a second batched launch) with its fluence (16 dwell
-    vectors) and coverage; all of it replays as one CUDA graph per wave.  Jobs
-    whose check fails are then recomputed on all candidates (inside the timed
-    region).  The plain pipeline computes every job's full matrix, fluence and
-    coverage job by job.  Scenes, probe scenes, candidates and dwell vectors
-    are resident before timing.  The quality figures (lost coverage, added
-    dwell against the plain LP) comes from the scorer's report."""
+def setup_rooms(n_rooms: int, dev, base_seed: int = 100):
+    """Rooms of uneven size x the 12 designs, resident on the device: per room
+    the scene, the probe scene (1 % of the patches, for the learned proposal)
+    and per (room, design) job the candidates, the full and kept dwell vectors
+    and the buffers of the kept candidates."""
     import torch
 
     import paper_2103_14137_gb300 as uvc
@@ -747,16 +618,12 @@ def run_learned(args):
     from synth import dwell_vectors
     from synth.batched import batch
 
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    uvc.build()
     t_gen = time.perf_counter()
-    data = batch(args.rooms, base_seed=100 + 1000 * rank)
+    data = batch(n_rooms, base_seed=base_seed)
     t_gen = time.perf_counter() - t_gen
-    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for _, L, _ in data[0][1]]
+    lamps = [uvc.Lamp(L.offsets, L.weights, L.power) for _, L, _ in data[0][1]]   # the 12 designs' lamps
     Td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
-    rooms, total_nc = [], 0
+    rooms = []
     for room, jobs in data:
         sc = uvc.build_scene(Td(room.verts), Td(room.tris), Td(room.centroid), Td(room.normal), Td(room.area),
                              Td(room.excl))
@@ -771,56 +638,173 @@ def run_learned(args):
                        "t_kept": Td(dwell_vectors(NVEC, k, seed=d)),
                        "kept": torch.zeros((k, 3), dtype=torch.float32, device=dev),
                        "idx": torch.zeros(k, dtype=torch.int32, device=dev)})
-            total_nc += nc
-        rooms.append({"sc": sc, "psc": psc, "area_p": Td(room.area[probe].astype(np.float32)), "half": half,
-                      "P": int(probe.size), "np": room.np_, "jobs": js})
-    scorer = prop.Scorer.load(max_batch=max(1, total_nc))
-    # waves of whole rooms under the pool (reduced matrices + probe matrices)
-    pool_floats = int(args.pool_gb * 2 ** 30 / 4)
+        rooms.append({"seed": room.info["seed"], "sc": sc, "psc": psc, "area": Td(room.area.astype(np.float32)),
+                      "area_p": Td(room.area[probe].astype(np.float32)), "half": half, "P": int(probe.size),
+                      "np": room.np_, "nt": room.nt, "jobs": js})
+    q = 0
+    for R in rooms:
+        for j in R["jobs"]:
+            j["q"] = q
+            q += 1
+    return lamps, rooms, t_gen
+
+
+def free_rooms(rooms):
+    for R in rooms:
+        R["sc"].free()
+        R["psc"].free()
+
+
+def _waves(rooms, need, pool_floats):
+    """Whole rooms grouped into waves whose buffers fit the pool."""
     waves, cur, used = [], [], 0
     for r, R in enumerate(rooms):
-        need = sum(j["k"] * R["np"] + j["nc"] * R["P"] for j in R["jobs"])
-        if cur and used + need > pool_floats:
+        n = need(R)
+        if cur and used + n > pool_floats:
             waves.append(cur)
             cur, used = [], 0
         cur.append(r)
-        used += need
+        used += n
     waves.append(cur)
-    biggest_job = max(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
-    pool = torch.empty(max(sum(j["k"] * rooms[r]["np"] + j["nc"] * rooms[r]["P"] for r in w
-                               for j in rooms[r]["jobs"]) for w in waves), dtype=torch.float32, device=dev)
-    full_tmp = torch.empty(biggest_job, dtype=torch.float32, device=dev)
-    flags = torch.zeros(sum(len(R["jobs"]) for R in rooms), dtype=torch.float32, device=dev)
-    maxhalf = max(R["P"] - R["half"] for R in rooms)
+    return waves
+
+
+def _post(uvc, sc, A, t, mu):
+    """Fluence (16 dwell vectors) and coverage of one job's matrix."""
+    mu = uvc.fluence(sc, A, t, mu=mu)
+    uvc.coverage(sc, mu, MU_MIN)
+
+
+def timed_steps(fn, steps: int, warmup: int = 1):
+    """Milliseconds of each of `steps` calls of fn (CUDA events on the current
+    stream, synchronised on both sides), after `warmup` untimed calls."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return ms
+
+
+def plain_pipeline(uvc, rooms, lamps, dev):
+    """The plain method, job by job: every candidate's full matrix, its fluence
+    and coverage (one A buffer, reused)."""
+    import torch
+    full = torch.empty(max(j["nc"] * R["np"] for R in rooms for j in R["jobs"]), dtype=torch.float32, device=dev)
+    mus = torch.empty(NVEC * max(R["np"] for R in rooms), dtype=torch.float32, device=dev)
+
+    def job(R, j):
+        A = full[:j["nc"] * R["np"]].view(j["nc"], R["np"])
+        uvc.irradiance_matrix(R["sc"], j["cand"], lamps[j["d"]], A=A)
+        _post(uvc, R["sc"], A, j["t_full"], mus[:NVEC * R["np"]].view(NVEC, R["np"]))
+
+    def run():
+        for R in rooms:
+            for j in R["jobs"]:
+                job(R, j)
+    return run, job
+
+
+def batched_pipeline(uvc, rooms, lamps, dev, pool_gb: float):
+    """All matrices of a wave of rooms in one persistent launch, with every
+    job's fluence and coverage, captured as one CUDA graph per wave; A lives in
+    a pool reused by the waves.  Returns (run, free, info)."""
+    import torch
+    pool_floats = int(pool_gb * 2 ** 30 / 4)
+    waves = _waves(rooms, lambda R: sum(j["nc"] * R["np"] for j in R["jobs"]), pool_floats)
+    pool = torch.empty(max(sum(j["nc"] * rooms[r]["np"] for r in w for j in rooms[r]["jobs"]) for w in waves),
+                       dtype=torch.float32, device=dev)
+    graphs, batches, keep, tuned = [], [], [], None
+    for w in waves:
+        views, off = [], 0
+        for r in w:
+            R = rooms[r]
+            for j in R["jobs"]:
+                n = j["nc"] * R["np"]
+                views.append((R["sc"], j, pool[off:off + n].view(j["nc"], R["np"])))
+                off += n
+        b = uvc.Batch([(sc, j["cand"], j["d"], A, None) for sc, j, A in views], lamps)
+        if tuned is None:
+            tuned = b.autotune(0.02)
+        else:
+            b.set_config(*tuned)
+        mus = [torch.empty((NVEC, sc.np), device=dev) for sc, _, _ in views]
+
+        def wave(b=b, views=views, mus=mus):
+            b.launch()
+            for (sc, j, A), mu in zip(views, mus):
+                _post(uvc, sc, A, j["t_full"], mu)
+        wave()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            wave()
+        graphs.append(g)
+        batches.append(b)
+        keep.append(mus)
+
+    def run():
+        for g in graphs:
+            g.replay()
+
+    def free():
+        for b in batches:
+            b.free()
+        graphs.clear()
+        keep.clear()
+
+    return run, free, {"waves": len(waves), "tuned": {"cand_per_task": tuned[0], "blocks_per_sm": tuned[1]}}
+
+
+def learned_pipeline(uvc, rooms, lamps, dev, pool_gb: float, plain_job):
+    """Batched + learned proposal.  Per job: the irradiance of all candidates
+    on the probe patches (one batched launch), the scorer features, one scorer
+    pass over all jobs, the best source of every sketch patch plus the best
+    scores kept (20 % in all), the lit probe area the kept set loses, and the
+    exact matrix of the kept candidates (a second batched launch) with its
+    fluence and coverage: one CUDA graph per wave.  After the graphs the check
+    is read back once and the jobs that fail it are recomputed on all
+    candidates (plain_job).  Returns (run, free, info); run() returns the
+    number of fallback jobs."""
+    import torch
+
+    from paper_2103_14137_gb300 import proposal as prop
+    total_nc = sum(j["nc"] for R in rooms for j in R["jobs"])
+    njobs = sum(len(R["jobs"]) for R in rooms)
+    scorer = prop.Scorer.load(max_batch=max(1, total_nc))
+    pool_floats = int(pool_gb * 2 ** 30 / 4)
+    need = lambda R: sum(j["k"] * R["np"] + j["nc"] * R["P"] for j in R["jobs"])  # noqa: E731
+    waves = _waves(rooms, need, pool_floats)
+    pool = torch.empty(max(sum(need(rooms[r]) for r in w) for w in waves), dtype=torch.float32, device=dev)
+    flags = torch.zeros(njobs, dtype=torch.float32, device=dev)
     work = uvc.probe_features_work(max(R["half"] for R in rooms), dev)
-    lost_scratch = torch.empty(max(1, maxhalf), dtype=torch.float32, device=dev)
+    lost_scratch = torch.empty(max(1, max(R["P"] - R["half"] for R in rooms)), dtype=torch.float32, device=dev)
     feat = torch.empty((max(1, total_nc), prop.IN_DIM), dtype=torch.float32, device=dev)
     score = torch.empty(max(1, total_nc), dtype=torch.float32, device=dev)
     mus_flat = torch.empty(NVEC * max(R["np"] for R in rooms), dtype=torch.float32, device=dev)
-    mus = lambda n: mus_flat[:NVEC * n].view(NVEC, n)  # noqa: E731
 
-    def wave_layout(w):
-        """Views of the pool (probe then reduced matrices) and feature rows."""
+    def layout(w):
         off, row, lay = 0, 0, []
         for r in w:
             R = rooms[r]
             for j in R["jobs"]:
-                Ap = pool[off:off + j["nc"] * R["P"]].view(j["nc"], R["P"])
+                lay.append([R, j, pool[off:off + j["nc"] * R["P"]].view(j["nc"], R["P"]), None, row])
                 off += j["nc"] * R["P"]
-                lay.append((R, j, Ap, row))
                 row += j["nc"]
-        for q, (R, j, Ap, row0) in enumerate(lay):
-            Ar = pool[off:off + j["k"] * R["np"]].view(j["k"], R["np"])
+        for e in lay:
+            R, j = e[0], e[1]
+            e[3] = pool[off:off + j["k"] * R["np"]].view(j["k"], R["np"])
             off += j["k"] * R["np"]
-            lay[q] = (R, j, Ap, Ar, row0)
         return lay, row
 
-    job_ids = {}
-    for R in rooms:
-        for j in R["jobs"]:
-            job_ids[id(j)] = len(job_ids)
-
-    def learned_wave(lay, nrows, bprobe, bred):
+    def wave(lay, nrows, bprobe, bred):
         bprobe.launch()
         for R, j, Ap, Ar, row0 in lay:
             prop.features(R["sc"], j["cand"], Ap[:, :R["half"]], R["area_p"][:R["half"]],
@@ -832,99 +816,182 @@ def run_learned(args):
                 uvc.group_boost(sj, prop.GROUP)
             uvc.mark_best(Ap[:, :R["half"]], sj, rare=prop.rare_count(j["nc"]))
             uvc.select_top(sj, j["k"], cand=j["cand"], out_cand=j["kept"], out_idx=j["idx"])
-            q = job_ids[id(j)]
-            uvc.probe_lost(Ap[:, R["half"]:], j["idx"], R["area_p"][R["half"]:], out=flags[q:q + 1],
+            uvc.probe_lost(Ap[:, R["half"]:], j["idx"], R["area_p"][R["half"]:], out=flags[j["q"]:j["q"] + 1],
                            lost=lost_scratch[:R["P"] - R["half"]])
         bred.launch()
         for R, j, Ap, Ar, row0 in lay:
-            mu = uvc.fluence(R["sc"], Ar, j["t_kept"], mu=mus(R["np"]))
-            uvc.coverage(R["sc"], mu, MU_MIN)
+            _post(uvc, R["sc"], Ar, j["t_kept"], mus_flat[:NVEC * R["np"]].view(NVEC, R["np"]))
 
     graphs, batches, tuned = [], [], None
     for w in waves:
-        lay, nrows = wave_layout(w)
+        lay, nrows = layout(w)
         bprobe = uvc.Batch([(R["psc"], j["cand"], j["d"], Ap, None) for R, j, Ap, Ar, _ in lay], lamps)
         bred = uvc.Batch([(R["sc"], j["kept"], j["d"], Ar, None) for R, j, Ap, Ar, _ in lay], lamps)
         if tuned is None:
             tuned = bprobe.autotune(0.05)
         bprobe.set_config(*tuned)
         bred.set_config(*tuned)
-        learned_wave(lay, nrows, bprobe, bred)          # eager pass: fills the kept buffers
+        wave(lay, nrows, bprobe, bred)          # eager pass: fills the kept buffers
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
-            learned_wave(lay, nrows, bprobe, bred)
+            wave(lay, nrows, bprobe, bred)
         graphs.append(g)
         batches += [bprobe, bred]
+    jobs = [(R, j) for R in rooms for j in R["jobs"]]
+    last = {"fallback": []}
 
-    def plain_job(R, j):
-        A = full_tmp[:j["nc"] * R["np"]].view(j["nc"], R["np"])
-        uvc.irradiance_matrix(R["sc"], j["cand"], lamps[j["d"]], A=A)
-        mu = uvc.fluence(R["sc"], A, j["t_full"], mu=mus(R["np"]))
-        uvc.coverage(R["sc"], mu, MU_MIN)
-
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    for g in graphs:                                    # warm replay
-        g.replay()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    a, b = ev(), ev()
-    a.record()
-    for g in graphs:
-        g.replay()
-    fl = (flags > prop.LOST_MAX).cpu().numpy()          # the check, read back on the host
-    fallback = [(R, j) for R in rooms for j in R["jobs"] if fl[job_ids[id(j)]]]
-    for R, j in fallback:
-        plain_job(R, j)
-    b.record()
-    torch.cuda.synchronize()
-    ms_learned = a.elapsed_time(b)
-    clk = clocks.stop()
-    # plain: every job's full matrix, job by job
-    plain_job(rooms[0], rooms[0]["jobs"][0])
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    a.record()
-    for R in rooms:
-        for j in R["jobs"]:
+    def run():
+        for g in graphs:
+            g.replay()
+        fl = (flags > prop.LOST_MAX).cpu().numpy()      # the check, read back on the host
+        fb = [(R, j) for R, j in jobs if fl[j["q"]]]
+        for R, j in fb:
             plain_job(R, j)
-    b.record()
-    torch.cuda.synchronize()
-    ms_plain = a.elapsed_time(b)
-    n = args.rooms
-    pairs_plain = sum(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
-    pairs_learned = sum(j["k"] * R["np"] + j["nc"] * R["P"] for R in rooms for j in R["jobs"]) + \
-        sum(j["nc"] * R["np"] for R, j in fallback)
-    rep_path = os.path.join(ROOT, "paper_2103_14137_gb300", "data", "scorer_report.json")
-    quality = None
-    if os.path.exists(rep_path):
-        with open(rep_path) as f:
-            rep = json.load(f)
-        quality = {k: rep.get(k) for k in ("eval_jobs", "lost_coverage_mean", "lost_coverage_max",
-                                           "added_dwell_mean", "added_dwell_max", "fallback_rate",
-                                           "support_recall_mean")}
-        quality["source"] = "paper_2103_14137_gb300/data/scorer_report.json (train_scorer evaluation)"
-    out = {
-        "metric": METRIC, "value": round(n / (ms_learned * 1e-3), 4), "unit": "rooms/s", "n_gpus": 1, "steps": 1,
-        "warmup": 1, "ms_per_step": round(ms_learned, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 (scorer bf16)", "data": "synthetic",
-        "config": {"workload": f"learned: {n} seeded rooms of uneven size x 12 designs; batched + learned "
-                               f"proposal (keep {prop.KEEP:.0%}, probe {prop.PROBE:.0%}) vs plain full matrices; "
-                               "fluence (16 vectors) and coverage of every job",
-                   "rooms": n, "jobs": len(job_ids), "waves": len(waves), "tuned": list(tuned)},
-        "learned": {"rooms_per_s": round(n / (ms_learned * 1e-3), 4), "ms": round(ms_learned, 1),
-                    "pairs": pairs_learned, "fallback_jobs": len(fallback)},
-        "plain": {"rooms_per_s": round(n / (ms_plain * 1e-3), 4), "ms": round(ms_plain, 1), "pairs": pairs_plain},
-        "learned_over_plain": round(ms_plain / ms_learned, 4), "quality": quality,
-        "clocks": clk, "generation_s": round(t_gen, 1),
-    }
-    for bb in batches:
-        bb.free()
-    scorer.close()
-    for R in rooms:
-        R["sc"].free()
-        R["psc"].free()
+        last["fallback"] = [j["q"] for _, j in fb]
+        return len(fb)
+
+    def free():
+        for b in batches:
+            b.free()
+        graphs.clear()
+        scorer.close()
+
+    return run, free, {"waves": len(waves), "tuned": list(tuned), "last": last}
+
+
+def proposal_quality(uvc, rooms, lamps, dev, qjobs, fallback, workers: int):
+    """Lost coverage and added dwell time of the learned proposal on the jobs
+    `qjobs` (job numbers), measured on the kept sets the timed run produced:
+    the dwell-time LP of Eq. (9) (row generation over every patch) on all
+    candidates (the plain method) and on the kept candidates (all of them for a
+    job that fell back), coverage at 100 J/m^2 of every patch from the exact
+    matrix."""
+    import torch
+
+    from paper_2103_14137_gb300 import proposal as prop
+    sel = [(R, j) for R in rooms for j in R["jobs"] if j["q"] in set(qjobs)]
+    full, red, meta = [], [], []
+    for R, j in sel:
+        A, _ = uvc.irradiance_matrix(R["sc"], j["cand"], lamps[j["d"]])
+        fb = j["q"] in set(fallback)
+        rows = np.arange(j["nc"]) if fb else np.sort(j["idx"].cpu().numpy().astype(np.int64))
+        seed = R["seed"] * 16 + j["d"]
+        full.append({"A": A, "rows": None, "area": R["area"], "seed": seed, "scene": R["sc"]})
+        red.append({"A": A, "rows": rows, "area": R["area"], "seed": seed, "scene": R["sc"]})
+        meta.append({"room": R["seed"], "design": j["d"], "nc": j["nc"], "np": R["np"], "kept": int(rows.size),
+                     "fallback": fb})
+    t0 = time.perf_counter()
+    sols = prop.dwell_rowgen(full + red, workers)
+    lp_s = time.perf_counter() - t0
+    n = len(sel)
+    for k, m in enumerate(meta):
+        t_full, mu_full = sols[k][0], sols[k][1]
+        t_red, mu_red = sols[n + k][0], sols[n + k][1]
+        cf, cr = prop.coverage_of(sel[k][0]["area"], mu_full), prop.coverage_of(sel[k][0]["area"], mu_red)
+        m.update({"cov_full": round(cf, 6), "cov_kept": round(cr, 6), "lost_coverage": max(0.0, cf - cr),
+                  "dwell_full_s": round(float(t_full.sum()), 2), "dwell_kept_s": round(float(t_red.sum()), 2),
+                  "added_dwell": float(t_red.sum() / max(t_full.sum(), 1e-30) - 1.0)})
+    del full, red, sols
+    torch.cuda.empty_cache()
+    lost = np.array([m["lost_coverage"] for m in meta])
+    added = np.array([m["added_dwell"] for m in meta])
+    return {"jobs": len(meta), "lost_coverage_mean": float(lost.mean()), "lost_coverage_max": float(lost.max()),
+            "added_dwell_mean": float(added.mean()), "added_dwell_max": float(added.max()),
+            "lp_wall_s": round(lp_s, 1), "lp_workers": workers, "per_job": meta}
+
+
+def batched_learned(uvc, dev, n_rooms: int, steps: int, pool_gb: float = 96.0, quality_jobs: int = 8,
+                    pipelines=("plain", "batched", "learned"), base_seed: int = 100):
+    """Rooms/s of the plain method (job by job), the batched engine and the
+    batched + learned proposal on the same seeded rooms x 12 designs, each
+    timed over `steps` steps after one warm-up (a step = every job of every
+    room: all matrices, or the learned pipeline's probe, selection and kept
+    matrices with its fallbacks, plus every job's fluence and coverage), and
+    the learned proposal's quality on a seeded subset of the same timed jobs."""
+    import torch
+    lamps, rooms, t_gen = setup_rooms(n_rooms, dev, base_seed)
+    njobs = sum(len(R["jobs"]) for R in rooms)
+    pairs = sum(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
+    plain_run, plain_job = plain_pipeline(uvc, rooms, lamps, dev)
+    out = {"rooms": n_rooms, "designs": 12, "jobs": njobs, "pairs": pairs, "steps": steps, "warmup": 1,
+           "room_seeds": [rooms[0]["seed"], rooms[-1]["seed"]], "generation_s": round(t_gen, 1)}
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    if "plain" in pipelines:
+        ms = timed_steps(plain_run, steps)
+        out["plain"] = {"rooms_per_s": round(n_rooms / (np.mean(ms) * 1e-3), 4), "ms_per_step": round(float(np.mean(ms)), 1),
+                        "ms_steps": [round(x, 1) for x in ms], "gpairs_per_s": round(pairs / (np.mean(ms) * 1e-3) / 1e9, 4)}
+    if "batched" in pipelines:
+        run, free, info = batched_pipeline(uvc, rooms, lamps, dev, pool_gb)
+        ms = timed_steps(run, steps)
+        free()
+        torch.cuda.empty_cache()
+        out["batched"] = {"rooms_per_s": round(n_rooms / (np.mean(ms) * 1e-3), 4), "ms_per_step": round(float(np.mean(ms)), 1),
+                          "ms_steps": [round(x, 1) for x in ms], "gpairs_per_s": round(pairs / (np.mean(ms) * 1e-3) / 1e9, 4),
+                          **{k: v for k, v in info.items() if k != "last"}}
+    fallback = []
+    if "learned" in pipelines:
+        run, free, info = learned_pipeline(uvc, rooms, lamps, dev, pool_gb, plain_job)
+        nfb = []
+        ms = timed_steps(lambda: nfb.append(run()), steps)
+        fallback = info["last"]["fallback"]
+        free()
+        torch.cuda.empty_cache()
+        out["learned"] = {"rooms_per_s": round(n_rooms / (np.mean(ms) * 1e-3), 4), "ms_per_step": round(float(np.mean(ms)), 1),
+                          "ms_steps": [round(x, 1) for x in ms], "fallback_jobs": nfb[-1], "waves": info["waves"],
+                          "tuned": info["tuned"]}
+    out["clocks"] = clocks.stop()
+    if "plain" in out and "batched" in out:
+        out["batched_over_plain"] = round(out["plain"]["ms_per_step"] / out["batched"]["ms_per_step"], 4)
+    if "plain" in out and "learned" in out:
+        out["learned_over_plain"] = round(out["plain"]["ms_per_step"] / out["learned"]["ms_per_step"], 4)
+        if quality_jobs > 0:
+            rng = np.random.default_rng(2103)
+            qjobs = sorted(rng.choice(njobs, size=min(quality_jobs, njobs), replace=False).tolist())
+            workers = max(1, (os.cpu_count() or 2) - 1)
+            out["quality"] = proposal_quality(uvc, rooms, lamps, dev, qjobs, fallback, workers)
+            out["quality"]["sample"] = (f"{len(qjobs)} of the {njobs} timed jobs (seeded), the kept sets of the "
+                                        f"last timed step")
+    free_rooms(rooms)
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    """Rooms of uneven size x 12 lamp designs: all matrices A plus the fluence
+    (16 dwell vectors) and coverage of every (room, design) job, through the
+    batched engine (one captured graph per wave of rooms) against the plain
+    job-by-job calls.  Metric: rooms per second."""
+    _run_rooms(args, ("plain", "batched"), "batched", 0)
+
+
+def run_learned(args):
+    """Batched + learned proposal against the plain method, in rooms/s, with
+    the proposal's lost coverage and added dwell time measured on a seeded
+    subset of the timed jobs."""
+    _run_rooms(args, ("plain", "learned"), "learned", 8)
+
+
+def _run_rooms(args, pipelines, key, quality_jobs):
+    import torch
+
+    import paper_2103_14137_gb300 as uvc
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    uvc.build()
+    steps = max(3, args.steps)
+    r = batched_learned(uvc, dev, args.rooms, steps, args.pool_gb, quality_jobs, pipelines, 100 + 1000 * rank)
+    ms = r[key]["ms_per_step"]
+    out = {"metric": METRIC, "value": r[key]["rooms_per_s"], "unit": "rooms/s", "n_gpus": 1, "steps": steps,
+           "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if key == "batched" else "f32 (scorer bf16)", "data": "synthetic",
+           "config": {"workload": f"{key}: {args.rooms} seeded rooms of uneven size (10k-200k triangles, 5k-300k "
+                                  "patches, 500-5,000 candidates, log-uniform) x 12 designs (lamp-bottom heights "
+                                  "0.3/0.5/0.8/1.1 m x line lamps 0.6/1.2/1.8 m, K = 4/8/12); fluence (16 vectors) and "
+                                  "coverage of every job", "rooms": args.rooms, "pool_gib": args.pool_gb},
+           **{k: v for k, v in r.items() if k not in ("steps",)}}
     print(json.dumps(out), flush=True)
 
 

@@ -86,3 +86,27 @@ def test_measured_traffic_scales_and_goes_stale(tmp_path):
     assert bench.measured_traffic(1000, str(stale)) is None
     assert bench.measured_traffic(1000, str(tmp_path / "missing.txt")) is None
 
+
+
+def test_room_waves_fit_the_pool():
+    """Whole rooms are grouped into waves in order; a wave's buffers never
+    exceed the pool unless a single room does (it then forms its own wave)."""
+    rooms = [{"n": n} for n in (5, 3, 4, 9, 1, 2, 12)]
+    waves = bench._waves(rooms, lambda R: R["n"], 8)
+    assert [r for w in waves for r in w] == list(range(len(rooms)))
+    assert waves == [[0, 1], [2], [3], [4, 5], [6]]
+    for w in waves:
+        assert sum(rooms[r]["n"] for r in w) <= 8 or len(w) == 1
+
+
+def test_rooms_block_is_bounded():
+    """The rooms-per-second block of the default line runs a fixed number of
+    timed steps whatever --steps says, on a stated number of rooms."""
+    assert bench.BL_STEPS == 3 and bench.BL_QUALITY_JOBS >= 1
+    saved = sys.argv
+    try:
+        sys.argv = ["bench.py", "--steps", "20"]
+        a = bench.parse()
+    finally:
+        sys.argv = saved
+    assert a.bl_rooms == 16 and a.steps == 20
