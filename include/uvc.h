@@ -147,7 +147,8 @@ int uvc_free_scene(uvc_scene* scene);
  * each triangle it reaches against every source still searching; with 0,
  * every source is searched on its own.  Both give the visibility of Eq. (7)
  * source by source with the same segment test; they can differ only where a
- * segment grazes a triangle lying in the patch's own plane.  The setting is
+ * segment grazes a triangle lying in the patch's own plane.  Scenes of more
+ * than 2^27 triangles are always searched source by source.  The setting is
  * read when a call (or uvc_batch_create) converts its lamp.
  *   enable    0 or 1
  *   previous  HOST int32, may be NULL: receives the setting before the call

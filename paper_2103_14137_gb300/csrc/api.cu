@@ -34,7 +34,7 @@ std::atomic<int> g_wedge{1};
 
 }  // namespace
 
-int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound) {
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound, int64_t max_tris) {
     if (!lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES) return UVC_E_INVAL;
     if (!std::isfinite(lamp->power) || lamp->power < 0.f) return UVC_E_INVAL;
     std::memset(out, 0, sizeof(*out));
@@ -51,7 +51,8 @@ int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound) {
     }
     bool vertical = lamp->K >= 2 && lamp->K <= kWedgeMaxK;
     for (int m = 0; m < lamp->K && vertical; ++m) vertical = out->ox[m] == 0.f && out->oy[m] == 0.f;
-    out->wedge = vertical && g_wedge.load(std::memory_order_relaxed) ? 1 : 0;
+    // the wedge search queues leaf indices in 27 bits (larger scenes search source by source)
+    out->wedge = vertical && max_tris <= kWedgeMaxTris && g_wedge.load(std::memory_order_relaxed) ? 1 : 0;
     if (out->wedge) {
         const int K = lamp->K;
         const double z0 = out->oz[0], dz = ((double)out->oz[K - 1] - z0) / (K - 1);
@@ -110,7 +111,7 @@ int uvc_irradiance_matrix(const uvc_scene* scene, const float* cand, int64_t nc,
                           int64_t lda, uint32_t* vis, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc)) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc == 0 || scene->np == 0) return UVC_OK;
@@ -122,7 +123,7 @@ int uvc_irradiance_counters(const uvc_scene* scene, const float* cand, int64_t n
                             float* A, int64_t lda, uint64_t* counters, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || !counters) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc > 0 && scene->np > 0 && (!cand || !A)) return UVC_E_INVAL;
@@ -134,7 +135,7 @@ int uvc_irradiance_area_mean(const uvc_scene* scene, const float* cand, int64_t 
                              const float* ptri, float* A, int64_t lda, uint8_t* nclosed, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (lda < scene->np) return UVC_E_INVAL;
     if (nc > 0 && scene->np > 0 && (!cand || !A || !ptri)) return UVC_E_INVAL;
@@ -152,7 +153,7 @@ int uvc_irradiance_raster(const uvc_scene* scene, const float* tri_normal, const
                           uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nc > INT32_MAX || R < 1 || R > 4096) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (lda < scene->nt) return UVC_E_INVAL;
     if (nc > 0 && scene->nt > 0 && (!cand || !A || !tri_normal || !workspace)) return UVC_E_INVAL;
@@ -171,7 +172,7 @@ int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, 
                          const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (scene->np == 0) return UVC_OK;
     if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;
@@ -182,7 +183,7 @@ int uvc_fluence_streamed_noalloc(const uvc_scene* scene, const float* cand, int6
                                  const float* t, int32_t nvec, float* mu, uvc_stream_t stream) {
     if (!scene || !uvc::count_ok(nc) || nvec < 1 || nvec > 256) return UVC_E_INVAL;
     uvc::LampDev L;
-    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound);
+    int rc = uvc::lamp_to_device(lamp, &L, scene->coord_bound, scene->nt);
     if (rc != UVC_OK) return rc;
     if (scene->np == 0) return UVC_OK;
     if (!mu || (nc > 0 && (!cand || !t))) return UVC_E_INVAL;

@@ -33,14 +33,24 @@ struct JobDev {
     int nc, lamp, nchunk, njb;
 };
 
+// The lamps of a batch of at most kParamLamps lamps travel in the kernel's
+// parameters (constant memory: the sources' heights and powers, read in the
+// inner loops, are warp-uniform broadcasts there); larger batches read them
+// from the device table.
+constexpr int kParamLamps = 16;
+struct LampPack {
+    LampDev L[kParamLamps];
+};
+
 // Lamps with the wedge path (LampDev::wedge) use the per-source shared
 // arrays, sized for the batch's largest such lamp (wedge_k).  MODE: 0 = no
 // lamp of the batch takes the wedge path, 1 = all do, 2 = mixed (chosen per
-// job; both paths inlined).
-template <int CPT, int MODE>
+// job; both paths inlined).  PACK: the lamps come from `pack`.
+template <int MODE, bool PACK>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     k_irradiance_batch(const JobDev* __restrict__ jobs, int njobs, const LampDev* __restrict__ lamps,
-                       int64_t task_lo, int64_t task_hi, int stack_cap, int wedge_k) {
+                       const __grid_constant__ LampPack pack, int cpt, int64_t task_lo, int64_t task_hi,
+                       int stack_cap, int wedge_k) {
     extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * stack_cap;
@@ -58,9 +68,9 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
         const int j = jb * 32 + lane;
         const PatchLane P = load_patch(J.S, j);
         int cache = -1;
-        const int i1 = min(J.nc, (ic + 1) * CPT);
-        const LampDev& L = lamps[J.lamp];
-        for (int i = ic * CPT; i < i1; ++i) {
+        const int i1 = min(J.nc, (ic + 1) * cpt);
+        const LampDev& L = PACK ? pack.L[J.lamp] : lamps[J.lamp];
+        for (int i = ic * cpt; i < i1; ++i) {
             const bool wedge = MODE == 1 || (MODE == 2 && L.wedge);
             const float E = wedge ? irradiance_wedge<false>(J.S, J.cand, J.nc, L, i, jb, lane, stack, ws, J.vis,
                                                             J.njb, P, cache)
@@ -71,21 +81,14 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     }
 }
 
-using BatchKernel = void (*)(const JobDev*, int, const LampDev*, int64_t, int64_t, int, int);
+using BatchKernel = void (*)(const JobDev*, int, const LampDev*, const LampPack, int, int64_t, int64_t, int, int);
 
-template <int MODE>
-BatchKernel kernel_for_mode(int cpt) {
-    switch (cpt) {
-        case 2: return k_irradiance_batch<2, MODE>;
-        case 4: return k_irradiance_batch<4, MODE>;
-        case 16: return k_irradiance_batch<16, MODE>;
-        default: return k_irradiance_batch<8, MODE>;
-    }
+template <bool PACK>
+BatchKernel kernel_for_pack(int mode) {
+    return mode == 0 ? k_irradiance_batch<0, PACK> : (mode == 1 ? k_irradiance_batch<1, PACK> : k_irradiance_batch<2, PACK>);
 }
 
-BatchKernel kernel_for(int cpt, int mode) {
-    return mode == 0 ? kernel_for_mode<0>(cpt) : (mode == 1 ? kernel_for_mode<1>(cpt) : kernel_for_mode<2>(cpt));
-}
+BatchKernel kernel_for(int mode, bool pack) { return pack ? kernel_for_pack<true>(mode) : kernel_for_pack<false>(mode); }
 
 bool valid_cpt(int c) { return c == 2 || c == 4 || c == 8 || c == 16; }
 
@@ -104,6 +107,7 @@ struct uvc_batch {
     int wedge_k = 0;                      // largest K among the lamps with the wedge path
     int mode = 0;                         // kernel variant: 0 no wedge lamp, 1 all wedge, 2 mixed
     int64_t total_pairs = 0;
+    uvc::LampPack pack{};                 // the lamps again, for the kernel parameters (nlamps <= kParamLamps)
     int uploaded_cpt = 0;                 // cand_per_task of the uploaded table
     uvc_batch_config tuned{8, 0};        // configuration used by uvc_batch_launch
 };
@@ -134,7 +138,8 @@ int upload(uvc_batch* b, int cpt, cudaStream_t stream, int64_t* total_tasks) {
 
 int launch_range(const uvc_batch* b, int cpt, int blocks_per_sm, int64_t lo, int64_t hi, cudaStream_t stream) {
     if (hi <= lo) return UVC_OK;
-    BatchKernel k = kernel_for(cpt, b->mode);
+    const bool pack = b->nlamps <= kParamLamps;
+    BatchKernel k = kernel_for(b->mode, pack);
     const size_t smem = stack_smem_bytes(b->stack_cap) + wedge_smem_bytes(b->wedge_k);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -148,7 +153,8 @@ int launch_range(const uvc_batch* b, int cpt, int blocks_per_sm, int64_t lo, int
     int64_t grid = (int64_t)per_sm * sm_count();
     const int64_t warps_needed = (hi - lo + kWarpsPerBlock - 1) / kWarpsPerBlock;
     grid = std::max<int64_t>(1, std::min(grid, warps_needed));
-    k<<<(int)grid, kThreads, smem, stream>>>(b->dev_jobs, b->njobs, b->dev_lamps, lo, hi, b->stack_cap, b->wedge_k);
+    k<<<(int)grid, kThreads, smem, stream>>>(b->dev_jobs, b->njobs, b->dev_lamps, b->pack, cpt, lo, hi, b->stack_cap,
+                                             b->wedge_k);
     return status_from_cuda(cudaGetLastError());
 }
 
@@ -190,12 +196,17 @@ int uvc_batch_create(const uvc_job* jobs, int32_t njobs, const uvc_lamp* lamps, 
     b->nlamps = nlamps;
     b->host_lamps.resize(nlamps);
     float coord_bound = 0.f;   // over every job's scene (a lamp may serve several)
+    int64_t max_tris = 0;
     for (int q = 0; q < njobs; ++q)
-        if (jobs[q].scene) coord_bound = std::max(coord_bound, jobs[q].scene->coord_bound);
+        if (jobs[q].scene) {
+            coord_bound = std::max(coord_bound, jobs[q].scene->coord_bound);
+            max_tris = std::max(max_tris, jobs[q].scene->nt);
+        }
     for (int l = 0; l < nlamps; ++l) {
         uvc::LampDev& D = b->host_lamps[l];
-        if (uvc::lamp_to_device(&lamps[l], &D, coord_bound) != UVC_OK) { delete b; return UVC_E_INVAL; }
+        if (uvc::lamp_to_device(&lamps[l], &D, coord_bound, max_tris) != UVC_OK) { delete b; return UVC_E_INVAL; }
         if (D.wedge) b->wedge_k = std::max(b->wedge_k, D.K);
+        if (l < uvc::kParamLamps) b->pack.L[l] = D;
     }
     int nwedge = 0;
     for (const auto& D : b->host_lamps) nwedge += D.wedge ? 1 : 0;

@@ -553,8 +553,10 @@ __device__ __forceinline__ void wedge_pair_hits(const WedgeLane& w, float2 nx, f
 // Per (source, lane) data of the wedge path, in shared memory (one warp's
 // slice): shear constants and axis permutation of the source's segment, and
 // its Eq. (7) term w_m P <n, v> / (4 pi |v|^3); and the warp's queue of leaf
-// tests (see wedge_traverse): a ring of (leaf, lane) items, and per lane the
-// sources found occluded by the last batch and the leaf that did it.
+// tests (see wedge_traverse): a ring of items (lane << 27 | leaf), and per
+// lane the sources found occluded by the last batch and the leaf that did it.
+// The packed items need leaf indices below 2^27 (kWedgeMaxTris); larger
+// scenes take the per-source traversal.
 // The queue is worked off, up to 32 items at a time, once kLeafFlush items
 // wait (a tuning constant: fewer waiting items stop lanes sooner, more keep
 // the batches fuller; on the ward 16: 76.7, 24: 75.9, 32: 77.1, 48: 80.4 ms
@@ -566,11 +568,12 @@ constexpr int kLeafQueue = 256;       // ring entries per warp (a node adds at m
 constexpr int kLeafBatch = 32;        // items per batch: one per lane
 constexpr int kLeafFlush = UVC_LEAF_FLUSH;
 constexpr uint32_t kOobBit = 0x80000000u;   // checked build: a leaf index out of range (sources use bits 0..15)
+constexpr int kItemLeafBits = 27;
+constexpr uint32_t kItemLeafMask = (1u << kItemLeafBits) - 1u;
 struct WedgeSmem {
     float4* shear;            // [K][32]: (sx, sy, sz, kx | ky << 2 | kz << 4)
     float* term;              // [K][32]
-    int* qleaf;               // [kLeafQueue]
-    unsigned char* qlane;     // [kLeafQueue]
+    uint32_t* qitem;          // [kLeafQueue]: lane << 27 | leaf
     uint32_t* occ;            // [32]
     int* qhit;                // [32]
 };
@@ -581,7 +584,7 @@ struct WedgeSmem {
 __host__ __device__ inline size_t stack_smem_bytes(int stack_cap) {
     return ((size_t)kWarpsPerBlock * stack_cap * sizeof(int) + 15) & ~size_t(15);
 }
-constexpr size_t kWedgeQueueBytes = kLeafQueue * (sizeof(int) + 1) + 32 * (sizeof(uint32_t) + sizeof(int));
+constexpr size_t kWedgeQueueBytes = kLeafQueue * sizeof(uint32_t) + 32 * (sizeof(uint32_t) + sizeof(int));
 inline size_t wedge_smem_bytes(int K) {
     return (size_t)kWarpsPerBlock * (K * 32 * (sizeof(float4) + sizeof(float)) + kWedgeQueueBytes);
 }
@@ -592,13 +595,11 @@ __device__ __forceinline__ WedgeSmem wedge_smem(char* base, int K, int warp) {
     w.shear = reinterpret_cast<float4*>(base) + (size_t)warp * K * 32;
     w.term = reinterpret_cast<float*>(base + per_src * sizeof(float4)) + (size_t)warp * K * 32;
     char* q = base + per_src * (sizeof(float4) + sizeof(float));   // 4-byte aligned
-    w.qleaf = reinterpret_cast<int*>(q) + (size_t)warp * kLeafQueue;
-    q += (size_t)kWarpsPerBlock * kLeafQueue * sizeof(int);
+    w.qitem = reinterpret_cast<uint32_t*>(q) + (size_t)warp * kLeafQueue;
+    q += (size_t)kWarpsPerBlock * kLeafQueue * sizeof(uint32_t);
     w.occ = reinterpret_cast<uint32_t*>(q) + (size_t)warp * 32;
     q += (size_t)kWarpsPerBlock * 32 * sizeof(uint32_t);
     w.qhit = reinterpret_cast<int*>(q) + (size_t)warp * 32;
-    q += (size_t)kWarpsPerBlock * 32 * sizeof(int);
-    w.qlane = reinterpret_cast<unsigned char*>(q) + (size_t)warp * kLeafQueue;
     return w;
 }
 
@@ -615,9 +616,9 @@ __device__ __forceinline__ void wedge_leaf_batch(const SceneView& S, const LampD
                                                  float cz, float sz, float gx, float gy, float mh, int ex0, int ex1,
                                                  unsigned& c_leaf, unsigned& c_tri, int& hit_tri, bool& oob) {
     const bool has = lane < n;
-    const int slot = (head + lane) & (kLeafQueue - 1);
-    const int own = has ? (int)ws.qlane[slot] : lane;
-    const int leaf = has ? ws.qleaf[slot] : 0;
+    const uint32_t item = has ? ws.qitem[(head + lane) & (kLeafQueue - 1)] : (uint32_t)lane << kItemLeafBits;
+    const int own = (int)(item >> kItemLeafBits);
+    const int leaf = (int)(item & kItemLeafMask);
     const uint32_t owant = __shfl_sync(kFull, want, own);
     const float osz = __shfl_sync(kFull, sz, own);
     const float ogx = __shfl_sync(kFull, gx, own);
@@ -743,8 +744,7 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
             int pos = tail + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
             tail += __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
             for (unsigned m = mine; m; m &= m - 1) {
-                ws.qleaf[pos & (kLeafQueue - 1)] = ~pick4(rr, __ffs(m) - 1);
-                ws.qlane[pos & (kLeafQueue - 1)] = (unsigned char)lane;
+                ws.qitem[pos & (kLeafQueue - 1)] = ((uint32_t)lane << kItemLeafBits) | (uint32_t)~pick4(rr, __ffs(m) - 1);
                 ++pos;
             }
             __syncwarp();

@@ -38,8 +38,10 @@ struct __align__(16) Node4 {
 };
 
 // Largest lamp for the wedge traversal of vertical line lamps (its shared
-// memory per warp grows with K).
+// memory per warp grows with K), and largest scene (its queue packs leaf
+// indices into 27 bits).
 constexpr int kWedgeMaxK = 16;
+constexpr int64_t kWedgeMaxTris = int64_t(1) << 27;
 
 // Lamp as seen by the kernels: source offsets and source powers w_m * P.
 // wedge = 1: every offset is vertical (x = y = 0), 2 <= K <= kWedgeMaxK, and
@@ -57,8 +59,9 @@ struct LampDev {
 };
 
 // Host: validate a lamp and convert it (api.cu); coord_bound is the largest
-// coordinate magnitude of the scene(s) it will be used with.
-int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound);
+// coordinate magnitude and max_tris the largest triangle count of the
+// scene(s) it will be used with.
+int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound, int64_t max_tris);
 
 }  // namespace uvc
 

@@ -203,3 +203,32 @@ def test_batch_of_uneven_rooms_and_designs_against_oracle():
     b.free()
     for sc in scenes:
         sc.free()
+
+
+def test_batch_with_more_lamps_than_the_parameter_pack():
+    """18 lamps (more than the 16 a launch carries in its parameters: the
+    kernel then reads them from the batch's device table) over two rooms,
+    point, tilted and vertical line lamps mixed; every job against the
+    single-matrix call."""
+    rooms = [tiny_room(), batched_room(113)]
+    scenes = [build(r) for r in rooms]
+    lamps_g = [line_lamp(0.3 + 0.1 * k, 2 + k % 11, 100.0) for k in range(16)]
+    tilted = line_lamp(1.2, 8, 120.0)
+    tilted.offsets[:, 1] = np.linspace(-0.1, 0.1, 8, dtype=np.float32)
+    lamps_g += [tiny_room().lamp, tilted]
+    L = [uvc.Lamp(x.offsets, x.weights, x.power) for x in lamps_g]
+    jobs = []
+    for r, (room, sc) in enumerate(zip(rooms, scenes)):
+        for d in range(len(L)):
+            cand = room.cand[: 7 + d] if room.nc else design_candidates(room, 0.6, 1.0, 9 + d, seed=d)
+            A = torch.full((cand.shape[0], sc.np), -1.0, device="cuda")
+            vis = torch.zeros((L[d].K, cand.shape[0], (sc.np + 31) // 32), dtype=torch.int32, device="cuda")
+            jobs.append((sc, T(cand), d, A, vis))
+    ref = _reference(jobs, L)
+    b = uvc.Batch(jobs, L)
+    b.launch()
+    _check(jobs, ref)
+    b.free()
+    for sc in scenes:
+        assert uvc.scene_status(sc) == 0
+        sc.free()
