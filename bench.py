@@ -68,9 +68,11 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["ward", "tiny", "large", "batched", "learned", "area", "raster"],
+    p.add_argument("--workload", choices=["ward", "tiny", "large", "large_tiles", "batched", "learned", "area",
+                                          "raster"],
                    default="ward")
     p.add_argument("--resolution", type=int, default=512, help="raster workload: cube face resolution R")
+    p.add_argument("--tile", type=int, default=500, help="large_tiles workload: candidates per tile of A")
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
@@ -96,7 +98,7 @@ def dist_env():
 def rank_seeds(name: str, rank: int):
     """Room and dwell-vector seeds of a rank: rank 0 runs the reference room of
     the workload; rank r an independent room of the same size (seed + 1000 r)."""
-    base = {"tiny": 0, "ward": 1, "large": 3}[name]
+    base = {"tiny": 0, "ward": 1, "large": 3, "large_tiles": 3}[name]
     return base + 1000 * rank, 2 + 1000 * rank
 
 
@@ -120,11 +122,11 @@ def make_workload(name: str, rank: int):
     room_seed, t_seed = rank_seeds(name, rank)
     if name == "tiny":
         s = tiny_room(seed=room_seed)
-    elif name == "large":
+    elif name in ("large", "large_tiles"):
         s = large_floor(seed=room_seed)
     else:
         s = ward_room(seed=room_seed)
-    nvec = 64 if name == "large" else NVEC
+    nvec = 64 if name in ("large", "large_tiles") else NVEC
     t = dwell_vectors(nvec, s.nc, seed=t_seed)
     return s, t
 
@@ -134,6 +136,8 @@ def workload_config(name, s, nvec, world):
         "ward": "plain method, ward-sized room: 10x8x3 m, 6 beds, 4 cabinets, 2 partitions; K=8 line lamp 1.2 m, P=120 W",
         "tiny": "plain method, tiny room: 4x4x3 m with a table; point lamp P=80 W",
         "large": "large floor: 30x30x3 m, 20 rooms + corridor; K=8 line lamp; streamed A^T t (A not stored)",
+        "large_tiles": "large floor: 30x30x3 m, 20 rooms + corridor; K=8 line lamp; FP32 A (10,000 x 994,000, "
+                       "40 GB) written tile by tile, then A^T t for 64 dwell vectors",
     }[name]
     return {"workload": desc, "triangles": s.nt, "patches": s.np_, "candidates": s.nc, "sources_K": s.lamp.K,
             "dwell_vectors": nvec, "mu_min_J_m2": MU_MIN, "global_batch_rooms": world,
@@ -221,7 +225,7 @@ def l2_read_peak(uvc, nbytes=32 * 2 ** 20, passes=40, reps=10) -> dict:
                       "launch, 4 x 512 threads per SM, best of 10 launches (CUDA events)"}
 
 
-def memory_roofline(uvc, sc, s, irr_s, pairs, pk, ntask=3000, seed=11) -> dict:
+def memory_roofline(uvc, sc, s, irr_s, pairs, pk, ntask=3000, seed=11, vis=True) -> dict:
     """Bytes per pair of the wedge traversal from the counting replay
     (replay/, the same hierarchy and visit order on the CPU, over a seeded
     sample of warp tasks) against the measured L2 and HBM read bandwidths."""
@@ -229,7 +233,7 @@ def memory_roofline(uvc, sc, s, irr_s, pairs, pk, ntask=3000, seed=11) -> dict:
     ex = uvc.scene_export_traversal(sc)
     tasks = replay.sample_tasks(s.nc, s.np_, ntask, seed)
     c = replay.replay(ex, s.cand, s.lamp.offsets, tasks)
-    bpp = replay.bytes_per_pair(c, s.lamp.K)
+    bpp = replay.bytes_per_pair(c, s.lamp.K, vis=vis)
     l2 = l2_read_peak(uvc)
     hbm = float(pk.get("hbm_gbs", 6800.0))
     ach_w = bpp["per_warp"] * pairs / irr_s / 1e9
@@ -277,13 +281,16 @@ def run_ours(args):
     nvec = t_host.shape[0]
     lamp = uvc.Lamp(s.lamp.offsets, s.lamp.weights, s.lamp.power)
     streamed = args.workload == "large"
+    tiled = args.workload == "large_tiles"
 
     host = {"verts": s.verts, "tris": s.tris, "centroid": s.centroid, "normal": s.normal, "area": s.area,
             "excl": s.excl, "cand": s.cand, "t": t_host}
     d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in host.items()}
     nwords = (s.np_ + 31) // 32
-    A = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32, device=dev)
-    vis = None if streamed else torch.empty((s.lamp.K, s.nc, nwords), dtype=torch.int32, device=dev)
+    # rows of A padded to a multiple of 16 bytes, so that the fluence can stream them with tensor-map copies
+    lda = (s.np_ + 3) // 4 * 4
+    A = None if streamed else torch.empty((s.nc, lda), dtype=torch.float32, device=dev)[:, :s.np_]
+    vis = None if (streamed or tiled) else torch.empty((s.lamp.K, s.nc, nwords), dtype=torch.int32, device=dev)
     flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
@@ -300,6 +307,11 @@ def run_ours(args):
         if streamed:
             mu = uvc.fluence_streamed(sc, d["cand"], lamp, d["t"])
             n += 2
+        elif tiled:
+            for i0 in range(0, s.nc, args.tile):   # A written tile by tile (row slices, lda = np)
+                i1 = min(s.nc, i0 + args.tile)
+                uvc.irradiance_matrix(sc, d["cand"][i0:i1], lamp, A=A[i0:i1])
+                n += 1
         else:
             uvc.irradiance_matrix(sc, d["cand"], lamp, A=A, vis=vis)
             n += 1
@@ -352,10 +364,11 @@ def run_ours(args):
 
     # instrumented run (outside timing) for the dominant kernel's algorithmic work
     sc = scenes[-1]
-    if streamed:
+    if streamed or tiled:
         # the streamed kernel runs the same per-(candidate, patch) search as the
         # matrix kernel, plus nvec FMAs per pair for the dwell-time products:
         # operations from the instrumented matrix run on evenly spaced rows
+        # (the tiled matrix: the same without the FMAs)
         rows = np.unique(np.linspace(0, s.nc - 1, min(s.nc, 48)).astype(np.int64))
         ri = torch.from_numpy(rows).to(dev)
         A_s = torch.empty((rows.size, s.np_), dtype=torch.float32, device=dev)
@@ -365,20 +378,27 @@ def run_ours(args):
         ops_s = (cnt["lane_box_tests"] * OPS_BOX_TEST + cnt["lane_tri_tests"] * OPS_TRI_TEST
                  + pairs_s * s.lamp.K * OPS_SEGMENT_SETUP + cnt["lane_wedge_box_tests"] * OPS_WEDGE_BOX_TEST
                  + cnt["lane_wedge_plane_tests"] * OPS_WEDGE_PLANE_TEST)
-        ops = int(ops_s * pairs / pairs_s) + pairs * nvec
+        ops = int(ops_s * pairs / pairs_s) + (pairs * nvec if streamed else 0)
         irr_s = (sum(irr_ms) / len(irr_ms)) * 1e-3
         pk = measured_peaks()
         sm_max = float(pk.get("sm_max_mhz", 2070.0))
         peak = 152 * 128 * sm_max * 1e6 / 1e12
         achieved = ops / irr_s / 1e12
-        traffic = measured_traffic(pairs, STREAMED_SUMMARY)
-        roof = {"bound": "alu", "kernel": "k_streamed", "achieved": round(achieved, 3), "peak": round(peak, 3),
-                "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+        # the tiled matrix has no committed capture of its own (the ward's counters include
+        # the visibility words this workload does not write): traffic unknown
+        traffic = measured_traffic(pairs, STREAMED_SUMMARY) if streamed else None
+        roof = {"bound": "alu", "kernel": "k_streamed" if streamed else "k_irradiance", "achieved": round(achieved, 3),
+                "peak": round(peak, 3), "unit": "Tops/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": f"152 SMs x 128 lanes x {sm_max:.0f} MHz (sm_max_mhz of measured)",
                 "ops_per_launch": ops, "launch_ms": round(irr_s * 1e3, 3),
                 "ops_sample": f"search operations counted on {rows.size} evenly spaced rows (uvc_irradiance_counters) "
-                              f"and scaled to all {s.nc} candidates, plus {nvec} FMAs per pair",
+                              f"and scaled to all {s.nc} candidates" + (f", plus {nvec} FMAs per pair" if streamed
+                                                                        else ""),
                 "counters_sample": cnt}
+        if tiled:
+            roof["launch_ms_note"] = f"all {(s.nc + args.tile - 1) // args.tile} tile launches of one step"
+            if lamp_is_vertical(s.lamp.offsets):
+                roof["memory"] = memory_roofline(uvc, sc, s, irr_s, pairs, pk, vis=False)
     else:
         cnt = uvc.irradiance_counters(sc, d["cand"], lamp, A=A)
         segments = pairs * s.lamp.K
@@ -415,7 +435,8 @@ def run_ours(args):
         "wall_s": round(wall, 3),
     }
     if not args.no_e2e:
-        out["e2e"] = run_e2e(args, s, host, lamp, streamed, nvec, world, dist if world > 1 else None)
+        out["e2e"] = run_e2e(args, s, host, lamp, streamed, nvec, world, dist if world > 1 else None,
+                             tile=args.tile if tiled else 0)
     if world == 1 and args.workload == "ward" and args.bl_rooms > 0 and not args.candidates:
         A = vis = None
         torch.cuda.empty_cache()
@@ -430,22 +451,25 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
 
 
-def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
+def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
     """Same metric through the public API from pinned host buffers: inputs
     copied host->device and results (A, mu, coverage) device->host inside the
-    timed region of every step."""
+    timed region of every step.  With tile > 0 (the tiled large floor) A is
+    computed and copied back tile by tile through one pinned tile buffer."""
     import torch
 
     import paper_2103_14137_gb300 as uvc
     dev = torch.cuda.current_device()
     pin = {k: torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for k, v in host.items()}
     dbuf = {k: torch.empty(v.shape, dtype=v.dtype, device=dev) for k, v in pin.items()}
-    A = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32, device=dev)
-    A_host = None if streamed else torch.empty((s.nc, s.np_), dtype=torch.float32).pin_memory()
+    lda = (s.np_ + 3) // 4 * 4   # padded rows, as in the device-side steps
+    A = None if streamed else torch.empty((s.nc, lda), dtype=torch.float32, device=dev)[:, :s.np_]
+    host_rows = min(s.nc, tile) if tile else s.nc
+    A_host = None if streamed else torch.empty((host_rows, s.np_), dtype=torch.float32).pin_memory()
     mu_host = torch.empty((nvec, s.np_), dtype=torch.float32).pin_memory()
     cov_host = torch.empty((nvec,), dtype=torch.float32).pin_memory()
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
-    d2h = mu_host.numel() * 4 + cov_host.numel() * 4 + (0 if streamed else A_host.numel() * 4)
+    d2h = mu_host.numel() * 4 + cov_host.numel() * 4 + (0 if streamed else s.nc * s.np_ * 4)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -455,6 +479,12 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist):
                              dbuf["excl"])
         if streamed:
             mu = uvc.fluence_streamed(sc, dbuf["cand"], lamp, dbuf["t"])
+        elif tile:
+            for i0 in range(0, s.nc, tile):   # each tile copied back once written (stream order)
+                i1 = min(s.nc, i0 + tile)
+                uvc.irradiance_matrix(sc, dbuf["cand"][i0:i1], lamp, A=A[i0:i1])
+                A_host[:i1 - i0].copy_(A[i0:i1], non_blocking=True)
+            mu = uvc.fluence(sc, A, dbuf["t"])
         else:
             uvc.irradiance_matrix(sc, dbuf["cand"], lamp, A=A)
             mu = uvc.fluence(sc, A, dbuf["t"])

@@ -7,7 +7,10 @@
 // compensation, the quarters in a fixed order (relative error near 36 ulp
 // whatever nc is).  At nvec = 16 the kernel should be bound by the HBM read of
 // A (16 FMA per 4 bytes).
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched through the runtime)
+
 #include <algorithm>
+#include <mutex>
 
 #include "uvc_internal.cuh"
 
@@ -131,6 +134,183 @@ __global__ void __launch_bounds__(256, 2) k_fluence(const float* __restrict__ A,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fluence with the rows of A fed by the tensor-memory accelerator
+// ---------------------------------------------------------------------------
+// The same block shape and summation order as k_fluence (so the same bits),
+// but A does not pass through registers: each row group streams its rows
+// through a ring of kTmaStages shared-memory tiles of kTmaRows x 128 floats,
+// loaded by cp.async.bulk.tensor (one 2-D tensor-map copy per tile, issued by
+// the group's first thread) and completed on an mbarrier per tile.  Up to
+// 4 groups x kTmaStages tiles = 128 KB per SM are in flight without
+// occupying a register, where k_fluence has 16 KB.  The grid is persistent
+// (one block per SM, looping over the 128-column strips).  Needs rows that
+// start on 16-byte boundaries (lda a multiple of 4, A 16-byte aligned); other
+// layouts take k_fluence.  Every wait is bounded: a wait that runs out
+// records UVC_E_TIMEOUT in the scene's status word and the block finishes
+// without further waiting (its results are then invalid).
+constexpr int kTmaRows = 16;                      // rows per tile
+constexpr int kTmaStages = 4;                     // tiles in flight per row group
+constexpr size_t kTmaTileBytes = sizeof(float) * kTmaRows * kFlCols;
+constexpr size_t kTmaSmem = kFlGroups * kTmaStages * kTmaTileBytes   // tiles
+                            + kFluenceSmem                          // dwell times (and the group results)
+                            + kFlGroups * kTmaStages * sizeof(uint64_t);   // mbarriers
+constexpr long long kTmaSpin = 1ll << 26;         // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long k = 0; k < kTmaSpin; ++k) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_tile(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((uint32_t)kTmaTileBytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ CUtensorMap amap, int nc,
+                                                        const float* __restrict__ t, int nvec, int v0,
+                                                        float* __restrict__ mu, int np, int* status) {
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    float* tiles = reinterpret_cast<float*>(tma_smem);
+    float4* tsbase = reinterpret_cast<float4*>(tma_smem + kFlGroups * kTmaStages * kTmaTileBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(tma_smem + kFlGroups * kTmaStages * kTmaTileBytes + kFluenceSmem);
+    const int g = threadIdx.x / kFlGroupThreads, gt = threadIdx.x % kFlGroupThreads;
+    float4* ts = tsbase + (size_t)g * kFlChunk * (kNV / 4);   // [kFlChunk][kNV / 4]
+    float* gtiles = tiles + (size_t)g * kTmaStages * kTmaRows * kFlCols;
+    uint64_t* gbar = bars + g * kTmaStages;
+    const bool producer = gt == 0;
+    if (producer)
+        for (int q = 0; q < kTmaStages; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&gbar[q])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+    const int per = (((nc + kFlGroups - 1) / kFlGroups) + 31) / 32 * 32;
+    const int r0 = min(nc, g * per), r1 = min(nc, r0 + per);
+    const int nst = (r1 - r0 + kTmaRows - 1) / kTmaRows;   // tiles of this group per strip
+    const int nchunk = (per + kFlChunk - 1) / kFlChunk;
+    const int nstrip = (np + kFlCols - 1) / kFlCols;
+    uint32_t issued = 0, consumed = 0;   // tiles issued / consumed by this group over all strips
+    bool ok = true;
+    for (int strip = blockIdx.x; strip < nstrip; strip += gridDim.x) {
+        const int x0 = strip * kFlCols;
+        if (producer) {
+            // the slots were last read through the generic proxy (the previous strip)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            for (int k = 0; k < min(kTmaStages, nst); ++k, ++issued)
+                tma_load_tile(&amap, &gbar[issued % kTmaStages], gtiles + (size_t)(issued % kTmaStages) * kTmaRows * kFlCols,
+                              x0, r0 + k * kTmaRows);
+        }
+        float2 part[kNV], acc[kNV], comp[kNV];
+#pragma unroll
+        for (int v = 0; v < kNV; ++v) {
+            part[v] = make_float2(0.f, 0.f);
+            acc[v] = part[v];
+            comp[v] = part[v];
+        }
+        int k = 0;   // tile of this strip
+        for (int ck = 0; ck < nchunk; ++ck) {
+            const int c0 = r0 + ck * kFlChunk, c1 = min(r1, c0 + kFlChunk);
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kFlGroupThreads) : "memory");
+            float* tsf = reinterpret_cast<float*>(ts);
+            for (int e = gt; e < kFlChunk * kNV; e += kFlGroupThreads) {
+                const int v = e / kFlChunk, q = e % kFlChunk;
+                const int i = c0 + q;
+                tsf[q * kNV + v] = (i < c1 && v0 + v < nvec) ? __ldg(&t[(size_t)(v0 + v) * nc + i]) : 0.f;
+            }
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kFlGroupThreads) : "memory");
+            // the chunk's tiles (a chunk is a whole number of tiles)
+            for (int q0 = 0; q0 < c1 - c0; q0 += kTmaRows, ++k) {
+                const uint32_t slot = consumed % kTmaStages;
+                if (ok && !mbar_wait(&gbar[slot], (consumed / kTmaStages) & 1u)) {
+                    ok = false;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                const float* tile = gtiles + (size_t)slot * kTmaRows * kFlCols + 2 * gt;
+                const int rows = min(kTmaRows, c1 - c0 - q0);
+                for (int u = 0; u < rows; ++u) {
+                    const float2 a = *reinterpret_cast<const float2*>(tile + (size_t)u * kFlCols);
+#pragma unroll
+                    for (int v4 = 0; v4 < kNV / 4; ++v4) {
+                        const float4 w = ts[(q0 + u) * (kNV / 4) + v4];
+                        part[4 * v4 + 0] = __ffma2_rn(make_float2(w.x, w.x), a, part[4 * v4 + 0]);
+                        part[4 * v4 + 1] = __ffma2_rn(make_float2(w.y, w.y), a, part[4 * v4 + 1]);
+                        part[4 * v4 + 2] = __ffma2_rn(make_float2(w.z, w.z), a, part[4 * v4 + 2]);
+                        part[4 * v4 + 3] = __ffma2_rn(make_float2(w.w, w.w), a, part[4 * v4 + 3]);
+                    }
+                    const int q = q0 + u;
+                    if (((q + 1) & 31) == 0 || q + 1 == c1 - c0) {   // a block of 32 rows ends
+#pragma unroll
+                        for (int v = 0; v < kNV; ++v) {
+                            kahan_add(acc[v].x, comp[v].x, part[v].x);
+                            kahan_add(acc[v].y, comp[v].y, part[v].y);
+                            part[v] = make_float2(0.f, 0.f);
+                        }
+                    }
+                }
+                ++consumed;
+                // every thread of the group is done with the slot: refill it
+                asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(kFlGroupThreads) : "memory");
+                if (producer && k + kTmaStages < nst) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tma_load_tile(&amap, &gbar[issued % kTmaStages],
+                                  gtiles + (size_t)(issued % kTmaStages) * kTmaRows * kFlCols, x0,
+                                  r0 + (k + kTmaStages) * kTmaRows);
+                    ++issued;
+                }
+            }
+        }
+        // fixed-order (group 0..3) compensated sum of the group results
+        __syncthreads();
+        float2* red = reinterpret_cast<float2*>(tsbase);   // [kFlGroups][kNV][kFlGroupThreads]
+#pragma unroll
+        for (int v = 0; v < kNV; ++v)
+            red[((size_t)g * kNV + v) * kFlGroupThreads + gt] =
+                make_float2(__fsub_rn(acc[v].x, comp[v].x), __fsub_rn(acc[v].y, comp[v].y));
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kNV * kFlGroupThreads; idx += blockDim.x) {
+            const int v = idx / kFlGroupThreads, l = idx % kFlGroupThreads;
+            const int jj = x0 + 2 * l;
+            if (v0 + v >= nvec) continue;
+            float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+            for (int w = 0; w < kFlGroups; ++w) {
+                const float2 x = red[((size_t)w * kNV + v) * kFlGroupThreads + l];
+                kahan_add(s0, c0, x.x);
+                kahan_add(s1, c1, x.y);
+            }
+            if (jj < np) mu[(size_t)(v0 + v) * np + jj] = s0;
+            if (jj + 1 < np) mu[(size_t)(v0 + v) * np + jj + 1] = s1;
+        }
+        __syncthreads();
+    }
+    // copies still in flight (only after a wait gave up): wait for them, bounded
+    if (producer)
+        while (consumed < issued) {
+            mbar_wait(&gbar[consumed % kTmaStages], (consumed / kTmaStages) & 1u);
+            ++consumed;
+        }
+}
+
 // Deterministic block sum of (float with Kahan terms, count).
 __device__ void block_reduce(float& s, unsigned long long& cnt) {
     __shared__ float ss[32];
@@ -191,6 +371,45 @@ void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream
     k_area_total<<<1, 1024, 0, stream>>>(patch_s, (int)np, out);
 }
 
+namespace {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry points (the
+// library does not link the driver library itself); nullptr if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+// The tensor map of A (nc rows of lda floats, np used) for kTmaRows x 128
+// tiles; false when the layout does not allow one (rows not 16-byte aligned).
+bool fluence_tensor_map(const float* A, int64_t nc, int64_t lda, int np, CUtensorMap* map) {
+    if (lda % 4 != 0 || reinterpret_cast<uintptr_t>(A) % 16 != 0 || np < 1 || nc < 1) return false;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)nc};
+    const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kFlCols, (cuuint32_t)kTmaRows};
+    const cuuint32_t estride[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
             float* mu, cudaStream_t stream) {
     const int np = (int)sc->np;
@@ -198,6 +417,18 @@ int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const 
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, sizeof(float) * (size_t)nvec * np, stream));
     static_assert(sizeof(float2) * kFlGroups * kNV * kFlGroupThreads <= kFluenceSmem, "group results fit");
     static_assert(kFlGroups * kFlGroupThreads == kThreads, "block shape");
+    static_assert(kFlChunk % kTmaRows == 0 && kTmaRows * kFlCols * sizeof(float) % 128 == 0, "tile shape");
+    CUtensorMap map;
+    if (fluence_tensor_map(A, nc, lda, np, &map)) {
+        static const cudaError_t tattr =
+            cudaFuncSetAttribute(k_fluence_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
+        if (tattr != cudaSuccess) return status_from_cuda(tattr);
+        const int nstrip = (np + kFlCols - 1) / kFlCols;
+        const int grid = std::min(nstrip, sm_count());
+        for (int v0 = 0; v0 < nvec; v0 += kNV)
+            k_fluence_tma<<<grid, kThreads, kTmaSmem, stream>>>(map, (int)nc, t, nvec, v0, mu, np, sc->status);
+        return status_from_cuda(cudaGetLastError());
+    }
     // once per process (and so not during a stream capture that follows a first call)
     static const cudaError_t attr =
         cudaFuncSetAttribute(k_fluence, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFluenceSmem);

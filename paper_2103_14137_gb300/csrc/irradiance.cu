@@ -67,8 +67,11 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(Sce
 }
 
 // Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
-// E values of up to 32 candidates are staged in shared memory, multiplied by
-// the dwell times and added to the chunk's partial sums partial[s][v][j].
+// E values of up to kStreamedBlock candidates are staged in shared memory,
+// multiplied by the dwell times and added to the chunk's partial sums
+// partial[s][v][j].  24 candidates per stage keeps a K = 8 lamp's block within
+// a third of an SM's shared memory (three resident blocks).
+constexpr int kStreamedBlock = 24;
 template <bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,
@@ -77,9 +80,9 @@ __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
     char* after_stacks = reinterpret_cast<char*>(smem) + stack_smem_bytes(S.stack_cap);
-    float* Et = reinterpret_cast<float*>(after_stacks) + warp * 32 * 32;
+    float* Et = reinterpret_cast<float*>(after_stacks) + warp * kStreamedBlock * 32;
     WedgeSmem ws;
-    if (WEDGE) ws = wedge_smem(after_stacks + sizeof(float) * kWarpsPerBlock * 32 * 32, L.K, warp);
+    if (WEDGE) ws = wedge_smem(after_stacks + sizeof(float) * kWarpsPerBlock * kStreamedBlock * 32, L.K, warp);
     const int njb = (S.np + 31) >> 5;
     const int64_t ntask = (int64_t)nsplit * njb;
     for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
@@ -89,8 +92,8 @@ __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(
         const PatchLane P = load_patch(S, j);
         int cache = -1;
         const int i0 = s * chunk, i1 = min(nc, i0 + chunk);
-        for (int ib = i0; ib < i1; ib += 32) {
-            const int nb = min(32, i1 - ib);
+        for (int ib = i0; ib < i1; ib += kStreamedBlock) {
+            const int nb = min(kStreamedBlock, i1 - ib);
             for (int q = 0; q < nb; ++q)
                 Et[q * 32 + lane] =
                     WEDGE ? irradiance_wedge(S, cand, nc, L, ib + q, jb, lane, stack, ws, nullptr, 0, P, cache)
@@ -142,7 +145,7 @@ int allow_smem(const void* kernel, size_t smem) {
 
 // k_streamed for this lamp: shared memory, grid, launch.
 size_t streamed_smem(const SceneView& S, const LampDev& lamp) {
-    return stack_smem_bytes(S.stack_cap) + sizeof(float) * kWarpsPerBlock * 32 * 32 +
+    return stack_smem_bytes(S.stack_cap) + sizeof(float) * kWarpsPerBlock * kStreamedBlock * 32 +
            (lamp.wedge ? wedge_smem_bytes(lamp.K) : 0);
 }
 

@@ -112,11 +112,12 @@ def replay(exported: dict, cand, lamp_offsets, tasks, cand_per_task: int = 4, th
     return dict(zip(COUNTERS, (int(x) for x in out)))
 
 
-def bytes_per_pair(c: dict, K: int) -> dict:
+def bytes_per_pair(c: dict, K: int, vis: bool = True) -> dict:
     """Algorithmic bytes per pair from replay counters (per warp: fetched by
-    the warp's loads; per lane: summed over the lanes that need them)."""
+    the warp's loads; per lane: summed over the lanes that need them); the
+    output is 4 B of A plus, when the visibility words are written, K bits."""
     pairs = max(1, c["pairs"])
-    out_b = 4.0 + K / 8.0
+    out_b = 4.0 + (K / 8.0 if vis else 0.0)
     per_warp = (c["node_visits"] * NODE_BYTES + c["leaf_step_unique"] * TRI_BYTES + c["cache_loads"] * TRI_BYTES
                 + c["tasks"] * 32 * PATCH_BYTES) / pairs + out_b
     per_lane = (c["lane_node_visits"] * NODE_BYTES + c["leaf_loads"] * TRI_BYTES + c["cache_loads"] * TRI_BYTES

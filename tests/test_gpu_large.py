@@ -69,3 +69,39 @@ def test_large_streamed_properties(large):
     scale = np.maximum(np.abs(a), 1e-30)
     assert np.max(np.abs(a - m) / scale) <= 1e-5            # streamed == materialised
     assert np.max(np.abs(c - (a + b)) / np.maximum(c, 1e-30)) <= 1e-5   # linear in t
+
+
+def test_large_tiled_matrix_whole_rows_against_bvh_oracle(large):
+    """The full 10,000 x 994,000 matrix of the large floor (40 GB) written tile
+    by tile (500 candidates per call, row slices of one buffer), as the
+    benchmark's tiled workload does; one whole row from each of 8 tiles is
+    recomputed with its visibility words (bitwise the tiled row) and checked
+    against the oracle's CPU-BVH mode: visibility exact except on grazing
+    pairs, entries within 1e-5."""
+    s, sc = large
+    tile = 500
+    lamp = lamp_of(s.lamp)
+    cand = T(s.cand)
+    A = torch.empty((s.nc, s.np_), dtype=torch.float32, device="cuda")
+    for i0 in range(0, s.nc, tile):
+        uvc.irradiance_matrix(sc, cand[i0:i0 + tile], lamp, A=A[i0:i0 + tile])
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    tiles = np.array([0, 2, 5, 7, 11, 13, 16, 19])
+    rows = tiles * tile + (37 * tiles + 11) % tile
+    ri = torch.from_numpy(rows).cuda()
+    Ar, vis = uvc.irradiance_matrix(sc, cand.index_select(0, ri).contiguous(), lamp, with_vis=True)
+    torch.cuda.synchronize()
+    assert torch.equal(Ar, A.index_select(0, ri))
+    del A
+    torch.cuda.empty_cache()
+    pairs = np.stack([np.repeat(rows, s.np_), np.tile(np.arange(s.np_), rows.size)], axis=1)
+    E, ovis, _ = oracle.irradiance_scene(s, pairs=pairs, bvh=True, flags=False)
+    visg = uvc.vis_to_bool(vis, s.np_).reshape(-1, s.lamp.K)
+    flag = np.zeros(pairs.shape[0], np.uint8)
+    diff = np.flatnonzero((visg != ovis.astype(bool)).any(axis=1))
+    if diff.size:
+        _, _, f = oracle.irradiance_scene(s, pairs=pairs[diff])
+        flag[diff] = f
+    st = compare_irradiance(Ar.cpu().numpy().reshape(-1), visg, E, ovis, flag)
+    assert st["pairs"] == 8 * s.np_ and st["visible_frac"] > 0.01
