@@ -221,13 +221,19 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
                 tma_load_tile(&amap, &gbar[issued % kTmaStages], gtiles + (size_t)(issued % kTmaStages) * kTmaRows * kFlCols,
                               x0, r0 + k * kTmaRows);
         }
-        float2 part[kNV], acc[kNV], comp[kNV];
+        // accumulators of column c (0, 1) hold the vector pairs (2p, 2p + 1): the
+        // dwell times of two vectors are adjacent in a 16-byte broadcast, so
+        // each packed FMA takes them as they are and only the A value is paired
+        // with itself (same terms, same order as k_fluence for every vector and column)
+        float2 part[2][kNV / 2], acc[2][kNV / 2], comp[2][kNV / 2];
 #pragma unroll
-        for (int v = 0; v < kNV; ++v) {
-            part[v] = make_float2(0.f, 0.f);
-            acc[v] = part[v];
-            comp[v] = part[v];
-        }
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int p = 0; p < kNV / 2; ++p) {
+                part[c][p] = make_float2(0.f, 0.f);
+                acc[c][p] = part[c][p];
+                comp[c][p] = part[c][p];
+            }
         int k = 0;   // tile of this strip
         for (int ck = 0; ck < nchunk; ++ck) {
             const int c0 = r0 + ck * kFlChunk, c1 = min(r1, c0 + kFlChunk);
@@ -248,24 +254,29 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
                 }
                 const float* tile = gtiles + (size_t)slot * kTmaRows * kFlCols + 2 * gt;
                 const int rows = min(kTmaRows, c1 - c0 - q0);
+#pragma unroll 4
                 for (int u = 0; u < rows; ++u) {
                     const float2 a = *reinterpret_cast<const float2*>(tile + (size_t)u * kFlCols);
+                    const float2 a0 = make_float2(a.x, a.x), a1 = make_float2(a.y, a.y);
 #pragma unroll
                     for (int v4 = 0; v4 < kNV / 4; ++v4) {
                         const float4 w = ts[(q0 + u) * (kNV / 4) + v4];
-                        part[4 * v4 + 0] = __ffma2_rn(make_float2(w.x, w.x), a, part[4 * v4 + 0]);
-                        part[4 * v4 + 1] = __ffma2_rn(make_float2(w.y, w.y), a, part[4 * v4 + 1]);
-                        part[4 * v4 + 2] = __ffma2_rn(make_float2(w.z, w.z), a, part[4 * v4 + 2]);
-                        part[4 * v4 + 3] = __ffma2_rn(make_float2(w.w, w.w), a, part[4 * v4 + 3]);
+                        const float2 w01 = make_float2(w.x, w.y), w23 = make_float2(w.z, w.w);
+                        part[0][2 * v4] = __ffma2_rn(w01, a0, part[0][2 * v4]);
+                        part[0][2 * v4 + 1] = __ffma2_rn(w23, a0, part[0][2 * v4 + 1]);
+                        part[1][2 * v4] = __ffma2_rn(w01, a1, part[1][2 * v4]);
+                        part[1][2 * v4 + 1] = __ffma2_rn(w23, a1, part[1][2 * v4 + 1]);
                     }
                     const int q = q0 + u;
                     if (((q + 1) & 31) == 0 || q + 1 == c1 - c0) {   // a block of 32 rows ends
 #pragma unroll
-                        for (int v = 0; v < kNV; ++v) {
-                            kahan_add(acc[v].x, comp[v].x, part[v].x);
-                            kahan_add(acc[v].y, comp[v].y, part[v].y);
-                            part[v] = make_float2(0.f, 0.f);
-                        }
+                        for (int c = 0; c < 2; ++c)
+#pragma unroll
+                            for (int p = 0; p < kNV / 2; ++p) {
+                                kahan_add(acc[c][p].x, comp[c][p].x, part[c][p].x);
+                                kahan_add(acc[c][p].y, comp[c][p].y, part[c][p].y);
+                                part[c][p] = make_float2(0.f, 0.f);
+                            }
                     }
                 }
                 ++consumed;
@@ -282,11 +293,14 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
         }
         // fixed-order (group 0..3) compensated sum of the group results
         __syncthreads();
-        float2* red = reinterpret_cast<float2*>(tsbase);   // [kFlGroups][kNV][kFlGroupThreads]
+        float2* red = reinterpret_cast<float2*>(tsbase);   // [kFlGroups][kNV][kFlGroupThreads]: (col 0, col 1)
 #pragma unroll
-        for (int v = 0; v < kNV; ++v)
-            red[((size_t)g * kNV + v) * kFlGroupThreads + gt] =
-                make_float2(__fsub_rn(acc[v].x, comp[v].x), __fsub_rn(acc[v].y, comp[v].y));
+        for (int p = 0; p < kNV / 2; ++p) {
+            red[((size_t)g * kNV + 2 * p) * kFlGroupThreads + gt] =
+                make_float2(__fsub_rn(acc[0][p].x, comp[0][p].x), __fsub_rn(acc[1][p].x, comp[1][p].x));
+            red[((size_t)g * kNV + 2 * p + 1) * kFlGroupThreads + gt] =
+                make_float2(__fsub_rn(acc[0][p].y, comp[0][p].y), __fsub_rn(acc[1][p].y, comp[1][p].y));
+        }
         __syncthreads();
         for (int idx = threadIdx.x; idx < kNV * kFlGroupThreads; idx += blockDim.x) {
             const int v = idx / kFlGroupThreads, l = idx % kFlGroupThreads;

@@ -69,9 +69,9 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(Sce
 // Streamed fluence, pass 1: warp task = (candidate chunk s, patch block jb).
 // E values of up to kStreamedBlock candidates are staged in shared memory,
 // multiplied by the dwell times and added to the chunk's partial sums
-// partial[s][v][j].  24 candidates per stage keeps a K = 8 lamp's block within
+// partial[s][v][j].  20 candidates per stage keeps a K = 8 lamp's block within
 // a third of an SM's shared memory (three resident blocks).
-constexpr int kStreamedBlock = 24;
+constexpr int kStreamedBlock = 20;
 template <bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,

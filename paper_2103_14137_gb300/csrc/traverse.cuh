@@ -564,9 +564,11 @@ __device__ __forceinline__ void wedge_pair_hits(const WedgeLane& w, float2 nx, f
 #ifndef UVC_LEAF_FLUSH
 #define UVC_LEAF_FLUSH 24
 #endif
-constexpr int kLeafQueue = 128;       // ring entries per warp (a node adds at most 4 x 32: see the guard)
+constexpr int kLeafQueue = 256;       // ring entries per warp (< kLeafFlush waiting + at most 4 x 32 new)
 constexpr int kLeafBatch = 32;        // items per batch: one per lane
 constexpr int kLeafFlush = UVC_LEAF_FLUSH;
+static_assert(kLeafFlush - 1 + 4 * 32 <= kLeafQueue && (kLeafQueue & (kLeafQueue - 1)) == 0,
+              "the ring holds the waiting items plus one node's");
 constexpr uint32_t kOobBit = 0x80000000u;   // checked build: a leaf index out of range (sources use bits 0..15)
 constexpr int kItemLeafBits = 27;
 constexpr uint32_t kItemLeafMask = (1u << kItemLeafBits) - 1u;
@@ -741,15 +743,8 @@ __device__ __forceinline__ void wedge_traverse(const SceneView& S, const LampDev
             const unsigned cnt = __popc(mine), lt = (1u << lane) - 1u;
             const unsigned b0 = __ballot_sync(kFull, cnt & 1u), b1 = __ballot_sync(kFull, cnt & 2u),
                            b2 = __ballot_sync(kFull, cnt & 4u);
-            const int add = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
-            if (tail - head + add > kLeafQueue) {
-                // rare (more than 104 new items): work off the waiting ones first so the ring cannot overflow
-                wedge_leaf_batch<COUNT>(S, L, w, want, lane, ws, head, tail - head, cx, cy, cz, sz, gx, gy, mh, ex0,
-                                        ex1, c_leaf, c_tri, hit_tri, oob);
-                head = tail;
-            }
             int pos = tail + __popc(b0 & lt) + 2 * __popc(b1 & lt) + 4 * __popc(b2 & lt);
-            tail += add;
+            tail += __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
             for (unsigned m = mine; m; m &= m - 1) {
                 ws.qitem[pos & (kLeafQueue - 1)] = ((uint32_t)lane << kItemLeafBits) | (uint32_t)~pick4(rr, __ffs(m) - 1);
                 ++pos;

@@ -271,7 +271,7 @@ typedef struct {
     wedge_t w;
 } lane_t;
 
-#define QCAP 128
+#define QCAP 256
 #define QBATCH 32
 #ifndef QFLUSH
 #define QFLUSH 24   /* the kernels' kLeafFlush */
@@ -434,12 +434,6 @@ static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float 
             hit |= nib[l];
         }
         if (hit & (unsigned)nd->m[0]) {
-            int add = 0;
-            for (int l = 0; l < 32; ++l) add += __builtin_popcount(nib[l] & (unsigned)nd->m[0]);
-            if (tail - head + add > QCAP) {   /* the kernels' overflow guard */
-                leaf_batch(S, L, ln, qlane, qleaf, head, tail - head, cx, cy, cz, C);
-                head = tail;
-            }
             for (int l = 0; l < 32; ++l)
                 for (unsigned b = nib[l] & (unsigned)nd->m[0]; b; b &= b - 1) {
                     qlane[tail & (QCAP - 1)] = l;
