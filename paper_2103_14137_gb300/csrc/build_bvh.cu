@@ -396,14 +396,14 @@ __global__ void k_node_depth(int n, const int* __restrict__ parent_int, const in
 // "Fast Parallel Construction of High-Quality Bounding Volume Hierarchies",
 // HPG 2013).  Cost of a subtree: C_i * area + children's costs; of a leaf:
 // C_t * area.  The set of triangles under every treelet root is unchanged, so
-// its box is too; only nodes inside the treelet are rewired.  One pass: on the
-// ward, passes 2 and 3 cost 2.1 ms each and save under 1 % of the traversal.
-// Treelets of 5 leaves: the dynamic programme over subsets costs about a
-// ninth of 7 leaves' (the pass takes ~0.3 ms instead of 2.3 ms on the ward)
-// and the traversal is as fast (ward matrix 75.4 ms with 5, 75.3 with 6, 75.6
-// with 7 leaves).
+// its box is too; only nodes inside the treelet are rewired.  Treelets of 5
+// leaves: the dynamic programme over subsets costs about a ninth of 7
+// leaves' (a pass takes ~0.3 ms instead of 2.3 ms on the ward) and one pass
+// gives as fast a traversal (ward matrix 75.4 ms with 5, 75.3 with 6, 75.6
+// with 7 leaves, 76.1 with 4); a second pass of 5-leaf treelets cuts node
+// visits by 3 % (74.0 ms).
 constexpr int kTreelet = 5;
-constexpr int kRestructurePasses = 1;
+constexpr int kRestructurePasses = 2;
 constexpr float kCostNode = 1.2f, kCostTri = 1.0f;
 
 __device__ __forceinline__ float half_area(float4 lo, float4 hi) {
@@ -552,8 +552,89 @@ __global__ void k_restructure(int n, TreeView T, const int* __restrict__ leaf_pa
     }
 }
 
+// Collapse to the four-wide tree, top down, one level of four-wide nodes per
+// launch: a four-wide node (kept at the index of the binary node it starts
+// from) takes that node's two children and, while it has fewer than four,
+// replaces the internal child of largest surface area by its two children
+// (in place, so the slots keep the binary tree's left-to-right order); its
+// internal children are the next level's four-wide nodes.  Fuller nodes than
+// taking the grandchildren of every node at even depth (a leaf child there
+// leaves a slot empty): on the ward, 4 % fewer node visits per query.
+__device__ __forceinline__ float box_half_area(const float* lo, const float* hi) {
+    const float dx = fmaxf(hi[0] - lo[0], 0.f), dy = fmaxf(hi[1] - lo[1], 0.f), dz = fmaxf(hi[2] - lo[2], 0.f);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void k_collapse_level(const Node* __restrict__ nodes, const int* __restrict__ fin,
+                                 const int* __restrict__ nin, int* __restrict__ fout, int* __restrict__ nout,
+                                 Node4* __restrict__ nodes4) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= *nin) return;
+    const int i = fin[k];
+    int ref[4];
+    float lo[4][3], hi[4][3];
+    int cnt = 0;
+    auto kids = [&](int b, int at) {   // the two children of binary node b into slots at, at + 1
+        const Node nd = nodes[b];
+        ref[at] = nd.r.x;
+        ref[at + 1] = nd.r.y;
+        lo[at][0] = nd.x.x; lo[at][1] = nd.y.x; lo[at][2] = nd.z.x;
+        hi[at][0] = nd.x.z; hi[at][1] = nd.y.z; hi[at][2] = nd.z.z;
+        lo[at + 1][0] = nd.x.y; lo[at + 1][1] = nd.y.y; lo[at + 1][2] = nd.z.y;
+        hi[at + 1][0] = nd.x.w; hi[at + 1][1] = nd.y.w; hi[at + 1][2] = nd.z.w;
+    };
+    kids(i, 0);
+    cnt = 2;
+    while (cnt < 4) {
+        int best = -1;
+        float ba = -1.f;
+        for (int q = 0; q < cnt; ++q)
+            if (ref[q] >= 0) {
+                const float a = box_half_area(lo[q], hi[q]);
+                if (a > ba) { ba = a; best = q; }
+            }
+        if (best < 0) break;
+        const int b = ref[best];
+        for (int q = cnt - 1; q > best; --q) {   // make room: slots after best move up by one
+            ref[q + 1] = ref[q];
+            for (int a = 0; a < 3; ++a) { lo[q + 1][a] = lo[q][a]; hi[q + 1][a] = hi[q][a]; }
+        }
+        kids(b, best);
+        ++cnt;
+    }
+    const float far = 1e30f;
+    for (int q = cnt; q < 4; ++q) {
+        ref[q] = kEmptyChild;
+        for (int a = 0; a < 3; ++a) { lo[q][a] = far; hi[q][a] = far; }
+    }
+    Node4 o;
+    for (int h = 0; h < 2; ++h)
+        for (int a = 0; a < 3; ++a)
+            o.q[3 * h + a] = make_float4(lo[2 * h][a], lo[2 * h + 1][a], hi[2 * h][a], hi[2 * h + 1][a]);
+    o.r = make_int4(ref[0], ref[1], ref[2], ref[3]);
+    int leafmask = 0, innermask = 0, ninner = 0;
+    for (int c = 0; c < 4; ++c) {
+        if (ref[c] < 0) leafmask |= 1 << c;
+        else if (ref[c] != kEmptyChild) { innermask |= 1 << c; ++ninner; }
+    }
+    o.m = make_int4(leafmask, innermask, 0, 0);
+    nodes4[i] = o;
+    if (ninner) {
+        int at = atomicAdd(nout, ninner);
+        for (int c = 0; c < 4; ++c)
+            if ((innermask >> c) & 1) fout[at++] = ref[c];
+    }
+}
+
+__global__ void k_collapse_start(int* frontier, int* counters, int nlevels) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nlevels) counters[k] = k == 0 ? 1 : 0;
+    if (k == 0) frontier[0] = 0;
+}
+
 // Collapse to the four-wide tree: every internal node at even depth gets a
 // four-wide node holding its children (leaf children) or grandchildren.
+// (Kept for UVC_BUILD_LBVH_ONLY, whose four-wide tree the LBVH tests know.)
 __global__ void k_collapse4(int n, const Node* __restrict__ nodes, const int* __restrict__ depth,
                             Node4* __restrict__ nodes4) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -885,7 +966,8 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
                     3 * align256(sizeof(int) * (size_t)ni) +                 // height, flags, depth
                     align256(sizeof(float) * (size_t)ni) +                   // subtree cost
                     align256(sizeof(int) * (size_t)n) +                      // leaf parents at pass start
-                    align256(sizeof(unsigned int) * 12) + align256(sizeof(int) * 2) + 256;
+                    align256(sizeof(unsigned int) * 12) + align256(sizeof(int) * 2) +
+                    align256(sizeof(int) * ((size_t)n + 2)) + 256;                    // collapse level counters
     void* tblock = nullptr;
     if (cudaMallocAsync(&tblock, tbytes, stream) != cudaSuccess) {
         cudaGetLastError();
@@ -916,6 +998,7 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     int* leaf_parent0 = tc.take<int>(n);
     unsigned int* bounds = tc.take<unsigned int>(12);   // reference points lo/hi, triangle boxes lo/hi
     int* errdepth = tc.take<int>(2);   // [0] = error bits, [1] = depth
+    int* level_counts = tc.take<int>((size_t)n + 2);   // four-wide nodes per level of the collapse
 
     cudaError_t e = cudaSuccess;
     unsigned int init_bounds[12] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u,
@@ -964,7 +1047,8 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
             k_pack_nodes<<<(ni + B - 1) / B, B, 0, stream>>>(n, children, parent_int, leaf_lo, leaf_hi, node_lo,
                                                              node_hi, sc->nodes);
             k_node_depth<<<(ni + B - 1) / B, B, 0, stream>>>(n, parent_int, children, ndepth, errdepth + 1);
-            k_collapse4<<<(ni + B - 1) / B, B, 0, stream>>>(n, sc->nodes, ndepth, sc->nodes4);
+            if (flags_in & UVC_BUILD_LBVH_ONLY)
+                k_collapse4<<<(ni + B - 1) / B, B, 0, stream>>>(n, sc->nodes, ndepth, sc->nodes4);
         }
         e = cudaGetLastError();
     }
@@ -987,6 +1071,24 @@ int build_scene(const float* verts, int64_t nv, const int32_t* tris, int64_t nt,
     if (host_ed[0] != 0) return fail(UVC_E_INVAL);
     sc->depth = host_ed[1];
     sc->depth4 = (sc->depth + 1) / 2;
+    if (n > 1 && !(flags_in & UVC_BUILD_LBVH_ONLY)) {
+        // the greedy collapse, one launch per level of four-wide nodes; a path
+        // of the four-wide tree advances at least one binary level per node,
+        // so it has at most `depth` levels (the bound the stacks are sized by)
+        sc->depth4 = sc->depth;
+        int* fa = height;
+        int* fb = flags;
+        int* counters = level_counts;   // depth + 2 <= n + 1 counters
+        const int nlev = sc->depth + 1;
+        k_collapse_start<<<(nlev + 1 + B - 1) / B, B, 0, stream>>>(fa, counters, nlev + 1);
+        for (int L = 0; L < nlev; ++L) {
+            const int64_t bound = L < 15 ? std::min<int64_t>(ni, int64_t(1) << (2 * L)) : ni;
+            k_collapse_level<<<(int)((bound + B - 1) / B), B, 0, stream>>>(sc->nodes, L & 1 ? fb : fa, counters + L,
+                                                                         L & 1 ? fa : fb, counters + L + 1,
+                                                                         sc->nodes4);
+        }
+        if (cudaGetLastError() != cudaSuccess) return fail(UVC_E_CUDA);
+    }
     float diam = 0.f;
     if (n > 0) {
         double d2 = 0.0, cmax = 0.0;

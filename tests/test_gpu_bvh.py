@@ -127,3 +127,55 @@ def test_restructured_tree_gives_identical_matrix():
     assert torch.equal(A0, A1) and torch.equal(v0, v1)
     sc0.free()
     sc1.free()
+
+
+def test_four_wide_tree_covers_every_triangle_once():
+    """The four-wide tree the traversal reads (uvc_scene_export_traversal): from
+    the root every triangle is reached exactly once, empty slots carry no
+    child, and every child box holds the triangles below it."""
+    import paper_2103_14137_gb300 as uvc
+    s = ward_room(n_cand=4)
+    for lbvh_only in (False, True):
+        sc = build(s, lbvh_only=lbvh_only)
+        ex = uvc.scene_export_traversal(sc)
+        words = ex["nodes4"]
+        q = words[:, :24].view(np.float32).reshape(-1, 6, 4)
+        ref = words[:, 24:28].view(np.int32)
+        mask = words[:, 28:30].view(np.int32)
+        tri = ex["tri"]
+        seen = np.zeros(s.nt, np.int64)
+        EMPTY = 0x7fffffff
+
+        def child_box(i, c):
+            h, k = divmod(c, 2)
+            lo = np.array([q[i, 3 * h + a, k] for a in range(3)])
+            hi = np.array([q[i, 3 * h + a, 2 + k] for a in range(3)])
+            return lo, hi
+
+        def visit(i, depth):
+            lo_all, hi_all = np.full(3, np.inf), np.full(3, -np.inf)
+            for c in range(4):
+                r = int(ref[i, c])
+                is_leaf, is_inner = (mask[i, 0] >> c) & 1, (mask[i, 1] >> c) & 1
+                if r == EMPTY:
+                    assert not is_leaf and not is_inner
+                    continue
+                lo, hi = child_box(i, c)
+                if r < 0:
+                    assert is_leaf and not is_inner
+                    k = ~r
+                    seen[k] += 1
+                    v = tri[k, :, :3]
+                    tlo, thi = v.min(axis=0), v.max(axis=0)
+                else:
+                    assert is_inner and not is_leaf
+                    tlo, thi = visit(r, depth + 1)
+                assert np.all(lo <= tlo) and np.all(hi >= thi), (i, c)
+                lo_all, hi_all = np.minimum(lo_all, tlo), np.maximum(hi_all, thi)
+            return lo_all, hi_all
+
+        import sys
+        sys.setrecursionlimit(100000)
+        visit(0, 0)
+        assert np.all(seen == 1)
+        sc.free()
