@@ -42,6 +42,7 @@ UNIT = "Gpairs/s"
 MU_MIN = 100.0          # 10 mJ/cm^2
 NVEC = 16
 BL_STEPS = 3            # timed steps of each pipeline in the rooms-per-second block
+E2E_TILE = 500          # candidates per tile of A in the end-to-end steps (copied back while the next is computed)
 BL_QUALITY_JOBS = 8     # timed jobs (seeded subset) whose proposal quality is measured
 L2_BYTES = 129 * 2 ** 20
 # ALU work per operation of the traversal (FP32 arithmetic, min/max, compare
@@ -455,7 +456,10 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
     """Same metric through the public API from pinned host buffers: inputs
     copied host->device and results (A, mu, coverage) device->host inside the
     timed region of every step.  With tile > 0 (the tiled large floor) A is
-    computed and copied back tile by tile through one pinned tile buffer."""
+    computed and copied back tile by tile through one pinned tile buffer.
+    Otherwise A is computed in row tiles of E2E_TILE candidates and each tile
+    is copied back on a second stream while the next one is computed (the
+    step ends when every copy has)."""
     import torch
 
     import paper_2103_14137_gb300 as uvc
@@ -471,6 +475,8 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
     h2d = sum(v.numel() * v.element_size() for v in pin.values())
     d2h = mu_host.numel() * 4 + cov_host.numel() * 4 + (0 if streamed else s.nc * s.np_ * 4)
     stream = torch.cuda.current_stream()
+    copy_stream = torch.cuda.Stream()
+    pipelined = not streamed and not tile
 
     def step():
         for k in pin:
@@ -485,6 +491,16 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
                 uvc.irradiance_matrix(sc, dbuf["cand"][i0:i1], lamp, A=A[i0:i1])
                 A_host[:i1 - i0].copy_(A[i0:i1], non_blocking=True)
             mu = uvc.fluence(sc, A, dbuf["t"])
+        elif pipelined:
+            for i0 in range(0, s.nc, E2E_TILE):
+                i1 = min(s.nc, i0 + E2E_TILE)
+                uvc.irradiance_matrix(sc, dbuf["cand"][i0:i1], lamp, A=A[i0:i1])
+                ready = torch.cuda.Event()
+                ready.record(stream)
+                copy_stream.wait_event(ready)
+                with torch.cuda.stream(copy_stream):
+                    A_host[i0:i1].copy_(A[i0:i1], non_blocking=True)
+            mu = uvc.fluence(sc, A, dbuf["t"])
         else:
             uvc.irradiance_matrix(sc, dbuf["cand"], lamp, A=A)
             mu = uvc.fluence(sc, A, dbuf["t"])
@@ -492,6 +508,10 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
         ca, _ = uvc.coverage(sc, mu, MU_MIN)
         mu_host.copy_(mu, non_blocking=True)
         cov_host.copy_(ca, non_blocking=True)
+        if pipelined:
+            done = torch.cuda.Event()
+            done.record(copy_stream)
+            stream.wait_event(done)   # the step's end includes the last tile's copy
         return sc
 
     for _ in range(max(1, args.warmup)):
@@ -508,7 +528,10 @@ def run_e2e(args, s, host, lamp, streamed, nvec, world, dist, tile=0):
     ms = max_over_ranks(a.elapsed_time(b) / n, dist, dev)
     return {"value": round(job_value(s.nc * s.np_, world, ms), 4), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3),
-            "steps": n}
+            "steps": n, "a_copy": ("row tiles of %d candidates copied on a second stream while the next tile is "
+                                   "computed" % E2E_TILE) if pipelined else ("tile by tile" if tile else
+                                                                              ("none (A not stored)" if streamed
+                                                                               else "after the matrix"))}
 
 
 _KERNEL_FILES = ("irradiance.cu", "traverse.cuh", "uvc_internal.cuh")
