@@ -101,9 +101,9 @@ __device__ __forceinline__ void setup_ray(Ray& r) {
     float dkz = pick(r.dx, r.dy, r.dz, kz);
     if (dkz < 0.f) { int t = kx; kx = ky; ky = t; }
     r.kx = kx; r.ky = ky; r.kz = kz;
-    r.sx = __fdiv_rn(pick(r.dx, r.dy, r.dz, kx), dkz);
-    r.sy = __fdiv_rn(pick(r.dx, r.dy, r.dz, ky), dkz);
-    r.sz = __fdiv_rn(1.0f, dkz);
+    r.sz = __frcp_rn(dkz);   // the shear constants need no particular rounding, only one value per segment
+    r.sx = __fmul_rn(pick(r.dx, r.dy, r.dz, kx), r.sz);
+    r.sy = __fmul_rn(pick(r.dx, r.dy, r.dz, ky), r.sz);
 }
 
 __device__ __forceinline__ float max3f(float a, float b, float c) {
@@ -462,7 +462,7 @@ __device__ __forceinline__ float irradiance_entry(const SceneView& S, const floa
 // searching sources.
 
 struct WedgeLane {
-    float2 oxn, oxf, oyn, oyf;   // -(c.x + delta sgn g.x), -(c.x - delta sgn g.x), same in y
+    float2 oxn, oxf, oyn, oyf;   // -(c.x + delta sgn g.x) / g.x, -(c.x - delta sgn g.x) / g.x, same in y
     float2 igx, igy;             // 1/g.x, 1/g.y (as safe_rcp)
     float2 zl, zh, sl, sh;       // z_lo - delta, z_hi + delta, s.z - z_lo, s.z - z_hi
     float lend;                  // lambda_end
@@ -538,10 +538,13 @@ __device__ __forceinline__ uint32_t lamp_interval(float ig2, float mz, uint32_t 
     return in;
 }
 
+// The slab parameters lambda = (x - X) / g come as one FMA, x (1/g) + (-X / g),
+// with -X / g rounded once per lane: the rounding moves a plane by about
+// 2^-24 of the coordinates, far inside the delta the boxes are widened by.
 __device__ __forceinline__ void wedge_pair_hits(const WedgeLane& w, float2 nx, float2 fx, float2 ny, float2 fy,
                                                 float2 z0, float2 z1, bool& h0, bool& h1) {
-    const float2 lnx = __fmul2_rn(__fadd2_rn(nx, w.oxn), w.igx), lfx = __fmul2_rn(__fadd2_rn(fx, w.oxf), w.igx);
-    const float2 lny = __fmul2_rn(__fadd2_rn(ny, w.oyn), w.igy), lfy = __fmul2_rn(__fadd2_rn(fy, w.oyf), w.igy);
+    const float2 lnx = __ffma2_rn(nx, w.igx, w.oxn), lfx = __ffma2_rn(fx, w.igx, w.oxf);
+    const float2 lny = __ffma2_rn(ny, w.igy, w.oyn), lfy = __ffma2_rn(fy, w.igy, w.oyf);
     const float2 a = make_float2(max3f(lnx.x, lny.x, 0.f), max3f(lnx.y, lny.y, 0.f));
     const float2 b = make_float2(min3f(lfx.x, lfy.x, w.lend), min3f(lfx.y, lfy.y, w.lend));
     const float2 la = __ffma2_rn(a, w.sl, w.zl), lb = __ffma2_rn(b, w.sl, w.zl);
@@ -931,12 +934,13 @@ __device__ __forceinline__ uint32_t wedge_search(const SceneView& S, const LampD
         } else {
             const float sgx = (__float_as_uint(gx) >> 31) ? -delta : delta;
             const float sgy = (__float_as_uint(gy) >> 31) ? -delta : delta;
-            w.oxn = dup2(-(cx + sgx));
-            w.oxf = dup2(-(cx - sgx));
-            w.oyn = dup2(-(cy + sgy));
-            w.oyf = dup2(-(cy - sgy));
-            w.igx = dup2(safe_rcp(gx));
-            w.igy = dup2(safe_rcp(gy));
+            const float igxs = safe_rcp(gx), igys = safe_rcp(gy);
+            w.oxn = dup2(__fmul_rn(-(cx + sgx), igxs));
+            w.oxf = dup2(__fmul_rn(-(cx - sgx), igxs));
+            w.oyn = dup2(__fmul_rn(-(cy + sgy), igys));
+            w.oyf = dup2(__fmul_rn(-(cy - sgy), igys));
+            w.igx = dup2(igxs);
+            w.igy = dup2(igys);
             w.lend = lend;
             w.onx = (int)(__float_as_uint(gx) >> 31) * 8;
             w.ony = (int)(__float_as_uint(gy) >> 31) * 8;

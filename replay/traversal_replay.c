@@ -103,9 +103,9 @@ static shear_t shear_of(float dx, float dy, float dz) {
     float dkz = pick(dx, dy, dz, kz);
     if (dkz < 0.f) { int t = kx; kx = ky; ky = t; }
     s.kx = kx; s.ky = ky; s.kz = kz;
-    s.sx = pick(dx, dy, dz, kx) / dkz;
-    s.sy = pick(dx, dy, dz, ky) / dkz;
     s.sz = 1.0f / dkz;
+    s.sx = pick(dx, dy, dz, kx) * s.sz;
+    s.sy = pick(dx, dy, dz, ky) * s.sz;
     return s;
 }
 
@@ -183,7 +183,8 @@ static void source_terms(float ox, float oy, float oz, const f4* s4, const f4* n
 
 /* per-lane wedge state */
 typedef struct {
-    float oxn, oxf, oyn, oyf, igx, igy, zl, zh, sl, sh, lend, ig2, mz;
+    float oxn, oxf, oyn, oyf;   /* -(c.x +- delta) / g.x and the same in y: the slab FMAs' addends */
+    float igx, igy, zl, zh, sl, sh, lend, ig2, mz;
     int nx_hi, ny_hi;   /* near planes are the upper bounds (direction < 0) */
 } wedge_t;
 
@@ -238,10 +239,10 @@ static void wedge_pair_hits(const wedge_t* w, const node4_t* nd, int p, int* h0,
     else { nx0 = X[0]; nx1 = X[1]; fx0 = X[2]; fx1 = X[3]; }
     if (w->ny_hi) { ny0 = Y[2]; ny1 = Y[3]; fy0 = Y[0]; fy1 = Y[1]; }
     else { ny0 = Y[0]; ny1 = Y[1]; fy0 = Y[2]; fy1 = Y[3]; }
-    const float lnx0 = (nx0 + w->oxn) * w->igx, lnx1 = (nx1 + w->oxn) * w->igx;
-    const float lfx0 = (fx0 + w->oxf) * w->igx, lfx1 = (fx1 + w->oxf) * w->igx;
-    const float lny0 = (ny0 + w->oyn) * w->igy, lny1 = (ny1 + w->oyn) * w->igy;
-    const float lfy0 = (fy0 + w->oyf) * w->igy, lfy1 = (fy1 + w->oyf) * w->igy;
+    const float lnx0 = fmaf(nx0, w->igx, w->oxn), lnx1 = fmaf(nx1, w->igx, w->oxn);
+    const float lfx0 = fmaf(fx0, w->igx, w->oxf), lfx1 = fmaf(fx1, w->igx, w->oxf);
+    const float lny0 = fmaf(ny0, w->igy, w->oyn), lny1 = fmaf(ny1, w->igy, w->oyn);
+    const float lfy0 = fmaf(fy0, w->igy, w->oyf), lfy1 = fmaf(fy1, w->igy, w->oyf);
     const float a0 = fmax3(lnx0, lny0, 0.f), a1 = fmax3(lnx1, lny1, 0.f);
     const float b0 = fmin3(lfx0, lfy0, w->lend), b1 = fmin3(lfx1, lfy1, w->lend);
     const float la0 = fmaf(a0, w->sl, w->zl), lb0 = fmaf(b0, w->sl, w->zl);
@@ -401,12 +402,12 @@ static void replay_candidate(const scene_t* S, const lamp_t* L, float cx, float 
         wedge_t* w = &P->w;
         const float sgx = signbit(P->gx) ? -delta : delta;
         const float sgy = signbit(P->gy) ? -delta : delta;
-        w->oxn = -(cx + sgx);
-        w->oxf = -(cx - sgx);
-        w->oyn = -(cy + sgy);
-        w->oyf = -(cy - sgy);
         w->igx = safe_rcp(P->gx);
         w->igy = safe_rcp(P->gy);
+        w->oxn = -(cx + sgx) * w->igx;
+        w->oxf = -(cx - sgx) * w->igx;
+        w->oyn = -(cy + sgy) * w->igy;
+        w->oyf = -(cy - sgy) * w->igy;
         w->lend = P->lend;
         w->nx_hi = signbit(P->gx) ? 1 : 0;
         w->ny_hi = signbit(P->gy) ? 1 : 0;
