@@ -163,25 +163,36 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
             int closed = 0;
             uint32_t failed_all = 0;
             if (WEDGE) {
-                uint32_t want, failed;
+                uint32_t want;
                 float lend, dmax, gx, gy;
                 const uint32_t facing = wedge_setup_patch(S, L, cx, cy, cz, P, lane, ws, want, lend, dmax, gx, gy);
-                const uint32_t occl = wedge_search<false>(S, L, cx, cy, cz, P.s.z, gx, gy, want, lend, dmax, P.ex, lane,
-                                                          stack, ws, cache, failed, nullptr);
-                failed_all |= failed;
-                const uint32_t vis_c = ((failed >> lane) & 1u) ? 0u : (facing & ~occl);
-                uint32_t all = tmask != 0 ? vis_c : 0u;   // sources that saw every check point so far
-                for (int q = 0; q < 6; ++q) {
-                    const uint32_t want_q = ((tmask >> (q / 3)) & 1) ? all : 0u;
-                    if (!__any_sync(kFull, want_q != 0u)) continue;
-                    const float3 pq = want_q ? pulled(vertex(g, q), P.s) : make_float3(0.f, 0.f, 0.f);
-                    float dq = 0.f, gxq = 0.f, gyq = 0.f;
-                    if (want_q) wedge_setup_point(L, cx, cy, cz, pq, want_q, lane, ws, dq, gxq, gyq);
+                uint32_t vis_c = 0u, all = 0u;   // all: sources that saw every check point so far
+                // q = -1: the centroid; q = 0..5: the check points.  One call site of
+                // the (large, inlined) wedge search keeps the kernel's code small.
+                for (int q = -1; q < 6; ++q) {
+                    uint32_t want_q = want;
+                    float szq = P.s.z, gxq = gx, gyq = gy, lq = lend, dq = dmax;
+                    if (q >= 0) {
+                        want_q = ((tmask >> (q / 3)) & 1) ? all : 0u;
+                        if (!__any_sync(kFull, want_q != 0u)) continue;
+                        const float3 pq = want_q ? pulled(vertex(g, q), P.s) : make_float3(0.f, 0.f, 0.f);
+                        dq = 0.f;
+                        gxq = 0.f;
+                        gyq = 0.f;
+                        if (want_q) wedge_setup_point(L, cx, cy, cz, pq, want_q, lane, ws, dq, gxq, gyq);
+                        szq = pq.z;
+                        lq = 1.f;
+                    }
                     uint32_t fq;
-                    const uint32_t oc = wedge_search<false>(S, L, cx, cy, cz, pq.z, gxq, gyq, want_q, 1.f, dq, P.ex,
+                    const uint32_t oc = wedge_search<false>(S, L, cx, cy, cz, szq, gxq, gyq, want_q, lq, dq, P.ex,
                                                             lane, stack, ws, cache, fq, nullptr);
                     failed_all |= fq;
-                    all &= ~oc;
+                    if (q < 0) {
+                        vis_c = ((fq >> lane) & 1u) ? 0u : (facing & ~oc);
+                        all = tmask != 0 ? vis_c : 0u;
+                    } else {
+                        all &= ~oc;
+                    }
                 }
                 for (int m = 0; m < L.K; ++m) {
                     if ((all >> m) & 1u) {
