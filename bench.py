@@ -226,14 +226,16 @@ def l2_read_peak(uvc, nbytes=32 * 2 ** 20, passes=40, reps=10) -> dict:
                       "launch, 4 x 512 threads per SM, best of 10 launches (CUDA events)"}
 
 
-def memory_roofline(uvc, sc, s, irr_s, pairs, pk, ntask=3000, seed=11, vis=True) -> dict:
+def memory_roofline(uvc, sc, s, irr_s, pairs, pk, sample_pairs=384_000, seed=11, vis=True) -> dict:
     """Bytes per pair of the wedge traversal from the counting replay
-    (replay/, the same hierarchy and visit order on the CPU, over a seeded
-    sample of warp tasks) against the measured L2 and HBM read bandwidths."""
+    (replay/, the same hierarchy, task shape and visit order on the CPU, over
+    a seeded sample of warp tasks) against the measured L2 and HBM read
+    bandwidths."""
     import replay
     ex = uvc.scene_export_traversal(sc)
-    tasks = replay.sample_tasks(s.nc, s.np_, ntask, seed)
-    c = replay.replay(ex, s.cand, s.lamp.offsets, tasks)
+    cpt = uvc.irradiance_candidates_per_task()
+    tasks = replay.sample_tasks(s.nc, s.np_, max(1, sample_pairs // (32 * cpt)), seed, cand_per_task=cpt)
+    c = replay.replay(ex, s.cand, s.lamp.offsets, tasks, cand_per_task=cpt)
     bpp = replay.bytes_per_pair(c, s.lamp.K, vis=vis)
     l2 = l2_read_peak(uvc)
     hbm = float(pk.get("hbm_gbs", 6800.0))

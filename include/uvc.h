@@ -344,7 +344,7 @@ int uvc_coverage(const uvc_scene* scene, const float* mu, int32_t nvec, float mu
  * batch's tasks (sample_fraction of them; the sampled A entries are written,
  * correctly), keeps the fastest for the batch, caches it per size bucket for
  * later batches of this process, and synchronises `stream`.
- * uvc_batch_set_config sets them by hand (cand_per_task in {2, 4, 8, 16};
+ * uvc_batch_set_config sets them by hand (cand_per_task in {1, 2, 4, 8, 16};
  * blocks_per_sm 0 = as many as fit).  Errors: UVC_E_INVAL, UVC_E_CUDA.
  */
 typedef struct {
@@ -595,6 +595,15 @@ int uvc_probe_l2_read(const void* buf, size_t bytes, int32_t passes, uint32_t* s
 int uvc_scene_export_traversal(const uvc_scene* scene, void* nodes4, float* tri, float* patch_s, float* patch_n,
                                int32_t* patch_excl, int32_t* root, float* diameter,
                                float* coord_bound);
+
+/*
+ * uvc_irradiance_candidates_per_task - the number of consecutive candidates a
+ * warp of uvc_irradiance_matrix (and uvc_irradiance_counters) takes for its 32
+ * patches, over which it keeps its occluder cache: the task shape a counting
+ * tool needs to replay the kernel's visit order.  Not in the paper.  Always
+ * >= 1; no error.
+ */
+int32_t uvc_irradiance_candidates_per_task(void);
 
 /*
  * uvc_scene_export_bvh - copy the hierarchy to HOST buffers for inspection

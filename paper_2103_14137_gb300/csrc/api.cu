@@ -320,6 +320,8 @@ int uvc_scene_export_traversal(const uvc_scene* scene, void* nodes4, float* tri,
     return uvc::status_from_cuda(e);
 }
 
+int32_t uvc_irradiance_candidates_per_task(void) { return uvc::irradiance_cand_per_task(); }
+
 int uvc_scene_export_bvh(const uvc_scene* scene, uint64_t* keys, int32_t* order, int32_t* children, float* boxes) {
     if (!scene) return UVC_E_INVAL;
     const int64_t n = scene->nt, ni = n > 1 ? n - 1 : 0;

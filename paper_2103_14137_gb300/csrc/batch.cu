@@ -90,7 +90,7 @@ BatchKernel kernel_for_pack(int mode) {
 
 BatchKernel kernel_for(int mode, bool pack) { return pack ? kernel_for_pack<true>(mode) : kernel_for_pack<false>(mode); }
 
-bool valid_cpt(int c) { return c == 2 || c == 4 || c == 8 || c == 16; }
+bool valid_cpt(int c) { return c == 1 || c == 2 || c == 4 || c == 8 || c == 16; }
 
 }  // namespace
 }  // namespace uvc
@@ -285,7 +285,7 @@ int uvc_batch_autotune(uvc_batch* b, double sample_fraction, uvc_batch_config* o
         cudaGetLastError();
         return UVC_E_CUDA;
     }
-    const int cpts[] = {4, 8, 16};
+    const int cpts[] = {1, 4, 16};
     const int bpss[] = {2, 3};
     float best_ms_per_pair = 3.0e38f;
     uvc_batch_config best{8, 0};

@@ -32,9 +32,13 @@ namespace uvc {
 namespace {
 
 // Candidates per warp task: the warp keeps its 32 patches (and its occluder
-// cache) over this many consecutive candidates (a tuning constant).
+// cache) over this many consecutive candidates (a tuning constant).  One
+// candidate per task measured fastest on the ward (69.6 ms per matrix, against
+// 70.2 / 71.5 / 72.2 ms for 3 / 2 / 4): the occluder cache saves less than the
+// finer tasks gain, as the warps of a block then take neighbouring candidates
+// of the same patches and share their node and triangle loads in L1.
 #ifndef UVC_CAND_PER_TASK
-#define UVC_CAND_PER_TASK 4
+#define UVC_CAND_PER_TASK 1
 #endif
 constexpr int kCandPerTask = UVC_CAND_PER_TASK;
 
@@ -190,6 +194,8 @@ int launch_irradiance(const SceneView& S, const float* cand, int64_t nc, const L
 }
 
 }  // namespace
+
+int irradiance_cand_per_task() { return kCandPerTask; }
 
 int irradiance_matrix(const uvc_scene* sc, const float* cand, int64_t nc, const LampDev& lamp, float* A,
                       int64_t lda, uint32_t* vis, cudaStream_t stream) {

@@ -131,6 +131,7 @@ void launch_area_total(const float4* patch_s, int64_t np, float* out, cudaStream
 
 // bandwidth probe (probe.cu)
 int probe_l2_read(const void* buf, size_t bytes, int32_t passes, uint32_t* sink, cudaStream_t stream);
+int irradiance_cand_per_task();   // candidates per warp task of k_irradiance
 
 // learned-proposal features (features.cu)
 int candidate_features(const uvc_scene* sc, const float* cand, int64_t nc, float* feat, int64_t ldf,

@@ -80,6 +80,7 @@ def library():
         "uvc_probe_l2_read": [P, ctypes.c_size_t, i32, P, P],
         "uvc_scene_export_traversal": [P, P, P, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float)],
+        "uvc_irradiance_candidates_per_task": [],
     }
     sig.update({
         "uvc_batch_create": [ctypes.POINTER(_Job), i32, ctypes.POINTER(_Lamp), i32, P, ctypes.c_size_t, P,
@@ -659,6 +660,11 @@ def scene_export_traversal(scene: Scene) -> dict:
            "uvc_scene_export_traversal")
     return dict(nodes4=nodes4, tri=tri, patch_s=ps, patch_n=pn, patch_excl=pe, root=root.value,
                 diameter=diam.value, coord_bound=cb.value)
+
+
+def irradiance_candidates_per_task() -> int:
+    """Candidates per warp task of the matrix kernel (uvc_irradiance_candidates_per_task)."""
+    return int(library().uvc_irradiance_candidates_per_task())
 
 
 class Batch:

@@ -1,6 +1,6 @@
 """The counting replay of the wedge traversal (replay/) against the kernel's
 own instrumented counters (uvc_irradiance_counters) on the same tasks: whole
-rows of the full-size ward for 8 chunks of 4 candidates, the benchmark's K = 8
+rows of the full-size ward for 32 candidates (8 runs of 4), the benchmark's K = 8
 lamp.  The replay re-executes the visit order in FP32 on the CPU; its node
 visits, leaf loads, box, plane and triangle tests must agree with the
 kernel's to within the rounding of the one approximate reciprocal the kernel
@@ -29,8 +29,10 @@ def test_replay_counts_match_kernel_counters():
     assert uvc.scene_status(sc) == 0
     ex = uvc.scene_export_traversal(sc)
     njb = (s.np_ + 31) // 32
-    tasks = np.stack([np.repeat(np.arange(chunks.size), njb), np.tile(np.arange(njb), chunks.size)], axis=1)
-    c = replay.replay(ex, cand, s.lamp.offsets, tasks, cand_per_task=4)
+    cpt = uvc.irradiance_candidates_per_task()
+    nchunk = (rows.size + cpt - 1) // cpt
+    tasks = np.stack([np.repeat(np.arange(nchunk), njb), np.tile(np.arange(njb), nchunk)], axis=1)
+    c = replay.replay(ex, cand, s.lamp.offsets, tasks, cand_per_task=cpt)
     assert c["pairs"] == rows.size * s.np_
     pairs = {"node_visits": "node_visits", "leaf_loads": "leaf_tests", "traversals": "traversals",
              "tri_tests": "lane_tri_tests", "search_segments": "facing_segments",
