@@ -542,15 +542,18 @@ STREAMED_SUMMARY = os.path.join(ROOT, "profiles", "k_streamed_large.txt")
 
 
 def measured_traffic(pairs, summary):
-    """DRAM bytes of one full launch, scaled from the committed ncu summary of
-    a smaller launch of the same kernel (null once the kernel has changed)."""
+    """DRAM bytes of one launch from the committed ncu summary of the same
+    kernel: its full-size capture when the launch has the same pairs, else its
+    bytes per pair scaled to this launch; null once the kernel has changed."""
     try:
         kv = dict(line.split(":", 1) for line in open(summary) if ":" in line)
         if kv.get("kernel_source_hash", "").strip() != kernel_hash():
             return None
-        if "dram_bytes_per_launch" in kv:   # traffic that does not grow with the pairs
+        if "dram_bytes_per_launch" in kv and int(kv.get("pairs_per_launch", "-1")) == int(pairs):
             return float(kv["dram_bytes_per_launch"])
-        return float(kv["dram_bytes_per_pair"]) * pairs
+        if "dram_bytes_per_pair" in kv:
+            return float(kv["dram_bytes_per_pair"]) * pairs
+        return None
     except (OSError, ValueError, KeyError):
         return None
 

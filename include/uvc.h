@@ -137,6 +137,18 @@ int uvc_build_scene_ex(const float* verts, int64_t nv, const int32_t* tris, int6
 int uvc_free_scene(uvc_scene* scene);
 
 /*
+ * uvc_set_fluence_tensor_cores - which kernel uvc_fluence uses for A^T t
+ * (Eq. (5)) where the rows of A start on 16-byte boundaries: 1 (the default)
+ * the tensor cores (tcgen05 MMAs on split TF32 operands, accumulators in
+ * tensor memory), 0 the CUDA cores (FP32 FMAs).  Not in the paper.  Process-
+ * wide; read when uvc_fluence enqueues its launch.
+ *   enable    0 or 1
+ *   previous  HOST int32, may be NULL: receives the setting before the call
+ * Returns UVC_OK, or UVC_E_INVAL (setting unchanged) for other values of enable.
+ */
+int uvc_set_fluence_tensor_cores(int32_t enable, int32_t* previous);
+
+/*
  * uvc_set_wedge_traversal - how the K sources of a vertical line lamp are
  * searched (process-wide; default 1).  Sec. IV-C ("Non-Point Light Sources")
  * approximates a line light by point sources evenly spread along it; when
@@ -264,9 +276,15 @@ int uvc_irradiance_raster(const uvc_scene* scene, const float* tri_normal, const
  *   t   float[nvec][nc] dwell times (seconds)
  *   mu  float[nvec][np] output (J/m^2)
  *
- * FP32 with compensated accumulation.  nvec in [1, 256].  Uses temporary
- * device memory from the stream-ordered allocator.  Errors: UVC_E_INVAL,
- * UVC_E_NOMEM, UVC_E_CUDA.
+ * Where the rows of A start on 16-byte boundaries (lda a multiple of 4, A
+ * 16-byte aligned) the product runs on the tensor cores (see
+ * uvc_set_fluence_tensor_cores): TF32 operands split in two (x = hi + lo),
+ * FP32 accumulation of 32 candidate rows at a time, the stage sums added with
+ * Kahan compensation; otherwise, or with the tensor cores switched off, on the
+ * CUDA cores in FP32 with blocks of 32 rows summed plainly and the block sums
+ * Kahan-compensated.  nvec in [1, 256].  Allocates nothing.  A wait of the
+ * tensor-core kernel that runs out records UVC_E_TIMEOUT in the scene's status
+ * word (uvc_scene_status).  Errors: UVC_E_INVAL, UVC_E_CUDA.
  */
 int uvc_fluence(const uvc_scene* scene, const float* A, int64_t nc, int64_t lda, const float* t,
                 int32_t nvec, float* mu, uvc_stream_t stream);

@@ -33,6 +33,9 @@ bool count_ok(int64_t n) { return n >= 0 && n < kLimit; }
 std::atomic<int> g_wedge{1};
 
 }  // namespace
+// uvc_fluence's kernel where the rows of A allow a tensor map: 1 = tensor cores,
+// 0 = CUDA cores (defined in fluence.cu)
+extern std::atomic<int> g_fluence_tc;
 
 int lamp_to_device(const uvc_lamp* lamp, LampDev* out, float coord_bound, int64_t max_tris) {
     if (!lamp || lamp->K < 1 || lamp->K > UVC_MAX_SOURCES) return UVC_E_INVAL;
@@ -103,6 +106,13 @@ int uvc_free_scene(uvc_scene* scene) {
 int uvc_set_wedge_traversal(int32_t enable, int32_t* previous) {
     if (enable != 0 && enable != 1) return UVC_E_INVAL;
     const int prev = uvc::g_wedge.exchange(enable);
+    if (previous) *previous = prev;
+    return UVC_OK;
+}
+
+int uvc_set_fluence_tensor_cores(int32_t enable, int32_t* previous) {
+    if (enable != 0 && enable != 1) return UVC_E_INVAL;
+    const int prev = uvc::g_fluence_tc.exchange(enable);
     if (previous) *previous = prev;
     return UVC_OK;
 }

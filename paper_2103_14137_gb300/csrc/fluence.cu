@@ -10,6 +10,7 @@
 #include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched through the runtime)
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "uvc_internal.cuh"
@@ -155,7 +156,7 @@ constexpr size_t kTmaTileBytes = sizeof(float) * kTmaRows * kFlCols;
 constexpr size_t kTmaSmem = kFlGroups * kTmaStages * kTmaTileBytes   // tiles
                             + kFluenceSmem                          // dwell times (and the group results)
                             + kFlGroups * kTmaStages * sizeof(uint64_t);   // mbarriers
-constexpr long long kTmaSpin = 1ll << 26;         // try_wait rounds before a wait gives up
+constexpr long long kTmaSpinCycles = 1ll << 31;   // SM clock cycles (about a second) before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -163,7 +164,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     const uint32_t a = smem_u32(bar);
-    for (long long k = 0; k < kTmaSpin; ++k) {
+    const long long t0 = clock64();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -173,8 +175,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (clock64() - t0 > kTmaSpinCycles) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void tma_load_tile(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
@@ -325,6 +327,312 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
         }
 }
 
+// ---------------------------------------------------------------------------
+// Fluence on the tensor cores (tcgen05, TF32 operands split in two)
+// ---------------------------------------------------------------------------
+// The same product as a matrix multiply on the fifth-generation tensor cores:
+// per strip of 128 patches, D (128 patches x 16 vectors, FP32, in tensor
+// memory) takes A_strip^T (128 x nc) times t^T (nc x 16).  TF32 keeps 10 of
+// FP32's 23 fraction bits, so every operand value x is split as x = hi + lo,
+// hi = tf32(x) and lo = tf32(x - hi) (round to nearest), which leaves
+// |x - hi - lo| <= 2^-22 |x|; D takes hi*hi + hi*lo + lo*hi + lo*lo, products
+// of TF32 values being exact in FP32.  Each stage of 32 candidate rows is
+// accumulated from zero into one of two tensor-memory buffers (128 products
+// per value); the converting threads read the stage sum back and add it to
+// per-thread sums with Kahan compensation while the tensor core works on the
+// next stage.  The tensor core thus sums within a stage in its own order and
+// the stage sums are added in candidate order: the result is not bitwise that
+// of k_fluence, and its accuracy is tested against the FP64 product.
+//
+// Roles (kTcThreads = 320): warps 0-7 convert - read the stage's tile of A
+// (landed by a tensor-map copy) and write the hi / lo operand tiles in the
+// tensor core's K-major layout, the same for the stage's dwell times - and
+// then drain the previous stage's accumulator; warp 8 lane 0 issues the copies
+// of A into a ring of kTcSlots tiles; warp 9 allocates the tensor memory and
+// its lane 0 issues the MMAs.  One block per SM (shared memory), persistent
+// over the strips.  Every wait is bounded (kTmaSpinCycles); a wait that runs out
+// records UVC_E_TIMEOUT in the status word, its thread stops waiting, and the
+// block drains what it started before it frees the tensor memory.
+constexpr int kTcRows = 32;                       // candidate rows per stage (4 MMA K-steps of 8)
+constexpr int kTcSlots = 6;                       // tiles of A in flight
+constexpr int kTcConvWarps = 8;
+constexpr int kTcThreads = 32 * (kTcConvWarps + 2);
+constexpr int kTcConv = 32 * kTcConvWarps;        // converting threads
+constexpr uint32_t kTcTileBytes = sizeof(float) * kTcRows * kFlCols;   // 16 KB
+// K-major operand layout without swizzle: 8-row x 16-byte core matrices; for
+// one K-step (8 TF32 values) the two core matrices of an 8-row group lie
+// kTcLbo apart and consecutive 8-row groups kTcSbo apart.
+constexpr uint32_t kTcLbo = 128, kTcSbo = 256;
+constexpr uint32_t kTcAStep = (kFlCols / 8) * kTcSbo;   // 4 KB: one K-step of A (128 rows)
+constexpr uint32_t kTcBStep = (kNV / 8) * kTcSbo;       // 512 B: one K-step of t (16 rows)
+constexpr uint32_t kTcAOp = (kTcRows / 8) * kTcAStep;   // 16 KB per stage and part
+constexpr uint32_t kTcBOp = (kTcRows / 8) * kTcBStep;   // 2 KB per stage and part
+constexpr uint32_t kTcOpBuf = 2 * kTcAOp + 2 * kTcBOp;  // hi and lo of A and of t
+constexpr int kTcBars = 2 * kTcSlots + 3 * 2;           // full, empty; opready, mmadone, accfree (x2)
+constexpr size_t kTcSmem = (size_t)kTcSlots * kTcTileBytes + 2 * (size_t)kTcOpBuf + kTcBars * sizeof(uint64_t) + 16;
+constexpr uint32_t kTcTmemCols = 32;              // two accumulators of kNV FP32 columns
+
+// Instruction descriptor of tcgen05.mma .kind::tf32: D FP32 (bits 4-5 = 1),
+// A and B TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kNV >> 3) << 17) |
+                              ((uint32_t)(kFlCols >> 4) << 24);
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M / N) byte offsets in 16-byte units, descriptor version 1 (bits 46-47),
+// no swizzle (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((kTcSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ float tf32_rn(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 8 consecutive FP32 columns of the warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tc_load8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+}
+
+__device__ __forceinline__ void tma_load_bytes(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
+                                               uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_constant__ CUtensorMap amap, int nc,
+                                                              const float* __restrict__ t, int nvec, int v0,
+                                                              float* __restrict__ mu, int np, int* status) {
+    extern __shared__ __align__(1024) unsigned char tc_smem[];
+    __shared__ int fail;
+    unsigned char* slots = tc_smem;                                     // kTcSlots tiles of A
+    unsigned char* ops = tc_smem + (size_t)kTcSlots * kTcTileBytes;    // 2 operand buffers
+    uint64_t* full = reinterpret_cast<uint64_t*>(ops + 2 * (size_t)kTcOpBuf);   // [kTcSlots] tile landed
+    uint64_t* empty = full + kTcSlots;        // [kTcSlots] tile read by every converting thread
+    uint64_t* opready = empty + kTcSlots;     // [2] operands of the stage written
+    uint64_t* mmadone = opready + 2;          // [2] the stage's MMAs complete
+    uint64_t* accfree = mmadone + 2;          // [2] the stage's accumulator read back
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfree + 2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kProducer = kTcConvWarps, kMma = kTcConvWarps + 1;
+    if (threadIdx.x == 0) {
+        fail = 0;
+        for (int q = 0; q < kTcSlots; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kTcConv);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&opready[q], kTcConv);
+            mbar_init(&mmadone[q], 1);
+            mbar_init(&accfree[q], kTcConv);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMma) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTcTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int nst = (nc + kTcRows - 1) / kTcRows;                // stages per strip
+    const int nstrip = (np + kFlCols - 1) / kFlCols;
+    const int G = (nstrip - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * nst;   // stages of this block
+    bool ok = true;
+
+    if (warp == kProducer) {
+        if (lane == 0)
+            for (int g = 0; g < G; ++g) {
+                const int slot = g % kTcSlots;
+                if (g >= kTcSlots && ok && !mbar_wait(&empty[slot], ((g / kTcSlots) - 1) & 1u)) {
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                const int strip = (int)blockIdx.x + (g / nst) * (int)gridDim.x;
+                // the slot was last read through the generic proxy
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                tma_load_bytes(&amap, &full[slot], slots + (size_t)slot * kTcTileBytes, strip * kFlCols,
+                               (g % nst) * kTcRows, kTcTileBytes);
+            }
+    } else if (warp == kMma) {
+        if (lane == 0)
+            for (int g = 0; g < G; ++g) {
+                const int b = g & 1;
+                if (ok && !mbar_wait(&opready[b], (g >> 1) & 1u)) {
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                if (g >= 2 && ok && !mbar_wait(&accfree[b], ((g >> 1) - 1) & 1u)) {
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                tc_fence_after();
+                const uint32_t ahi = smem_u32(ops + (size_t)b * kTcOpBuf), alo = ahi + kTcAOp;
+                const uint32_t bhi = ahi + 2 * kTcAOp, blo = bhi + kTcBOp;
+                const uint32_t d = tmem + (uint32_t)(b * kNV);
+#pragma unroll
+                for (int ks = 0; ks < kTcRows / 8; ++ks) {
+                    const uint64_t ah = tc_desc(ahi + ks * kTcAStep), al = tc_desc(alo + ks * kTcAStep);
+                    const uint64_t bh = tc_desc(bhi + ks * kTcBStep), bl = tc_desc(blo + ks * kTcBStep);
+                    tc_mma(d, al, bl, ks > 0 ? 1u : 0u);   // a stage starts from zero
+                    tc_mma(d, al, bh, 1u);
+                    tc_mma(d, ah, bl, 1u);
+                    tc_mma(d, ah, bh, 1u);
+                }
+                tc_commit(&mmadone[b]);
+            }
+    } else {
+        const int tid = threadIdx.x;                              // < kTcConv
+        const int h = tid / kFlCols, m = tid % kFlCols;           // row half of the stage, patch of the strip
+        const int tn = (tid >> 3) & (kNV - 1), tk = 4 * (tid & 7);   // dwell values (tid < 128): vector, rows
+        const int q = warp & 3, ch = warp >> 2;                   // drain: lane quarter, column half
+        float tv[4];
+        auto load_t = [&](int st) {
+            const int i0 = st * kTcRows + tk;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                tv[e] = (tid < kFlCols && v0 + tn < nvec && i0 + e < nc) ? __ldg(&t[(size_t)(v0 + tn) * nc + i0 + e])
+                                                                                 : 0.f;
+        };
+        float acc[8], comp[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = comp[c] = 0.f;
+        if (G > 0) load_t(0);
+        for (int g = 0; g <= G; ++g) {
+            if (g < G) {
+                const int slot = g % kTcSlots, b = g & 1;
+                if (ok && !mbar_wait(&full[slot], (g / kTcSlots) & 1u)) {
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                if (g >= 2 && ok && !mbar_wait(&mmadone[b], ((g >> 1) - 1) & 1u)) {   // buffer b free again
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                const float* tile = reinterpret_cast<const float*>(slots + (size_t)slot * kTcTileBytes);
+                unsigned char* op = ops + (size_t)b * kTcOpBuf;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const int k0 = 16 * h + 4 * kk;
+                    float a[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) a[e] = tile[(k0 + e) * kFlCols + m];
+                    float4 hi, lo;
+                    hi.x = tf32_rn(a[0]); lo.x = tf32_rn(__fsub_rn(a[0], hi.x));
+                    hi.y = tf32_rn(a[1]); lo.y = tf32_rn(__fsub_rn(a[1], hi.y));
+                    hi.z = tf32_rn(a[2]); lo.z = tf32_rn(__fsub_rn(a[2], hi.z));
+                    hi.w = tf32_rn(a[3]); lo.w = tf32_rn(__fsub_rn(a[3], hi.w));
+                    const uint32_t off = (uint32_t)(k0 >> 3) * kTcAStep + (uint32_t)(m >> 3) * kTcSbo +
+                                         (uint32_t)((k0 >> 2) & 1) * kTcLbo + (uint32_t)(m & 7) * 16u;
+                    *reinterpret_cast<float4*>(op + off) = hi;
+                    *reinterpret_cast<float4*>(op + kTcAOp + off) = lo;
+                }
+                if (tid < kFlCols) {
+                    float4 hi, lo;
+                    hi.x = tf32_rn(tv[0]); lo.x = tf32_rn(__fsub_rn(tv[0], hi.x));
+                    hi.y = tf32_rn(tv[1]); lo.y = tf32_rn(__fsub_rn(tv[1], hi.y));
+                    hi.z = tf32_rn(tv[2]); lo.z = tf32_rn(__fsub_rn(tv[2], hi.z));
+                    hi.w = tf32_rn(tv[3]); lo.w = tf32_rn(__fsub_rn(tv[3], hi.w));
+                    const uint32_t off = (uint32_t)(tk >> 3) * kTcBStep + (uint32_t)(tn >> 3) * kTcSbo +
+                                         (uint32_t)((tk >> 2) & 1) * kTcLbo + (uint32_t)(tn & 7) * 16u;
+                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + off) = hi;
+                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + kTcBOp + off) = lo;
+                }
+                mbar_arrive(&empty[slot]);
+                // the operands were written through the generic proxy; the tensor core reads them through the async one
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&opready[b]);
+                if (g + 1 < G) load_t((g + 1) % nst);
+            }
+            if (g >= 1) {   // drain the previous stage
+                const int s = g - 1, b = s & 1;
+                if (ok && !mbar_wait(&mmadone[b], (s >> 1) & 1u)) {
+                    ok = false;
+                    fail = 1;
+                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                }
+                __syncwarp();
+                tc_fence_after();
+                float v[8];
+                tc_load8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNV + 8 * ch), v);
+                tc_fence_before();
+                mbar_arrive(&accfree[b]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) kahan_add(acc[c], comp[c], v[c]);
+                if (s % nst == nst - 1) {   // the strip's last stage: store and restart
+                    const int j = ((int)blockIdx.x + (s / nst) * (int)gridDim.x) * kFlCols + 32 * q + lane;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int v = v0 + 8 * ch + c;
+                        if (j < np && v < nvec) mu[(size_t)v * np + j] = __fsub_rn(acc[c], comp[c]);
+                        acc[c] = comp[c] = 0.f;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (fail) {   // only after a wait ran out: let what was started finish (bounded) before the memory goes
+        if (warp == kProducer && lane == 0)
+            for (int g = G > kTcSlots ? G - kTcSlots : 0; g < G; ++g)
+                mbar_wait(&full[g % kTcSlots], (g / kTcSlots) & 1u);
+        if (warp == kMma && lane == 0 && G > 0) mbar_wait(&mmadone[(G - 1) & 1], ((G - 1) >> 1) & 1u);
+        __syncthreads();
+    }
+    if (warp == kMma) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+    }
+}
+
 // Deterministic block sum of (float with Kahan terms, count).
 __device__ void block_reduce(float& s, unsigned long long& cnt) {
     __shared__ float ss[32];
@@ -407,15 +715,15 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-// The tensor map of A (nc rows of lda floats, np used) for kTmaRows x 128
+// The tensor map of A (nc rows of lda floats, np used) for `rows` x 128
 // tiles; false when the layout does not allow one (rows not 16-byte aligned).
-bool fluence_tensor_map(const float* A, int64_t nc, int64_t lda, int np, CUtensorMap* map) {
+bool fluence_tensor_map(const float* A, int64_t nc, int64_t lda, int np, int rows, CUtensorMap* map) {
     if (lda % 4 != 0 || reinterpret_cast<uintptr_t>(A) % 16 != 0 || np < 1 || nc < 1) return false;
     EncodeTiledFn enc = encode_tiled();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)np, (cuuint64_t)nc};
     const cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(float)};
-    const cuuint32_t box[2] = {(cuuint32_t)kFlCols, (cuuint32_t)kTmaRows};
+    const cuuint32_t box[2] = {(cuuint32_t)kFlCols, (cuuint32_t)rows};
     const cuuint32_t estride[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(A), dims, strides, box, estride,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -423,6 +731,8 @@ bool fluence_tensor_map(const float* A, int64_t nc, int64_t lda, int np, CUtenso
 }
 
 }  // namespace
+
+std::atomic<int> g_fluence_tc{1};
 
 int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const float* t, int32_t nvec,
             float* mu, cudaStream_t stream) {
@@ -433,7 +743,17 @@ int fluence(const uvc_scene* sc, const float* A, int64_t nc, int64_t lda, const 
     static_assert(kFlGroups * kFlGroupThreads == kThreads, "block shape");
     static_assert(kFlChunk % kTmaRows == 0 && kTmaRows * kFlCols * sizeof(float) % 128 == 0, "tile shape");
     CUtensorMap map;
-    if (fluence_tensor_map(A, nc, lda, np, &map)) {
+    if (g_fluence_tc.load() && fluence_tensor_map(A, nc, lda, np, kTcRows, &map)) {
+        static const cudaError_t cattr =
+            cudaFuncSetAttribute(k_fluence_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+        if (cattr != cudaSuccess) return status_from_cuda(cattr);
+        const int nstrip = (np + kFlCols - 1) / kFlCols;
+        const int grid = std::min(nstrip, sm_count());
+        for (int v0 = 0; v0 < nvec; v0 += kNV)
+            k_fluence_tc<<<grid, kTcThreads, kTcSmem, stream>>>(map, (int)nc, t, nvec, v0, mu, np, sc->status);
+        return status_from_cuda(cudaGetLastError());
+    }
+    if (fluence_tensor_map(A, nc, lda, np, kTmaRows, &map)) {
         static const cudaError_t tattr =
             cudaFuncSetAttribute(k_fluence_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTmaSmem);
         if (tattr != cudaSuccess) return status_from_cuda(tattr);

@@ -81,6 +81,7 @@ def library():
         "uvc_scene_export_traversal": [P, P, P, P, P, P, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                        ctypes.POINTER(ctypes.c_float)],
         "uvc_irradiance_candidates_per_task": [],
+        "uvc_set_fluence_tensor_cores": [i32, ctypes.POINTER(i32)],
     }
     sig.update({
         "uvc_batch_create": [ctypes.POINTER(_Job), i32, ctypes.POINTER(_Lamp), i32, P, ctypes.c_size_t, P,
@@ -304,6 +305,16 @@ def set_wedge_traversal(enable: bool) -> bool:
     previous setting (see uvc_set_wedge_traversal)."""
     prev = ctypes.c_int32(0)
     _check(library().uvc_set_wedge_traversal(1 if enable else 0, ctypes.byref(prev)), "uvc_set_wedge_traversal")
+    return bool(prev.value)
+
+
+def set_fluence_tensor_cores(enable: bool) -> bool:
+    """Run A^T t on the tensor cores (True, the default) or the CUDA cores
+    (False) where the rows of A allow it; returns the previous setting (see
+    uvc_set_fluence_tensor_cores)."""
+    prev = ctypes.c_int32(0)
+    _check(library().uvc_set_fluence_tensor_cores(1 if enable else 0, ctypes.byref(prev)),
+           "uvc_set_fluence_tensor_cores")
     return bool(prev.value)
 
 

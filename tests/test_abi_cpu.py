@@ -113,6 +113,18 @@ def test_wedge_switch_is_host_only(lib):
     assert lib.uvc_set_wedge_traversal(1, None) == 0
 
 
+def test_host_only_entry_points_through_the_package(lib):
+    """The package re-exports the host-only calls: the matrix kernel's task
+    shape (the counting replay needs it) and the fluence kernel switch."""
+    import paper_2103_14137_gb300 as uvc
+    assert uvc.irradiance_candidates_per_task() >= 1
+    assert uvc.set_fluence_tensor_cores(False) is True      # the default: tensor cores
+    assert uvc.set_fluence_tensor_cores(True) is False
+    prev = ctypes.c_int32(-1)
+    assert lib.uvc_set_fluence_tensor_cores(2, ctypes.byref(prev)) == 1   # UVC_E_INVAL, unchanged
+    assert prev.value == -1 and uvc.set_fluence_tensor_cores(True) is True
+
+
 def test_matrix_row_layouts():
     """The binding passes the library a row stride only for layouts it can
     read and write in bounds: padded rows are fine, too few rows or columns

@@ -79,8 +79,14 @@ def test_measured_traffic_scales_and_goes_stale(tmp_path):
     per_pair.write_text(f"header line\nkernel_source_hash: {cur}\ndram_bytes_per_pair: 4.5\n")
     assert bench.measured_traffic(1000, str(per_pair)) == pytest.approx(4500.0)
     per_launch = tmp_path / "per_launch.txt"
-    per_launch.write_text(f"kernel_source_hash: {cur}\ndram_bytes_per_launch: 1.25e9\n")
+    per_launch.write_text(f"kernel_source_hash: {cur}\ndram_bytes_per_launch: 1.25e9\npairs_per_launch: 1000\n")
     assert bench.measured_traffic(1000, str(per_launch)) == pytest.approx(1.25e9)
+    assert bench.measured_traffic(999, str(per_launch)) is None      # another launch size: not scalable
+    both = tmp_path / "both.txt"
+    both.write_text(f"kernel_source_hash: {cur}\ndram_bytes_per_launch: 1.25e9\npairs_per_launch: 1000\n"
+                    "dram_bytes_per_pair: 4.5\n")
+    assert bench.measured_traffic(1000, str(both)) == pytest.approx(1.25e9)
+    assert bench.measured_traffic(2000, str(both)) == pytest.approx(9000.0)
     stale = tmp_path / "stale.txt"
     stale.write_text("kernel_source_hash: 0000000000000000\ndram_bytes_per_pair: 4.5\n")
     assert bench.measured_traffic(1000, str(stale)) is None

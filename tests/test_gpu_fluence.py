@@ -37,10 +37,11 @@ def _rows_of(nc, n, lda):
 
 @pytest.mark.parametrize("n", [3, 640, 641, 643, 988])
 def test_fluence_padded_rows_match_unpadded(n):
-    """A given as a view of wider rows (row stride a multiple of 4 floats, so
-    8-byte loads) and with odd or unpadded strides give the same fluence bit
-    for bit and match the oracle, including column tiles with 1-3 leftover
-    columns and fewer than 4 patches."""
+    """On the CUDA cores, A given as a view of wider rows (row stride a
+    multiple of 4 floats: the tensor-map kernel) and with odd or unpadded
+    strides (register-fed kernel) give the same fluence bit for bit and match
+    the oracle, including column tiles with 1-3 leftover columns and fewer
+    than 4 patches."""
     rng = np.random.default_rng(n)
     s = tiny_room(n_cand=3)
     sc = build_arrays(s.verts, s.tris, s.centroid[:n], s.normal[:n], s.area[:n], s.excl[:n])
@@ -52,8 +53,12 @@ def test_fluence_padded_rows_match_unpadded(n):
         Ab.copy_(T(A))
         Ap = _rows_of(nc, n, n if n % 2 else n + 1)   # odd stride: 4-byte loads
         Ap.copy_(T(A))
-        mu_b = uvc.fluence(sc, Ab, T(t))
-        mu_p = uvc.fluence(sc, Ap, T(t))
+        prev = uvc.set_fluence_tensor_cores(False)
+        try:
+            mu_b = uvc.fluence(sc, Ab, T(t))
+            mu_p = uvc.fluence(sc, Ap, T(t))
+        finally:
+            uvc.set_fluence_tensor_cores(prev)
         torch.cuda.synchronize()
         assert uvc.scene_status(sc) == 0
         assert torch.equal(mu_b, mu_p), (n, nc, nvec)
@@ -63,7 +68,7 @@ def test_fluence_padded_rows_match_unpadded(n):
 
 def test_fluence_padded_rows_ward_size():
     """The ward's shape (2,000 x 102,030, 16 vectors, ragged last tile of 14
-    columns) with even and odd row strides: bit-identical."""
+    columns) with even and odd row strides on the CUDA cores: bit-identical."""
     from synth import ward_room
     s = ward_room(n_cand=4)
     sc = build(s)
@@ -73,9 +78,75 @@ def test_fluence_padded_rows_ward_size():
     Ap = _rows_of(2000, s.np_, s.np_ + 1)
     Ap.copy_(Ab)
     t = torch.rand((16, 2000), generator=g, device="cuda") * 60
-    mu_b, mu_p = uvc.fluence(sc, Ab, t), uvc.fluence(sc, Ap, t)
+    prev = uvc.set_fluence_tensor_cores(False)
+    try:
+        mu_b, mu_p = uvc.fluence(sc, Ab, t), uvc.fluence(sc, Ap, t)
+    finally:
+        uvc.set_fluence_tensor_cores(prev)
     torch.cuda.synchronize()
     assert uvc.scene_status(sc) == 0 and torch.equal(mu_b, mu_p)
+    sc.free()
+
+
+@pytest.mark.parametrize("n", [3, 128, 129, 641, 988])
+def test_fluence_tensor_cores_against_oracle(n):
+    """The tensor-core kernel (rows on 16-byte boundaries) against the FP64
+    product, element by element within the same 1e-5 relative bound as the
+    CUDA cores: candidate counts below, at and across the 32-row stage (1, 31,
+    32, 33, 77, 301, 2,000), vector counts across the 16-vector pass (1, 16,
+    17, 37), strips with a ragged tail, values over six decades and exact
+    zeros; and against the CUDA-core kernel on the same buffer."""
+    rng = np.random.default_rng(100 + n)
+    s = tiny_room(n_cand=3)
+    sc = build_arrays(s.verts, s.tris, s.centroid[:n], s.normal[:n], s.area[:n], s.excl[:n])
+    for nc, nvec in ((1, 1), (31, 2), (32, 16), (33, 17), (77, 3), (2000, 16), (301, 37)):
+        A = np.exp(rng.uniform(np.log(1e-4), np.log(1e2), size=(nc, n))).astype(np.float32)
+        A[rng.uniform(size=A.shape) < 0.3] = 0.0
+        t = rng.uniform(0, 60, size=(nvec, nc)).astype(np.float32)
+        Ab = _rows_of(nc, n, (n + 3) // 4 * 4)
+        Ab.copy_(T(A))
+        mu_tc = uvc.fluence(sc, Ab, T(t))
+        prev = uvc.set_fluence_tensor_cores(False)
+        try:
+            mu_cc = uvc.fluence(sc, Ab, T(t))
+        finally:
+            uvc.set_fluence_tensor_cores(prev)
+        torch.cuda.synchronize()
+        assert uvc.scene_status(sc) == 0
+        ref = oracle.fluence(A, t)
+        got = mu_tc.cpu().numpy()
+        assert np.all(got[ref == 0] == 0), (n, nc, nvec)
+        assert _rel(got, ref) <= MU_TOL, (n, nc, nvec, _rel(got, ref))
+        assert _rel(got, mu_cc.cpu().numpy()) <= 2 * MU_TOL, (n, nc, nvec)
+    sc.free()
+
+
+def test_fluence_tensor_cores_ward_size():
+    """The ward's shape (2,000 x 102,030, 16 vectors) on the tensor cores
+    against the FP64 product and the CUDA-core kernel; all-zero A gives zeros."""
+    from synth import ward_room
+    s = ward_room(n_cand=4)
+    sc = build(s)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    Ab = _rows_of(2000, s.np_, (s.np_ + 3) // 4 * 4)
+    Ab.copy_(torch.rand((2000, s.np_), generator=g, device="cuda") * 20)
+    t = torch.rand((16, 2000), generator=g, device="cuda") * 60
+    mu_tc = uvc.fluence(sc, Ab, t)
+    prev = uvc.set_fluence_tensor_cores(False)
+    try:
+        mu_cc = uvc.fluence(sc, Ab, t)
+    finally:
+        uvc.set_fluence_tensor_cores(prev)
+    torch.cuda.synchronize()
+    assert uvc.scene_status(sc) == 0
+    ref = oracle.fluence(Ab.cpu().numpy(), t.cpu().numpy())
+    got = mu_tc.cpu().numpy()
+    err = _rel(got, ref)
+    print(f"tensor-core fluence, ward shape: max relative error {err:.3e} "
+          f"(CUDA cores {_rel(mu_cc.cpu().numpy(), ref):.3e})")
+    assert err <= MU_TOL
+    Ab.zero_()
+    assert torch.count_nonzero(uvc.fluence(sc, Ab, t)).item() == 0
     sc.free()
 
 
