@@ -336,18 +336,18 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
 // FP32's 23 fraction bits, so every operand value x is split as x = hi + lo,
 // hi = tf32(x) and lo = tf32(x - hi) (round to nearest), which leaves
 // |x - hi - lo| <= 2^-22 |x|; D takes hi*hi + hi*lo + lo*hi + lo*lo, products
-// of TF32 values being exact in FP32.  Each stage of 32 candidate rows is
-// accumulated from zero into one of two tensor-memory buffers (128 products
-// per value); the converting threads read the stage sum back and add it to
-// per-thread sums with Kahan compensation while the tensor core works on the
-// next stage.  The tensor core thus sums within a stage in its own order and
+// of TF32 values being exact in FP32 (one MMA takes a part of A times both
+// parts of t).  Each stage of 32 candidate rows is accumulated from zero into
+// one of kTcAccs tensor-memory buffers (128 products per value); the
+// converting threads read the stage sum back and add it to per-thread sums
+// with Kahan compensation while the tensor core works on later stages.  The tensor core thus sums within a stage in its own order and
 // the stage sums are added in candidate order: the result is not bitwise that
 // of k_fluence, and its accuracy is tested against the FP64 product.
 //
 // Roles (kTcThreads = 320): warps 0-7 convert - read the stage's tile of A
 // (landed by a tensor-map copy) and write the hi / lo operand tiles in the
 // tensor core's K-major layout, the same for the stage's dwell times - and
-// then drain the previous stage's accumulator; warp 8 lane 0 issues the copies
+// then drain the accumulator of the stage kTcLag behind; warp 8 lane 0 issues the copies
 // of A into a ring of kTcSlots tiles; warp 9 allocates the tensor memory and
 // its lane 0 issues the MMAs.  One block per SM (shared memory), persistent
 // over the strips.  Every wait is bounded (kTmaSpinCycles); a wait that runs out
@@ -363,19 +363,28 @@ constexpr uint32_t kTcTileBytes = sizeof(float) * kTcRows * kFlCols;   // 16 KB
 // one K-step (8 TF32 values) the two core matrices of an 8-row group lie
 // kTcLbo apart and consecutive 8-row groups kTcSbo apart.
 constexpr uint32_t kTcLbo = 128, kTcSbo = 256;
+// The B operand holds t's hi and lo parts as 2 x kNV rows (N = 32), so one MMA
+// takes a part of A times both parts of t.
+constexpr int kTcN = 2 * kNV;
 constexpr uint32_t kTcAStep = (kFlCols / 8) * kTcSbo;   // 4 KB: one K-step of A (128 rows)
-constexpr uint32_t kTcBStep = (kNV / 8) * kTcSbo;       // 512 B: one K-step of t (16 rows)
-constexpr uint32_t kTcAOp = (kTcRows / 8) * kTcAStep;   // 16 KB per stage and part
-constexpr uint32_t kTcBOp = (kTcRows / 8) * kTcBStep;   // 2 KB per stage and part
-constexpr uint32_t kTcOpBuf = 2 * kTcAOp + 2 * kTcBOp;  // hi and lo of A and of t
-constexpr int kTcBars = 2 * kTcSlots + 3 * 2;           // full, empty; opready, mmadone, accfree (x2)
-constexpr size_t kTcSmem = (size_t)kTcSlots * kTcTileBytes + 2 * (size_t)kTcOpBuf + kTcBars * sizeof(uint64_t) + 16;
-constexpr uint32_t kTcTmemCols = 32;              // two accumulators of kNV FP32 columns
+constexpr uint32_t kTcBStep = (kTcN / 8) * kTcSbo;      // 1 KB: one K-step of t (32 rows)
+constexpr uint32_t kTcAOp = (kTcRows / 8) * kTcAStep;   // 16 KB per stage and part of A
+constexpr uint32_t kTcBOp = (kTcRows / 8) * kTcBStep;   // 4 KB per stage
+constexpr uint32_t kTcOpBuf = 2 * kTcAOp + kTcBOp;      // hi and lo of A, t
+// Rings: kTcOps operand buffers, kTcAccs tensor-memory accumulators; the
+// converting threads drain stage g - kTcLag after converting stage g, so an
+// MMA batch has kTcLag conversion periods to complete (kTcLag < kTcOps keeps
+// every mbarrier at most one phase ahead of its waiters; kTcLag < kTcAccs).
+constexpr int kTcOps = 3, kTcAccs = 4, kTcLag = 2;
+static_assert(kTcLag < kTcOps && kTcLag < kTcAccs, "pipeline depths");
+constexpr int kTcBars = 2 * kTcSlots + 2 * kTcOps + kTcAccs;   // full, empty; opready, mmadone; accfree
+constexpr size_t kTcSmem = (size_t)kTcSlots * kTcTileBytes + kTcOps * (size_t)kTcOpBuf + kTcBars * sizeof(uint64_t) + 16;
+constexpr uint32_t kTcTmemCols = kTcAccs * kTcN;  // kTcAccs accumulators of kTcN FP32 columns
 
 // Instruction descriptor of tcgen05.mma .kind::tf32: D FP32 (bits 4-5 = 1),
 // A and B TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kNV >> 3) << 17) |
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
                               ((uint32_t)(kFlCols >> 4) << 24);
 
 // Shared-memory matrix descriptor: start address, leading (K) and stride
@@ -447,12 +456,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
     __shared__ int fail;
     unsigned char* slots = tc_smem;                                     // kTcSlots tiles of A
     unsigned char* ops = tc_smem + (size_t)kTcSlots * kTcTileBytes;    // 2 operand buffers
-    uint64_t* full = reinterpret_cast<uint64_t*>(ops + 2 * (size_t)kTcOpBuf);   // [kTcSlots] tile landed
+    uint64_t* full = reinterpret_cast<uint64_t*>(ops + kTcOps * (size_t)kTcOpBuf);   // [kTcSlots] tile landed
     uint64_t* empty = full + kTcSlots;        // [kTcSlots] tile read by every converting thread
-    uint64_t* opready = empty + kTcSlots;     // [2] operands of the stage written
-    uint64_t* mmadone = opready + 2;          // [2] the stage's MMAs complete
-    uint64_t* accfree = mmadone + 2;          // [2] the stage's accumulator read back
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfree + 2);
+    uint64_t* opready = empty + kTcSlots;     // [kTcOps] operands of the stage written
+    uint64_t* mmadone = opready + kTcOps;     // [kTcOps] the stage's MMAs complete
+    uint64_t* accfree = mmadone + kTcOps;     // [kTcAccs] the stage's accumulator read back
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfree + kTcAccs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kProducer = kTcConvWarps, kMma = kTcConvWarps + 1;
     if (threadIdx.x == 0) {
@@ -461,11 +470,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], kTcConv);
         }
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kTcOps; ++q) {
             mbar_init(&opready[q], kTcConv);
             mbar_init(&mmadone[q], 1);
-            mbar_init(&accfree[q], kTcConv);
         }
+        for (int q = 0; q < kTcAccs; ++q) mbar_init(&accfree[q], kTcConv);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMma) {
@@ -501,36 +510,36 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
     } else if (warp == kMma) {
         if (lane == 0)
             for (int g = 0; g < G; ++g) {
-                const int b = g & 1;
-                if (ok && !mbar_wait(&opready[b], (g >> 1) & 1u)) {
+                const int b = g % kTcOps, a = g % kTcAccs;
+                if (ok && !mbar_wait(&opready[b], (g / kTcOps) & 1u)) {
                     ok = false;
                     fail = 1;
                     atomicCAS(status, 0, UVC_E_TIMEOUT);
                 }
-                if (g >= 2 && ok && !mbar_wait(&accfree[b], ((g >> 1) - 1) & 1u)) {
+                if (g >= kTcAccs && ok && !mbar_wait(&accfree[a], ((g / kTcAccs) - 1) & 1u)) {
                     ok = false;
                     fail = 1;
                     atomicCAS(status, 0, UVC_E_TIMEOUT);
                 }
                 tc_fence_after();
                 const uint32_t ahi = smem_u32(ops + (size_t)b * kTcOpBuf), alo = ahi + kTcAOp;
-                const uint32_t bhi = ahi + 2 * kTcAOp, blo = bhi + kTcBOp;
-                const uint32_t d = tmem + (uint32_t)(b * kNV);
+                const uint32_t bt = ahi + 2 * kTcAOp;
+                const uint32_t d = tmem + (uint32_t)(a * kTcN);
 #pragma unroll
                 for (int ks = 0; ks < kTcRows / 8; ++ks) {
                     const uint64_t ah = tc_desc(ahi + ks * kTcAStep), al = tc_desc(alo + ks * kTcAStep);
-                    const uint64_t bh = tc_desc(bhi + ks * kTcBStep), bl = tc_desc(blo + ks * kTcBStep);
-                    tc_mma(d, al, bl, ks > 0 ? 1u : 0u);   // a stage starts from zero
-                    tc_mma(d, al, bh, 1u);
-                    tc_mma(d, ah, bl, 1u);
-                    tc_mma(d, ah, bh, 1u);
+                    const uint64_t bd = tc_desc(bt + ks * kTcBStep);
+                    tc_mma(d, al, bd, ks > 0 ? 1u : 0u);   // a stage starts from zero
+                    tc_mma(d, ah, bd, 1u);
                 }
                 tc_commit(&mmadone[b]);
             }
     } else {
         const int tid = threadIdx.x;                              // < kTcConv
         const int h = tid / kFlCols, m = tid % kFlCols;           // row half of the stage, patch of the strip
-        const int tn = (tid >> 3) & (kNV - 1), tk = 4 * (tid & 7);   // dwell values (tid < 128): vector, rows
+        // dwell values (tid < 128): vector tn, rows tk..tk+3; the 8 lanes of a
+        // quarter warp take 8 vectors of one 8-row group (one 128-byte row of stores)
+        const int tn = (tid & 7) | (((tid >> 6) & 1) << 3), tk = 4 * ((tid >> 3) & 7);
         const int q = warp & 3, ch = warp >> 2;                   // drain: lane quarter, column half
         float tv[4];
         auto load_t = [&](int st) {
@@ -544,15 +553,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
 #pragma unroll
         for (int c = 0; c < 8; ++c) acc[c] = comp[c] = 0.f;
         if (G > 0) load_t(0);
-        for (int g = 0; g <= G; ++g) {
+        for (int g = 0; g < G + kTcLag; ++g) {
             if (g < G) {
-                const int slot = g % kTcSlots, b = g & 1;
+                const int slot = g % kTcSlots, b = g % kTcOps;
                 if (ok && !mbar_wait(&full[slot], (g / kTcSlots) & 1u)) {
                     ok = false;
                     fail = 1;
                     atomicCAS(status, 0, UVC_E_TIMEOUT);
                 }
-                if (g >= 2 && ok && !mbar_wait(&mmadone[b], ((g >> 1) - 1) & 1u)) {   // buffer b free again
+                if (g >= kTcOps && ok && !mbar_wait(&mmadone[b], ((g / kTcOps) - 1) & 1u)) {   // buffer b free again
                     ok = false;
                     fail = 1;
                     atomicCAS(status, 0, UVC_E_TIMEOUT);
@@ -581,10 +590,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
                     hi.y = tf32_rn(tv[1]); lo.y = tf32_rn(__fsub_rn(tv[1], hi.y));
                     hi.z = tf32_rn(tv[2]); lo.z = tf32_rn(__fsub_rn(tv[2], hi.z));
                     hi.w = tf32_rn(tv[3]); lo.w = tf32_rn(__fsub_rn(tv[3], hi.w));
+                    // rows tn (hi) and kNV + tn (lo) of the B operand
                     const uint32_t off = (uint32_t)(tk >> 3) * kTcBStep + (uint32_t)(tn >> 3) * kTcSbo +
                                          (uint32_t)((tk >> 2) & 1) * kTcLbo + (uint32_t)(tn & 7) * 16u;
                     *reinterpret_cast<float4*>(op + 2 * kTcAOp + off) = hi;
-                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + kTcBOp + off) = lo;
+                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + (kNV / 8) * kTcSbo + off) = lo;
                 }
                 mbar_arrive(&empty[slot]);
                 // the operands were written through the generic proxy; the tensor core reads them through the async one
@@ -592,21 +602,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
                 mbar_arrive(&opready[b]);
                 if (g + 1 < G) load_t((g + 1) % nst);
             }
-            if (g >= 1) {   // drain the previous stage
-                const int s = g - 1, b = s & 1;
-                if (ok && !mbar_wait(&mmadone[b], (s >> 1) & 1u)) {
+            if (g >= kTcLag) {   // drain stage g - kTcLag
+                const int s = g - kTcLag, b = s % kTcOps, a = s % kTcAccs;
+                if (ok && !mbar_wait(&mmadone[b], (s / kTcOps) & 1u)) {
                     ok = false;
                     fail = 1;
                     atomicCAS(status, 0, UVC_E_TIMEOUT);
                 }
                 __syncwarp();
                 tc_fence_after();
-                float v[8];
-                tc_load8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kNV + 8 * ch), v);
+                float vh[8], vl[8];   // the stage's sums against t's hi and lo parts
+                const uint32_t col = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * kTcN + 8 * ch);
+                tc_load8(col, vh);
+                tc_load8(col + kNV, vl);
                 tc_fence_before();
-                mbar_arrive(&accfree[b]);
+                mbar_arrive(&accfree[a]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) kahan_add(acc[c], comp[c], v[c]);
+                for (int c = 0; c < 8; ++c) kahan_add(acc[c], comp[c], __fadd_rn(vl[c], vh[c]));
                 if (s % nst == nst - 1) {   // the strip's last stage: store and restart
                     const int j = ((int)blockIdx.x + (s / nst) * (int)gridDim.x) * kFlCols + 32 * q + lane;
 #pragma unroll
@@ -624,7 +636,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
         if (warp == kProducer && lane == 0)
             for (int g = G > kTcSlots ? G - kTcSlots : 0; g < G; ++g)
                 mbar_wait(&full[g % kTcSlots], (g / kTcSlots) & 1u);
-        if (warp == kMma && lane == 0 && G > 0) mbar_wait(&mmadone[(G - 1) & 1], ((G - 1) >> 1) & 1u);
+        if (warp == kMma && lane == 0 && G > 0) mbar_wait(&mmadone[(G - 1) % kTcOps], ((G - 1) / kTcOps) & 1u);
         __syncthreads();
     }
     if (warp == kMma) {
