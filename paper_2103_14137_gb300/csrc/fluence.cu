@@ -340,24 +340,38 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
 // parts of t).  Each stage of 32 candidate rows is accumulated from zero into
 // one of kTcAccs tensor-memory buffers (128 products per value); the
 // converting threads read the stage sum back and add it to per-thread sums
-// with Kahan compensation while the tensor core works on later stages.  The tensor core thus sums within a stage in its own order and
-// the stage sums are added in candidate order: the result is not bitwise that
-// of k_fluence, and its accuracy is tested against the FP64 product.
+// with Kahan compensation.  The tensor core thus sums within a stage in its
+// own order and the stage sums are added in candidate order: the result is
+// not bitwise that of k_fluence, and its accuracy is tested against the FP64
+// product.
 //
-// Roles (kTcThreads = 320): warps 0-7 convert - read the stage's tile of A
-// (landed by a tensor-map copy) and write the hi / lo operand tiles in the
-// tensor core's K-major layout, the same for the stage's dwell times - and
-// then drain the accumulator of the stage kTcLag behind; warp 8 lane 0 issues the copies
-// of A into a ring of kTcSlots tiles; warp 9 allocates the tensor memory and
-// its lane 0 issues the MMAs.  One block per SM (shared memory), persistent
-// over the strips.  Every wait is bounded (kTmaSpinCycles); a wait that runs out
-// records UVC_E_TIMEOUT in the status word, its thread stops waiting, and the
-// block drains what it started before it frees the tensor memory.
+// Roles (kTcThreads = 576): warps 0-15 form two converting groups of 8 warps,
+// each an independent pipeline over alternate strips of the block (its own
+// tiles of A, operand buffer, accumulators and barriers), so that the
+// latency of one group's stage (wait for the tile, convert, wait for the
+// MMAs, read the accumulator back) overlaps the other's.  A group's threads
+// read the stage's tile of A (landed by a tensor-map copy), write the hi / lo
+// operand tiles in the tensor core's K-major layout, the same for the stage's
+// dwell times, and drain the accumulator of their previous stage.  Warp 16
+// lane 0 issues the copies of A for both groups; warp 17 allocates the tensor
+// memory and its lane 0 issues the MMAs of both groups in stage order.  One
+// block per SM (shared memory), persistent over the strips.  Every wait is
+// bounded (kTmaSpinCycles); a wait that runs out records UVC_E_TIMEOUT in the
+// status word, its thread stops waiting, and the block drains what it started
+// before it frees the tensor memory.
 constexpr int kTcRows = 32;                       // candidate rows per stage (4 MMA K-steps of 8)
-constexpr int kTcSlots = 6;                       // tiles of A in flight
-constexpr int kTcConvWarps = 8;
+#ifndef UVC_TC_GROUPS
+#define UVC_TC_GROUPS 2
+#endif
+constexpr int kTcGroups = UVC_TC_GROUPS;          // independent converting pipelines per block
+constexpr int kTcGroupWarps = 8;
+constexpr int kTcGroupThreads = 32 * kTcGroupWarps;
+constexpr int kTcSlotsPer = 6 / kTcGroups;       // tiles of A in flight per group
+constexpr int kTcConvWarps = kTcGroups * kTcGroupWarps;
 constexpr int kTcThreads = 32 * (kTcConvWarps + 2);
-constexpr int kTcConv = 32 * kTcConvWarps;        // converting threads
+constexpr int kTcRowsPer = kTcRows * kFlCols / kTcGroupThreads;   // rows of a stage each converting thread takes
+constexpr int kTcDrainCols = kNV * 4 / kTcGroupWarps;             // vectors each converting thread drains
+static_assert(kTcRowsPer % 4 == 0 && kTcDrainCols == 8, "converter shape");
 constexpr uint32_t kTcTileBytes = sizeof(float) * kTcRows * kFlCols;   // 16 KB
 // K-major operand layout without swizzle: 8-row x 16-byte core matrices; for
 // one K-step (8 TF32 values) the two core matrices of an 8-row group lie
@@ -371,15 +385,19 @@ constexpr uint32_t kTcBStep = (kTcN / 8) * kTcSbo;      // 1 KB: one K-step of t
 constexpr uint32_t kTcAOp = (kTcRows / 8) * kTcAStep;   // 16 KB per stage and part of A
 constexpr uint32_t kTcBOp = (kTcRows / 8) * kTcBStep;   // 4 KB per stage
 constexpr uint32_t kTcOpBuf = 2 * kTcAOp + kTcBOp;      // hi and lo of A, t
-// Rings: kTcOps operand buffers, kTcAccs tensor-memory accumulators; the
-// converting threads drain stage g - kTcLag after converting stage g, so an
-// MMA batch has kTcLag conversion periods to complete (kTcLag < kTcOps keeps
-// every mbarrier at most one phase ahead of its waiters; kTcLag < kTcAccs).
-constexpr int kTcOps = 3, kTcAccs = 4, kTcLag = 2;
-static_assert(kTcLag < kTcOps && kTcLag < kTcAccs, "pipeline depths");
-constexpr int kTcBars = 2 * kTcSlots + 2 * kTcOps + kTcAccs;   // full, empty; opready, mmadone; accfree
-constexpr size_t kTcSmem = (size_t)kTcSlots * kTcTileBytes + kTcOps * (size_t)kTcOpBuf + kTcBars * sizeof(uint64_t) + 16;
-constexpr uint32_t kTcTmemCols = kTcAccs * kTcN;  // kTcAccs accumulators of kTcN FP32 columns
+// Per group: kTcSlotsPer tiles of A, one operand buffer, kTcAccs
+// tensor-memory accumulators, and its barriers (full / empty per tile;
+// opready, mmadone; accfree per accumulator).
+constexpr int kTcAccs = 2;
+constexpr int kTcBarsPer = 2 * kTcSlotsPer + 2 + kTcAccs;
+constexpr int kTcTAhead = 8 / kTcGroups;         // stages of dwell times copied ahead (per group)
+constexpr size_t kTcOpsOff = (size_t)kTcGroups * kTcSlotsPer * kTcTileBytes;
+constexpr size_t kTcTRingOff = kTcOpsOff + kTcGroups * (size_t)kTcOpBuf;
+constexpr size_t kTcTRingBytes = (size_t)kTcGroups * kTcTAhead * 4 * kFlCols * sizeof(float);
+constexpr size_t kTcBarOff = kTcTRingOff + kTcTRingBytes;
+constexpr size_t kTcSmem = kTcBarOff + (size_t)kTcGroups * kTcBarsPer * sizeof(uint64_t) + 16;
+constexpr uint32_t tc_pow2(uint32_t x) { return x <= 32 ? 32 : 2 * tc_pow2((x + 1) / 2); }
+constexpr uint32_t kTcTmemCols = tc_pow2(kTcGroups * kTcAccs * kTcN);   // the groups' accumulators (a power of 2 >= 32)
 
 // Instruction descriptor of tcgen05.mma .kind::tf32: D FP32 (bits 4-5 = 1),
 // A and B TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
@@ -422,17 +440,22 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                  : "memory");
 }
 
-// 8 consecutive FP32 columns of the warp's 32 tensor-memory lanes
-__device__ __forceinline__ void tc_load8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
+// 2 x 8 FP32 columns (at taddr and taddr + kNV) of the warp's 32 tensor-memory lanes
+__device__ __forceinline__ void tc_load8x2(uint32_t taddr, float (&hi)[8], float (&lo)[8]) {
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-        : "r"(taddr)
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr), "r"(taddr + (uint32_t)kNV)
         : "memory");
 #pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = __uint_as_float(r[c]);
+    for (int c = 0; c < 8; ++c) {
+        hi[c] = __uint_as_float(r[c]);
+        lo[c] = __uint_as_float(r[8 + c]);
+    }
 }
 
 __device__ __forceinline__ void tma_load_bytes(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
@@ -449,32 +472,45 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+// Stage (group r, index j) of a block: the group's local strip kTcGroups (j / nst) + r
+// (the block's strips alternate between the groups), row tile j % nst.
+__device__ __forceinline__ int tc_strip(int r, int j, int nst) {
+    return (int)blockIdx.x + (kTcGroups * (j / nst) + r) * (int)gridDim.x;
+}
+
+__device__ __forceinline__ void tc_fail(bool& ok, int* fail, int* status) {
+    ok = false;
+    *fail = 1;
+    atomicCAS(status, 0, UVC_E_TIMEOUT);
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_constant__ CUtensorMap amap, int nc,
                                                               const float* __restrict__ t, int nvec, int v0,
                                                               float* __restrict__ mu, int np, int* status) {
     extern __shared__ __align__(1024) unsigned char tc_smem[];
     __shared__ int fail;
-    unsigned char* slots = tc_smem;                                     // kTcSlots tiles of A
-    unsigned char* ops = tc_smem + (size_t)kTcSlots * kTcTileBytes;    // 2 operand buffers
-    uint64_t* full = reinterpret_cast<uint64_t*>(ops + kTcOps * (size_t)kTcOpBuf);   // [kTcSlots] tile landed
-    uint64_t* empty = full + kTcSlots;        // [kTcSlots] tile read by every converting thread
-    uint64_t* opready = empty + kTcSlots;     // [kTcOps] operands of the stage written
-    uint64_t* mmadone = opready + kTcOps;     // [kTcOps] the stage's MMAs complete
-    uint64_t* accfree = mmadone + kTcOps;     // [kTcAccs] the stage's accumulator read back
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accfree + kTcAccs);
+    // per group r: tiles of A [kTcSlotsPer], operand buffer, barriers
+    auto slot_of = [&](int r, int s) { return tc_smem + (size_t)(r * kTcSlotsPer + s) * kTcTileBytes; };
+    auto ops_of = [&](int r) { return tc_smem + kTcOpsOff + (size_t)r * kTcOpBuf; };
+    auto bars_of = [&](int r) { return reinterpret_cast<uint64_t*>(tc_smem + kTcBarOff) + r * kTcBarsPer; };
+    // in a group's barriers: full [kTcSlotsPer], empty [kTcSlotsPer], opready, mmadone, accfree [kTcAccs]
+    constexpr int kFull = 0, kEmpty = kTcSlotsPer, kOpready = 2 * kTcSlotsPer, kMmadone = kOpready + 1,
+                  kAccfree = kMmadone + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tc_smem + kTcBarOff + (size_t)kTcGroups * kTcBarsPer * 8);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int kProducer = kTcConvWarps, kMma = kTcConvWarps + 1;
     if (threadIdx.x == 0) {
         fail = 0;
-        for (int q = 0; q < kTcSlots; ++q) {
-            mbar_init(&full[q], 1);
-            mbar_init(&empty[q], kTcConv);
+        for (int r = 0; r < kTcGroups; ++r) {
+            uint64_t* B = bars_of(r);
+            for (int q = 0; q < kTcSlotsPer; ++q) {
+                mbar_init(&B[kFull + q], 1);
+                mbar_init(&B[kEmpty + q], kTcGroupThreads);
+            }
+            mbar_init(&B[kOpready], kTcGroupThreads);
+            mbar_init(&B[kMmadone], 1);
+            for (int q = 0; q < kTcAccs; ++q) mbar_init(&B[kAccfree + q], kTcGroupThreads);
         }
-        for (int q = 0; q < kTcOps; ++q) {
-            mbar_init(&opready[q], kTcConv);
-            mbar_init(&mmadone[q], 1);
-        }
-        for (int q = 0; q < kTcAccs; ++q) mbar_init(&accfree[q], kTcConv);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMma) {
@@ -489,154 +525,158 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
     const uint32_t tmem = *tmem_slot;
     const int nst = (nc + kTcRows - 1) / kTcRows;                // stages per strip
     const int nstrip = (np + kFlCols - 1) / kFlCols;
-    const int G = (nstrip - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * nst;   // stages of this block
+    const int S = (nstrip - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;   // strips of this block
+    int Gr[kTcGroups];                                            // stages of each group
+    for (int r = 0; r < kTcGroups; ++r) Gr[r] = (S - r + kTcGroups - 1) / kTcGroups * nst;
+    const int Gmax = Gr[0];
     bool ok = true;
 
     if (warp == kProducer) {
         if (lane == 0)
-            for (int g = 0; g < G; ++g) {
-                const int slot = g % kTcSlots;
-                if (g >= kTcSlots && ok && !mbar_wait(&empty[slot], ((g / kTcSlots) - 1) & 1u)) {
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+            for (int j = 0; j < Gmax; ++j)
+                for (int r = 0; r < kTcGroups; ++r) {
+                    if (j >= Gr[r]) continue;
+                    uint64_t* B = bars_of(r);
+                    const int s = j % kTcSlotsPer;
+                    if (j >= kTcSlotsPer && ok && !mbar_wait(&B[kEmpty + s], ((j / kTcSlotsPer) - 1) & 1u))
+                        tc_fail(ok, &fail, status);
+                    // the slot was last read through the generic proxy
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tma_load_bytes(&amap, &B[kFull + s], slot_of(r, s), tc_strip(r, j, nst) * kFlCols,
+                                   (j % nst) * kTcRows, kTcTileBytes);
                 }
-                const int strip = (int)blockIdx.x + (g / nst) * (int)gridDim.x;
-                // the slot was last read through the generic proxy
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                tma_load_bytes(&amap, &full[slot], slots + (size_t)slot * kTcTileBytes, strip * kFlCols,
-                               (g % nst) * kTcRows, kTcTileBytes);
-            }
     } else if (warp == kMma) {
         if (lane == 0)
-            for (int g = 0; g < G; ++g) {
-                const int b = g % kTcOps, a = g % kTcAccs;
-                if (ok && !mbar_wait(&opready[b], (g / kTcOps) & 1u)) {
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
-                }
-                if (g >= kTcAccs && ok && !mbar_wait(&accfree[a], ((g / kTcAccs) - 1) & 1u)) {
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
-                }
-                tc_fence_after();
-                const uint32_t ahi = smem_u32(ops + (size_t)b * kTcOpBuf), alo = ahi + kTcAOp;
-                const uint32_t bt = ahi + 2 * kTcAOp;
-                const uint32_t d = tmem + (uint32_t)(a * kTcN);
+            for (int j = 0; j < Gmax; ++j)
+                for (int r = 0; r < kTcGroups; ++r) {
+                    if (j >= Gr[r]) continue;
+                    uint64_t* B = bars_of(r);
+                    const int a = j % kTcAccs;
+                    if (ok && !mbar_wait(&B[kOpready], j & 1u)) tc_fail(ok, &fail, status);
+                    if (j >= kTcAccs && ok && !mbar_wait(&B[kAccfree + a], ((j / kTcAccs) - 1) & 1u))
+                        tc_fail(ok, &fail, status);
+                    tc_fence_after();
+                    const uint32_t ahi = smem_u32(ops_of(r)), alo = ahi + kTcAOp, bt = ahi + 2 * kTcAOp;
+                    const uint32_t d = tmem + (uint32_t)((r * kTcAccs + a) * kTcN);
 #pragma unroll
-                for (int ks = 0; ks < kTcRows / 8; ++ks) {
-                    const uint64_t ah = tc_desc(ahi + ks * kTcAStep), al = tc_desc(alo + ks * kTcAStep);
-                    const uint64_t bd = tc_desc(bt + ks * kTcBStep);
-                    tc_mma(d, al, bd, ks > 0 ? 1u : 0u);   // a stage starts from zero
-                    tc_mma(d, ah, bd, 1u);
+                    for (int ks = 0; ks < kTcRows / 8; ++ks) {
+                        const uint64_t ah = tc_desc(ahi + ks * kTcAStep), al = tc_desc(alo + ks * kTcAStep);
+                        const uint64_t bd = tc_desc(bt + ks * kTcBStep);
+                        tc_mma(d, al, bd, ks > 0 ? 1u : 0u);   // a stage starts from zero
+                        tc_mma(d, ah, bd, 1u);
+                    }
+                    tc_commit(&B[kMmadone]);
                 }
-                tc_commit(&mmadone[b]);
-            }
     } else {
-        const int tid = threadIdx.x;                              // < kTcConv
-        const int h = tid / kFlCols, m = tid % kFlCols;           // row half of the stage, patch of the strip
-        // dwell values (tid < 128): vector tn, rows tk..tk+3; the 8 lanes of a
+        const int r = warp / kTcGroupWarps, wl = warp % kTcGroupWarps;   // group, warp in the group
+        const int gt = threadIdx.x % kTcGroupThreads;
+        const int h = gt / kFlCols, m = gt % kFlCols;             // row part of the stage, patch of the strip
+        // dwell values (gt < 128): vector tn, rows tk..tk+3; the 8 lanes of a
         // quarter warp take 8 vectors of one 8-row group (one 128-byte row of stores)
-        const int tn = (tid & 7) | (((tid >> 6) & 1) << 3), tk = 4 * ((tid >> 3) & 7);
-        const int q = warp & 3, ch = warp >> 2;                   // drain: lane quarter, column half
-        float tv[4];
-        auto load_t = [&](int st) {
-            const int i0 = st * kTcRows + tk;
+        const int tn = (gt & 7) | (((gt >> 6) & 1) << 3), tk = 4 * ((gt >> 3) & 7);
+        const int q = warp & 3, ch = wl >> 2;                     // drain: lane quarter, column group
+        uint64_t* B = bars_of(r);
+        unsigned char* op = ops_of(r);
+        const int G = Gr[r];
+        // the thread's 4 dwell values of the next kTcTAhead stages, copied
+        // asynchronously into its own slice of a shared ring (cp.async, one
+        // group per stage; zero-filled outside t), so that their L2 latency
+        // is hidden behind the stages before
+        float* tring = reinterpret_cast<float*>(tc_smem + kTcTRingOff) + (size_t)r * kTcTAhead * 4 * kFlCols + 4 * gt;
+        auto load_t = [&](int j1) {
+            if (gt < kFlCols && j1 < G) {
+                const int i0 = (j1 % nst) * kTcRows + tk;
+                float* dst = tring + (j1 % kTcTAhead) * (4 * kFlCols);
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                tv[e] = (tid < kFlCols && v0 + tn < nvec && i0 + e < nc) ? __ldg(&t[(size_t)(v0 + tn) * nc + i0 + e])
-                                                                                 : 0.f;
-        };
-        float acc[8], comp[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = comp[c] = 0.f;
-        if (G > 0) load_t(0);
-        for (int g = 0; g < G + kTcLag; ++g) {
-            if (g < G) {
-                const int slot = g % kTcSlots, b = g % kTcOps;
-                if (ok && !mbar_wait(&full[slot], (g / kTcSlots) & 1u)) {
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
+                for (int e = 0; e < 4; ++e) {
+                    const bool in = v0 + tn < nvec && i0 + e < nc;
+                    const float* src = in ? &t[(size_t)(v0 + tn) * nc + i0 + e] : t;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst + e)), "l"(src),
+                                 "r"(in ? 4 : 0)
+                                 : "memory");
                 }
-                if (g >= kTcOps && ok && !mbar_wait(&mmadone[b], ((g / kTcOps) - 1) & 1u)) {   // buffer b free again
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
-                }
-                const float* tile = reinterpret_cast<const float*>(slots + (size_t)slot * kTcTileBytes);
-                unsigned char* op = ops + (size_t)b * kTcOpBuf;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const int k0 = 16 * h + 4 * kk;
-                    float a[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) a[e] = tile[(k0 + e) * kFlCols + m];
-                    float4 hi, lo;
-                    hi.x = tf32_rn(a[0]); lo.x = tf32_rn(__fsub_rn(a[0], hi.x));
-                    hi.y = tf32_rn(a[1]); lo.y = tf32_rn(__fsub_rn(a[1], hi.y));
-                    hi.z = tf32_rn(a[2]); lo.z = tf32_rn(__fsub_rn(a[2], hi.z));
-                    hi.w = tf32_rn(a[3]); lo.w = tf32_rn(__fsub_rn(a[3], hi.w));
-                    const uint32_t off = (uint32_t)(k0 >> 3) * kTcAStep + (uint32_t)(m >> 3) * kTcSbo +
-                                         (uint32_t)((k0 >> 2) & 1) * kTcLbo + (uint32_t)(m & 7) * 16u;
-                    *reinterpret_cast<float4*>(op + off) = hi;
-                    *reinterpret_cast<float4*>(op + kTcAOp + off) = lo;
-                }
-                if (tid < kFlCols) {
-                    float4 hi, lo;
-                    hi.x = tf32_rn(tv[0]); lo.x = tf32_rn(__fsub_rn(tv[0], hi.x));
-                    hi.y = tf32_rn(tv[1]); lo.y = tf32_rn(__fsub_rn(tv[1], hi.y));
-                    hi.z = tf32_rn(tv[2]); lo.z = tf32_rn(__fsub_rn(tv[2], hi.z));
-                    hi.w = tf32_rn(tv[3]); lo.w = tf32_rn(__fsub_rn(tv[3], hi.w));
-                    // rows tn (hi) and kNV + tn (lo) of the B operand
-                    const uint32_t off = (uint32_t)(tk >> 3) * kTcBStep + (uint32_t)(tn >> 3) * kTcSbo +
-                                         (uint32_t)((tk >> 2) & 1) * kTcLbo + (uint32_t)(tn & 7) * 16u;
-                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + off) = hi;
-                    *reinterpret_cast<float4*>(op + 2 * kTcAOp + (kNV / 8) * kTcSbo + off) = lo;
-                }
-                mbar_arrive(&empty[slot]);
-                // the operands were written through the generic proxy; the tensor core reads them through the async one
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&opready[b]);
-                if (g + 1 < G) load_t((g + 1) % nst);
             }
-            if (g >= kTcLag) {   // drain stage g - kTcLag
-                const int s = g - kTcLag, b = s % kTcOps, a = s % kTcAccs;
-                if (ok && !mbar_wait(&mmadone[b], (s / kTcOps) & 1u)) {
-                    ok = false;
-                    fail = 1;
-                    atomicCAS(status, 0, UVC_E_TIMEOUT);
-                }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        float acc[kTcDrainCols], comp[kTcDrainCols];
+#pragma unroll
+        for (int c = 0; c < kTcDrainCols; ++c) acc[c] = comp[c] = 0.f;
+        for (int j1 = 0; j1 < kTcTAhead; ++j1) load_t(j1);
+        for (int j = 0; j <= G; ++j) {
+            if (j >= 1) {   // stage j - 1: its MMAs complete frees the operand buffer; drain its accumulator
+                const int s = j - 1, a = s % kTcAccs;
+                if (ok && !mbar_wait(&B[kMmadone], s & 1u)) tc_fail(ok, &fail, status);
                 __syncwarp();
                 tc_fence_after();
-                float vh[8], vl[8];   // the stage's sums against t's hi and lo parts
-                const uint32_t col = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(a * kTcN + 8 * ch);
-                tc_load8(col, vh);
-                tc_load8(col + kNV, vl);
+                float vh[kTcDrainCols], vl[kTcDrainCols];   // the stage's sums against t's hi and lo parts
+                tc_load8x2(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((r * kTcAccs + a) * kTcN + kTcDrainCols * ch),
+                           vh, vl);
                 tc_fence_before();
-                mbar_arrive(&accfree[a]);
+                mbar_arrive(&B[kAccfree + a]);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) kahan_add(acc[c], comp[c], __fadd_rn(vl[c], vh[c]));
+                for (int c = 0; c < kTcDrainCols; ++c) kahan_add(acc[c], comp[c], __fadd_rn(vl[c], vh[c]));
                 if (s % nst == nst - 1) {   // the strip's last stage: store and restart
-                    const int j = ((int)blockIdx.x + (s / nst) * (int)gridDim.x) * kFlCols + 32 * q + lane;
+                    const int jj = tc_strip(r, s, nst) * kFlCols + 32 * q + lane;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const int v = v0 + 8 * ch + c;
-                        if (j < np && v < nvec) mu[(size_t)v * np + j] = __fsub_rn(acc[c], comp[c]);
+                    for (int c = 0; c < kTcDrainCols; ++c) {
+                        const int v = v0 + kTcDrainCols * ch + c;
+                        if (jj < np && v < nvec) mu[(size_t)v * np + jj] = __fsub_rn(acc[c], comp[c]);
                         acc[c] = comp[c] = 0.f;
                     }
                 }
             }
+            if (j == G) break;
+            const int slot = j % kTcSlotsPer;
+            if (ok && !mbar_wait(&B[kFull + slot], (j / kTcSlotsPer) & 1u)) tc_fail(ok, &fail, status);
+            const float* tile = reinterpret_cast<const float*>(slot_of(r, slot));
+#pragma unroll
+            for (int kk = 0; kk < kTcRowsPer / 4; ++kk) {
+                const int k0 = kTcRowsPer * h + 4 * kk;
+                float a4[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a4[e] = tile[(k0 + e) * kFlCols + m];
+                float4 hi, lo;
+                hi.x = tf32_rn(a4[0]); lo.x = tf32_rn(__fsub_rn(a4[0], hi.x));
+                hi.y = tf32_rn(a4[1]); lo.y = tf32_rn(__fsub_rn(a4[1], hi.y));
+                hi.z = tf32_rn(a4[2]); lo.z = tf32_rn(__fsub_rn(a4[2], hi.z));
+                hi.w = tf32_rn(a4[3]); lo.w = tf32_rn(__fsub_rn(a4[3], hi.w));
+                const uint32_t off = (uint32_t)(k0 >> 3) * kTcAStep + (uint32_t)(m >> 3) * kTcSbo +
+                                     (uint32_t)((k0 >> 2) & 1) * kTcLbo + (uint32_t)(m & 7) * 16u;
+                *reinterpret_cast<float4*>(op + off) = hi;
+                *reinterpret_cast<float4*>(op + kTcAOp + off) = lo;
+            }
+            if (gt < kFlCols) {
+                asm volatile("cp.async.wait_group %0;" ::"n"(kTcTAhead - 1) : "memory");
+                float tv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) tv[e] = tring[(j % kTcTAhead) * (4 * kFlCols) + e];
+                float4 hi, lo;
+                hi.x = tf32_rn(tv[0]); lo.x = tf32_rn(__fsub_rn(tv[0], hi.x));
+                hi.y = tf32_rn(tv[1]); lo.y = tf32_rn(__fsub_rn(tv[1], hi.y));
+                hi.z = tf32_rn(tv[2]); lo.z = tf32_rn(__fsub_rn(tv[2], hi.z));
+                hi.w = tf32_rn(tv[3]); lo.w = tf32_rn(__fsub_rn(tv[3], hi.w));
+                // rows tn (hi) and kNV + tn (lo) of the B operand
+                const uint32_t off = (uint32_t)(tk >> 3) * kTcBStep + (uint32_t)(tn >> 3) * kTcSbo +
+                                     (uint32_t)((tk >> 2) & 1) * kTcLbo + (uint32_t)(tn & 7) * 16u;
+                *reinterpret_cast<float4*>(op + 2 * kTcAOp + off) = hi;
+                *reinterpret_cast<float4*>(op + 2 * kTcAOp + (kNV / 8) * kTcSbo + off) = lo;
+            }
+            mbar_arrive(&B[kEmpty + slot]);
+            // the operands were written through the generic proxy; the tensor core reads them through the async one
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(&B[kOpready]);
+            load_t(j + kTcTAhead);   // into the slot just read
         }
     }
     __syncthreads();
     if (fail) {   // only after a wait ran out: let what was started finish (bounded) before the memory goes
         if (warp == kProducer && lane == 0)
-            for (int g = G > kTcSlots ? G - kTcSlots : 0; g < G; ++g)
-                mbar_wait(&full[g % kTcSlots], (g / kTcSlots) & 1u);
-        if (warp == kMma && lane == 0 && G > 0) mbar_wait(&mmadone[(G - 1) % kTcOps], ((G - 1) / kTcOps) & 1u);
+            for (int r = 0; r < kTcGroups; ++r)
+                for (int j = Gr[r] > kTcSlotsPer ? Gr[r] - kTcSlotsPer : 0; j < Gr[r]; ++j)
+                    mbar_wait(&bars_of(r)[kFull + j % kTcSlotsPer], (j / kTcSlotsPer) & 1u);
+        if (warp == kMma && lane == 0)
+            for (int r = 0; r < kTcGroups; ++r)
+                if (Gr[r] > 0) mbar_wait(&bars_of(r)[kMmadone], (Gr[r] - 1) & 1u);
         __syncthreads();
     }
     if (warp == kMma) {
