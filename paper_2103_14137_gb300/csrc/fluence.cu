@@ -345,23 +345,25 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
 // not bitwise that of k_fluence, and its accuracy is tested against the FP64
 // product.
 //
-// Roles (kTcThreads = 576): warps 0-15 form two converting groups of 8 warps,
-// each an independent pipeline over alternate strips of the block (its own
-// tiles of A, operand buffer, accumulators and barriers), so that the
-// latency of one group's stage (wait for the tile, convert, wait for the
-// MMAs, read the accumulator back) overlaps the other's.  A group's threads
-// read the stage's tile of A (landed by a tensor-map copy), write the hi / lo
-// operand tiles in the tensor core's K-major layout, the same for the stage's
-// dwell times, and drain the accumulator of their previous stage.  Warp 16
-// lane 0 issues the copies of A for both groups; warp 17 allocates the tensor
-// memory and its lane 0 issues the MMAs of both groups in stage order.  One
-// block per SM (shared memory), persistent over the strips.  Every wait is
-// bounded (kTmaSpinCycles); a wait that runs out records UVC_E_TIMEOUT in the
-// status word, its thread stops waiting, and the block drains what it started
-// before it frees the tensor memory.
+// Roles (kTcThreads = 32 (8 kTcGroups + 2)): the first 8 kTcGroups warps form
+// kTcGroups converting groups of 8 warps, each an independent pipeline over
+// every kTcGroups-th strip of the block (its own tiles of A, operand buffer,
+// accumulators and barriers), so that the latency of one group's stage (wait
+// for the tile, convert, wait for the MMAs, read the accumulator back)
+// overlaps the others' (ward A^T t: one group 0.389 ms, two 0.297, three
+// 0.265; four do not fit the shared memory).  A group's threads read the
+// stage's tile of A (landed by a tensor-map copy), write the hi / lo operand
+// tiles in the tensor core's K-major layout, the same for the stage's dwell
+// times, and drain the accumulator of their previous stage.  The next warp's
+// lane 0 issues the copies of A for every group; the last warp allocates the
+// tensor memory and its lane 0 issues the MMAs of every group in stage order.
+// One block per SM (shared memory), persistent over the strips.  Every wait
+// is bounded (kTmaSpinCycles); a wait that runs out records UVC_E_TIMEOUT in
+// the status word, its thread stops waiting, and the block drains what it
+// started before it frees the tensor memory.
 constexpr int kTcRows = 32;                       // candidate rows per stage (4 MMA K-steps of 8)
 #ifndef UVC_TC_GROUPS
-#define UVC_TC_GROUPS 2
+#define UVC_TC_GROUPS 3
 #endif
 constexpr int kTcGroups = UVC_TC_GROUPS;          // independent converting pipelines per block
 constexpr int kTcGroupWarps = 8;
