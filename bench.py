@@ -250,7 +250,7 @@ def memory_roofline(uvc, sc, s, irr_s, pairs, pk, sample_pairs=384_000, seed=11,
             "peak_l2_method": l2["method"],
             "peak_hbm_source": "hbm_gbs of MEASURED_PEAKS.json (copy kernel)" if "hbm_gbs" in pk else "fallback",
             "leaf_step_lane_occupancy": round(bpp["leaf_step_lane_occupancy"], 3),
-            "sample": f"{tasks.shape[0]} seeded warp tasks (32 patches x 4 candidates) replayed on the CPU, "
+            "sample": f"{tasks.shape[0]} seeded warp tasks (32 patches x {cpt} candidate(s)) replayed on the CPU, "
                       f"{c['pairs']} pairs"}
 
 

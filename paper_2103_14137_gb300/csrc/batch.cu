@@ -33,19 +33,24 @@ struct JobDev {
     int nc, lamp, nchunk, njb;
 };
 
-// The lamps of a batch of at most kParamLamps lamps travel in the kernel's
-// parameters (constant memory: the sources' heights and powers, read in the
-// inner loops, are warp-uniform broadcasts there); larger batches read them
-// from the device table.
-constexpr int kParamLamps = 16;
+// The lamps and job records of a batch of at most kParamLamps lamps and
+// kParamJobs jobs travel in the kernel's parameters (constant memory: the
+// sources' heights and powers and the job's scene view, read in the inner
+// loops, are warp-uniform broadcasts there, and the compiler re-reads them
+// instead of holding them in registers); larger batches read them from the
+// device tables.
+constexpr int kParamLamps = 12;
+constexpr int kParamJobs = 192;
 struct LampPack {
     LampDev L[kParamLamps];
+    JobDev J[kParamJobs];
 };
+static_assert(sizeof(LampPack) + 64 <= 32764, "kernel parameters");
 
 // Lamps with the wedge path (LampDev::wedge) use the per-source shared
 // arrays, sized for the batch's largest such lamp (wedge_k).  MODE: 0 = no
 // lamp of the batch takes the wedge path, 1 = all do, 2 = mixed (chosen per
-// job; both paths inlined).  PACK: the lamps come from `pack`.
+// job; both paths inlined).  PACK: the lamps and jobs come from `pack`.
 template <int MODE, bool PACK>
 __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     k_irradiance_batch(const JobDev* __restrict__ jobs, int njobs, const LampDev* __restrict__ lamps,
@@ -55,14 +60,15 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * stack_cap;
     const WedgeSmem ws = wedge_smem(reinterpret_cast<char*>(smem) + stack_smem_bytes(stack_cap), wedge_k, warp);
+    const JobDev* jt = PACK ? pack.J : jobs;
     for (int64_t task = task_lo + (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < task_hi;
          task += (int64_t)gridDim.x * kWarpsPerBlock) {
         int lo = 0, hi = njobs - 1;   // last job starting at or before `task`
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].task_begin <= task) lo = mid; else hi = mid - 1;
+            if (jt[mid].task_begin <= task) lo = mid; else hi = mid - 1;
         }
-        const JobDev& J = jobs[lo];
+        const JobDev& J = jt[lo];
         const int64_t local = task - J.task_begin;
         const int jb = (int)(local / J.nchunk), ic = (int)(local % J.nchunk);
         const int j = jb * 32 + lane;
@@ -107,7 +113,7 @@ struct uvc_batch {
     int wedge_k = 0;                      // largest K among the lamps with the wedge path
     int mode = 0;                         // kernel variant: 0 no wedge lamp, 1 all wedge, 2 mixed
     int64_t total_pairs = 0;
-    uvc::LampPack pack{};                 // the lamps again, for the kernel parameters (nlamps <= kParamLamps)
+    uvc::LampPack pack{};                 // the lamps and jobs again, for the kernel parameters (small batches)
     int uploaded_cpt = 0;                 // cand_per_task of the uploaded table
     uvc_batch_config tuned{8, 0};        // configuration used by uvc_batch_launch
 };
@@ -127,6 +133,7 @@ int64_t fill_task_begin(uvc_batch* b, int cpt) {
 
 int upload(uvc_batch* b, int cpt, cudaStream_t stream, int64_t* total_tasks) {
     *total_tasks = fill_task_begin(b, cpt);
+    if (b->njobs <= kParamJobs) std::copy(b->host_jobs.begin(), b->host_jobs.end(), b->pack.J);
     if (b->uploaded_cpt == cpt) return UVC_OK;
     cudaError_t e = cudaMemcpyAsync(b->dev_jobs, b->host_jobs.data(), sizeof(JobDev) * b->njobs,
                                     cudaMemcpyHostToDevice, stream);
@@ -138,7 +145,7 @@ int upload(uvc_batch* b, int cpt, cudaStream_t stream, int64_t* total_tasks) {
 
 int launch_range(const uvc_batch* b, int cpt, int blocks_per_sm, int64_t lo, int64_t hi, cudaStream_t stream) {
     if (hi <= lo) return UVC_OK;
-    const bool pack = b->nlamps <= kParamLamps;
+    const bool pack = b->nlamps <= kParamLamps && b->njobs <= kParamJobs;
     BatchKernel k = kernel_for(b->mode, pack);
     const size_t smem = stack_smem_bytes(b->stack_cap) + wedge_smem_bytes(b->wedge_k);
     if (smem > 48 * 1024) {
