@@ -75,6 +75,8 @@ def parse():
     p.add_argument("--resolution", type=int, default=512, help="raster workload: cube face resolution R")
     p.add_argument("--tile", type=int, default=500, help="large_tiles workload: candidates per tile of A")
     p.add_argument("--rooms", type=int, default=16, help="batched workload: number of rooms (x 12 designs)")
+    p.add_argument("--keep", type=float, default=0.0,
+                   help="learned workload: fraction of the candidates kept (0: the proposal's default)")
     p.add_argument("--pool-gb", type=float, default=96.0, help="batched workload: A buffer pool (GiB)")
     p.add_argument("--candidates", type=int, default=0, help="use only the first N candidates (profiling)")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
@@ -664,11 +666,12 @@ def run_reference(args):
 # batched rooms x designs (one persistent launch per wave, CUDA graph)
 # ---------------------------------------------------------------------------
 
-def setup_rooms(n_rooms: int, dev, base_seed: int = 100):
+def setup_rooms(n_rooms: int, dev, base_seed: int = 100, keep: float = 0.0):
     """Rooms of uneven size x the 12 designs, resident on the device: per room
     the scene, the probe scene (1 % of the patches, for the learned proposal)
     and per (room, design) job the candidates, the full and kept dwell vectors
-    and the buffers of the kept candidates."""
+    and the buffers of the kept candidates (the proposal's fraction `keep`,
+    its default when 0)."""
     import torch
 
     import paper_2103_14137_gb300 as uvc
@@ -691,7 +694,7 @@ def setup_rooms(n_rooms: int, dev, base_seed: int = 100):
         js = []
         for cand, _, d in jobs:
             nc = cand.shape[0]
-            k = prop.keep_count(nc)
+            k = prop.keep_count(nc, keep if keep > 0 else prop.KEEP)
             js.append({"cand": Td(cand), "d": d, "nc": nc, "k": k, "t_full": Td(dwell_vectors(NVEC, nc, seed=d)),
                        "t_kept": Td(dwell_vectors(NVEC, k, seed=d)),
                        "kept": torch.zeros((k, 3), dtype=torch.float32, device=dev),
@@ -960,7 +963,7 @@ def proposal_quality(uvc, rooms, lamps, dev, qjobs, fallback, workers: int):
 
 
 def batched_learned(uvc, dev, n_rooms: int, steps: int, pool_gb: float = 96.0, quality_jobs: int = 8,
-                    pipelines=("plain", "batched", "learned"), base_seed: int = 100):
+                    pipelines=("plain", "batched", "learned"), base_seed: int = 100, keep: float = 0.0):
     """Rooms/s of the plain method (job by job), the batched engine and the
     batched + learned proposal on the same seeded rooms x 12 designs, each
     timed over `steps` steps after one warm-up (a step = every job of every
@@ -968,7 +971,7 @@ def batched_learned(uvc, dev, n_rooms: int, steps: int, pool_gb: float = 96.0, q
     matrices with its fallbacks, plus every job's fluence and coverage), and
     the learned proposal's quality on a seeded subset of the same timed jobs."""
     import torch
-    lamps, rooms, t_gen = setup_rooms(n_rooms, dev, base_seed)
+    lamps, rooms, t_gen = setup_rooms(n_rooms, dev, base_seed, keep)
     njobs = sum(len(R["jobs"]) for R in rooms)
     pairs = sum(j["nc"] * R["np"] for R in rooms for j in R["jobs"])
     plain_run, plain_job = plain_pipeline(uvc, rooms, lamps, dev)
@@ -1040,7 +1043,8 @@ def _run_rooms(args, pipelines, key, quality_jobs):
     dev = torch.device("cuda", local)
     uvc.build()
     steps = max(3, args.steps)
-    r = batched_learned(uvc, dev, args.rooms, steps, args.pool_gb, quality_jobs, pipelines, 100 + 1000 * rank)
+    r = batched_learned(uvc, dev, args.rooms, steps, args.pool_gb, quality_jobs, pipelines, 100 + 1000 * rank,
+                        args.keep)
     ms = r[key]["ms_per_step"]
     out = {"metric": METRIC, "value": r[key]["rooms_per_s"], "unit": "rooms/s", "n_gpus": 1, "steps": steps,
            "warmup": 1, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1048,7 +1052,8 @@ def _run_rooms(args, pipelines, key, quality_jobs):
            "config": {"workload": f"{key}: {args.rooms} seeded rooms of uneven size (10k-200k triangles, 5k-300k "
                                   "patches, 500-5,000 candidates, log-uniform) x 12 designs (lamp-bottom heights "
                                   "0.3/0.5/0.8/1.1 m x line lamps 0.6/1.2/1.8 m, K = 4/8/12); fluence (16 vectors) and "
-                                  "coverage of every job", "rooms": args.rooms, "pool_gib": args.pool_gb},
+                                  "coverage of every job", "rooms": args.rooms, "pool_gib": args.pool_gb,
+                      **({"keep": args.keep} if key == "learned" and args.keep > 0 else {})},
            **{k: v for k, v in r.items() if k not in ("steps",)}}
     print(json.dumps(out), flush=True)
 
