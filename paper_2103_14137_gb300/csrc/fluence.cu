@@ -13,6 +13,7 @@
 #include <atomic>
 #include <mutex>
 
+#include "tcgen05.cuh"
 #include "uvc_internal.cuh"
 
 namespace uvc {
@@ -156,28 +157,10 @@ constexpr size_t kTmaTileBytes = sizeof(float) * kTmaRows * kFlCols;
 constexpr size_t kTmaSmem = kFlGroups * kTmaStages * kTmaTileBytes   // tiles
                             + kFluenceSmem                          // dwell times (and the group results)
                             + kFlGroups * kTmaStages * sizeof(uint64_t);   // mbarriers
-constexpr long long kTmaSpinCycles = 1ll << 31;   // SM clock cycles (about a second) before a wait gives up
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    const long long t0 = clock64();
-    for (;;) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > kTmaSpinCycles) return false;
-    }
-}
+using tc::mbar_arrive;
+using tc::mbar_init;
+using tc::mbar_wait;
+using tc::smem_u32;
 
 __device__ __forceinline__ void tma_load_tile(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
@@ -358,7 +341,7 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
 // lane 0 issues the copies of A for every group; the last warp allocates the
 // tensor memory and its lane 0 issues the MMAs of every group in stage order.
 // One block per SM (shared memory), persistent over the strips.  Every wait
-// is bounded (kTmaSpinCycles); a wait that runs out records UVC_E_TIMEOUT in
+// is bounded (tc::kSpinCycles); a wait that runs out records UVC_E_TIMEOUT in
 // the status word, its thread stops waiting, and the block drains what it
 // started before it frees the tensor memory.
 constexpr int kTcRows = 32;                       // candidate rows per stage (4 MMA K-steps of 8)
@@ -401,63 +384,13 @@ constexpr size_t kTcSmem = kTcBarOff + (size_t)kTcGroups * kTcBarsPer * sizeof(u
 constexpr uint32_t tc_pow2(uint32_t x) { return x <= 32 ? 32 : 2 * tc_pow2((x + 1) / 2); }
 constexpr uint32_t kTcTmemCols = tc_pow2(kTcGroups * kTcAccs * kTcN);   // the groups' accumulators (a power of 2 >= 32)
 
-// Instruction descriptor of tcgen05.mma .kind::tf32: D FP32 (bits 4-5 = 1),
-// A and B TF32 (bits 7-9, 10-12 = 2), both K-major (bits 15, 16 = 0),
-// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kFlCols >> 4) << 24);
-
-// Shared-memory matrix descriptor: start address, leading (K) and stride
-// (M / N) byte offsets in 16-byte units, descriptor version 1 (bits 46-47),
-// no swizzle (bits 61-63 = 0).
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((kTcLbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((kTcSbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
-}
+// M = 128 patches, N = both parts of t, TF32 operands, FP32 accumulator
+constexpr uint32_t kTcIdesc = tc::idesc_f32acc(tc::kFmtTF32, kFlCols, kTcN);
 
 __device__ __forceinline__ float tf32_rn(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
     return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kTcIdesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 2 x 8 FP32 columns (at taddr and taddr + kNV) of the warp's 32 tensor-memory lanes
-__device__ __forceinline__ void tc_load8x2(uint32_t taddr, float (&hi)[8], float (&lo)[8]) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr), "r"(taddr + (uint32_t)kNV)
-        : "memory");
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        hi[c] = __uint_as_float(r[c]);
-        lo[c] = __uint_as_float(r[8 + c]);
-    }
 }
 
 __device__ __forceinline__ void tma_load_bytes(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
@@ -468,10 +401,6 @@ __device__ __forceinline__ void tma_load_bytes(const CUtensorMap* map, uint64_t*
             "r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
 // Stage (group r, index j) of a block: the group's local strip kTcGroups (j / nst) + r
@@ -516,14 +445,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == kMma) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTcTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc::alloc(tmem_slot, kTcTmemCols);
     }
-    tc_fence_before();
+    tc::fence_before();
     __syncthreads();
-    tc_fence_after();
+    tc::fence_after();
     const uint32_t tmem = *tmem_slot;
     const int nst = (nc + kTcRows - 1) / kTcRows;                // stages per strip
     const int nstrip = (np + kFlCols - 1) / kFlCols;
@@ -557,17 +483,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
                     if (ok && !mbar_wait(&B[kOpready], j & 1u)) tc_fail(ok, &fail, status);
                     if (j >= kTcAccs && ok && !mbar_wait(&B[kAccfree + a], ((j / kTcAccs) - 1) & 1u))
                         tc_fail(ok, &fail, status);
-                    tc_fence_after();
+                    tc::fence_after();
                     const uint32_t ahi = smem_u32(ops_of(r)), alo = ahi + kTcAOp, bt = ahi + 2 * kTcAOp;
                     const uint32_t d = tmem + (uint32_t)((r * kTcAccs + a) * kTcN);
 #pragma unroll
                     for (int ks = 0; ks < kTcRows / 8; ++ks) {
-                        const uint64_t ah = tc_desc(ahi + ks * kTcAStep), al = tc_desc(alo + ks * kTcAStep);
-                        const uint64_t bd = tc_desc(bt + ks * kTcBStep);
-                        tc_mma(d, al, bd, ks > 0 ? 1u : 0u);   // a stage starts from zero
-                        tc_mma(d, ah, bd, 1u);
+                        const uint64_t ah = tc::smem_desc(ahi + ks * kTcAStep, kTcLbo, kTcSbo);
+                        const uint64_t al = tc::smem_desc(alo + ks * kTcAStep, kTcLbo, kTcSbo);
+                        const uint64_t bd = tc::smem_desc(bt + ks * kTcBStep, kTcLbo, kTcSbo);
+                        tc::mma<true>(d, al, bd, kTcIdesc, ks > 0 ? 1u : 0u);   // a stage starts from zero
+                        tc::mma<true>(d, ah, bd, kTcIdesc, 1u);
                     }
-                    tc_commit(&B[kMmadone]);
+                    tc::commit(&B[kMmadone]);
                 }
     } else {
         const int r = warp / kTcGroupWarps, wl = warp % kTcGroupWarps;   // group, warp in the group
@@ -609,11 +536,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
                 const int s = j - 1, a = s % kTcAccs;
                 if (ok && !mbar_wait(&B[kMmadone], s & 1u)) tc_fail(ok, &fail, status);
                 __syncwarp();
-                tc_fence_after();
+                tc::fence_after();
                 float vh[kTcDrainCols], vl[kTcDrainCols];   // the stage's sums against t's hi and lo parts
-                tc_load8x2(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((r * kTcAccs + a) * kTcN + kTcDrainCols * ch),
-                           vh, vl);
-                tc_fence_before();
+                tc::load8x2(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)((r * kTcAccs + a) * kTcN + kTcDrainCols * ch),
+                            kNV, vh, vl);
+                tc::fence_before();
                 mbar_arrive(&B[kAccfree + a]);
 #pragma unroll
                 for (int c = 0; c < kTcDrainCols; ++c) kahan_add(acc[c], comp[c], __fadd_rn(vl[c], vh[c]));
@@ -682,8 +609,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fluence_tc(const __grid_const
         __syncthreads();
     }
     if (warp == kMma) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols) : "memory");
+        tc::fence_after();
+        tc::dealloc(tmem, kTcTmemCols);
     }
 }
 

@@ -3,9 +3,9 @@
 // with BF16 weights and activations and FP32 accumulation, trained with
 // binary cross-entropy on LP dwell-time labels (candidate kept by the relaxed
 // LP (9) or not) and Adam.  The dense products run on the tensor cores
-// (mma.sync m16n8k16 BF16 -> FP32) through one GEMM kernel whose operands are
-// read with arbitrary strides, so the forward pass, the weight gradients
-// (X^T dZ) and the input gradients (dZ W^T) all use it.
+// (tcgen05.mma BF16 -> FP32, accumulator in tensor memory) through one GEMM
+// kernel whose operands are read with arbitrary strides, so the forward pass,
+// the weight gradients (X^T dZ) and the input gradients (dZ W^T) all use it.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -14,6 +14,7 @@
 #include <random>
 #include <vector>
 
+#include "tcgen05.cuh"
 #include "uvc_internal.cuh"
 
 struct uvc_mlp {
@@ -33,15 +34,23 @@ struct uvc_mlp {
 namespace uvc {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 32, kGemmThreads = 128;
-
-__device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
+// The GEMM on the fifth-generation tensor cores: one block per 128 x 64 tile
+// of C, accumulated in tensor memory by tcgen05.mma .kind::f16 (BF16 operands,
+// FP32 accumulator, M = 128, N = 64, K = 16 per instruction).  Per 32-wide
+// slice of K the block's threads gather the A and B tiles with the operands'
+// strides (zeros outside the matrices) into shared memory in the tensor
+// core's K-major layout (8-row x 16-byte core matrices), one thread issues the
+// two MMAs and commits them to an mbarrier, and the block waits for it before
+// the next slice overwrites the tiles; the epilogue reads the accumulator back
+// with tcgen05.ld (warp w: rows 32w..32w+31), adds the bias, applies the ReLU
+// and writes C and/or Ch.  A wait that runs out (bounded: about a second)
+// makes the block write NaN.
+constexpr int BM = 128, BN = 64, BK = 32, kGemmThreads = 128;
+constexpr uint32_t kGemmLbo = 128, kGemmSbo = 256;                  // core matrices along K, 8-row groups
+constexpr uint32_t kGemmAStep = (BM / 8) * kGemmSbo;                // one K-step (16 values) of A: 4 KB
+constexpr uint32_t kGemmBStep = (BN / 8) * kGemmSbo;                // of B: 2 KB
+constexpr uint32_t kGemmIdesc = tc::idesc_f32acc(tc::kFmtBF16, BM, BN);
+constexpr uint32_t kGemmTmemCols = BN;                              // FP32 accumulator columns
 
 // C[m][n] = sum_k A(m,k) B(k,n) (+ bias[n]) (relu), A(m,k) = Ap[m*sam + k*sak],
 // B(k,n) = Bp[k*sbk + n*sbn]; writes fp32 C (ldc) and/or bf16 Ch (ldh).
@@ -50,60 +59,86 @@ __global__ void __launch_bounds__(kGemmThreads) k_gemm(const __nv_bfloat16* __re
                                                        int64_t sbk, int64_t sbn, int M, int N, int K,
                                                        const float* __restrict__ bias, int relu, float* C,
                                                        int64_t ldc, __nv_bfloat16* Ch, int64_t ldh) {
-    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + 8];
-    __shared__ __align__(16) __nv_bfloat16 Bt[BN][BK + 8];   // B transposed: Bt[n][k]
+    __shared__ __align__(128) unsigned char As[(BK / 16) * kGemmAStep];
+    __shared__ __align__(128) unsigned char Bs[(BK / 16) * kGemmBStep];
+    __shared__ uint64_t mma_done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int fail;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1, g = lane >> 2, t4 = lane & 3;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-    float acc[2][4][4];
-    for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 4; ++b)
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    if (tid == 0) {
+        fail = 0;
+        tc::mbar_init(&mma_done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::alloc(&tmem_slot, kGemmTmemCols);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = tmem_slot;
     const __nv_bfloat16 zero = __float2bfloat16(0.f);
-    for (int k0 = 0; k0 < K; k0 += BK) {
-        for (int e = tid; e < BM * BK; e += kGemmThreads) {
-            const int r = e / BK, c = e % BK;
-            const int m = m0 + r, k = k0 + c;
-            As[r][c] = (m < M && k < K) ? Ap[(int64_t)m * sam + (int64_t)k * sak] : zero;
+    uint32_t phase = 0;
+    for (int k0 = 0; k0 < K; k0 += BK, phase ^= 1u) {
+        // A: 128 rows x 4 chunks of 8 K-values, B: 64 rows x 4 chunks; one 16-byte store per chunk
+        for (int e = tid; e < (BM + BN) * (BK / 8); e += kGemmThreads) {
+            const bool isA = e < BM * (BK / 8);
+            const int f = isA ? e : e - BM * (BK / 8);
+            const int row = f / (BK / 8), ch = f % (BK / 8);   // row (m or n), chunk of 8 along K
+            __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + ch * 8 + q;
+                if (isA) {
+                    const int m = m0 + row;
+                    v[q] = (m < M && k < K) ? Ap[(int64_t)m * sam + (int64_t)k * sak] : zero;
+                } else {
+                    const int n = n0 + row;
+                    v[q] = (n < N && k < K) ? Bp[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
+                }
+            }
+            const uint32_t off = (uint32_t)(ch >> 1) * (isA ? kGemmAStep : kGemmBStep) + (uint32_t)(row >> 3) * kGemmSbo +
+                                 (uint32_t)(ch & 1) * kGemmLbo + (uint32_t)(row & 7) * 16u;
+            *reinterpret_cast<uint4*>((isA ? As : Bs) + off) = *reinterpret_cast<const uint4*>(v);
         }
-        for (int e = tid; e < BN * BK; e += kGemmThreads) {
-            const int r = e / BK, c = e % BK;   // r = n, c = k
-            const int n = n0 + r, k = k0 + c;
-            Bt[r][c] = (n < N && k < K) ? Bp[(int64_t)k * sbk + (int64_t)n * sbn] : zero;
-        }
+        tc::fence_proxy_async();
         __syncthreads();
-        for (int kk = 0; kk < BK; kk += 16) {
-            uint32_t af[2][4], bf[4][2];
-            for (int mi = 0; mi < 2; ++mi) {
-                const int r = wm * 32 + mi * 16 + g, c = kk + t4 * 2;
-                af[mi][0] = *reinterpret_cast<const uint32_t*>(&As[r][c]);
-                af[mi][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c]);
-                af[mi][2] = *reinterpret_cast<const uint32_t*>(&As[r][c + 8]);
-                af[mi][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][c + 8]);
-            }
-            for (int ni = 0; ni < 4; ++ni) {
-                const int n = wn * 32 + ni * 8 + g, c = kk + t4 * 2;
-                bf[ni][0] = *reinterpret_cast<const uint32_t*>(&Bt[n][c]);
-                bf[ni][1] = *reinterpret_cast<const uint32_t*>(&Bt[n][c + 8]);
-            }
-            for (int mi = 0; mi < 2; ++mi)
-                for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni]);
+        if (tid == 0) {
+            tc::fence_after();
+#pragma unroll
+            for (int ks = 0; ks < BK / 16; ++ks)
+                tc::mma<false>(tmem, tc::smem_desc(tc::smem_u32(As) + ks * kGemmAStep, kGemmLbo, kGemmSbo),
+                               tc::smem_desc(tc::smem_u32(Bs) + ks * kGemmBStep, kGemmLbo, kGemmSbo), kGemmIdesc,
+                               (k0 > 0 || ks > 0) ? 1u : 0u);
+            tc::commit(&mma_done);
         }
+        // the MMAs have read the tiles before the next slice overwrites them
+        if (!fail && !tc::mbar_wait(&mma_done, phase)) fail = 1;
         __syncthreads();
     }
-    for (int mi = 0; mi < 2; ++mi)
-        for (int ni = 0; ni < 4; ++ni)
-            for (int h = 0; h < 2; ++h)
-                for (int q = 0; q < 2; ++q) {
-                    const int m = m0 + wm * 32 + mi * 16 + g + 8 * h;
-                    const int n = n0 + wn * 32 + ni * 8 + t4 * 2 + q;
-                    if (m >= M || n >= N) continue;
-                    float v = acc[mi][ni][2 * h + q];
-                    if (bias) v += bias[n];
-                    if (relu) v = fmaxf(v, 0.f);
-                    if (C) C[(int64_t)m * ldc + n] = v;
-                    if (Ch) Ch[(int64_t)m * ldh + n] = __float2bfloat16(v);
-                }
+    tc::fence_after();
+    const int m = m0 + 32 * warp + lane;
+#pragma unroll
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+        float v[16];
+        tc::load16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const int n = n0 + c0 + c;
+            if (m >= M || n >= N) continue;
+            float x = K > 0 ? v[c] : 0.f;
+            if (bias) x += bias[n];
+            if (relu) x = fmaxf(x, 0.f);
+            if (fail) x = __int_as_float(0x7fc00000);
+            if (C) C[(int64_t)m * ldc + n] = x;
+            if (Ch) Ch[(int64_t)m * ldh + n] = __float2bfloat16(x);
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after();
+        tc::dealloc(tmem, kGemmTmemCols);
+    }
 }
 
 void gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak, const __nv_bfloat16* B, int64_t sbk, int64_t sbn, int M,
