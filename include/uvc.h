@@ -306,15 +306,16 @@ int uvc_fluence_streamed(const uvc_scene* scene, const float* cand, int64_t nc, 
  * already holds all the device memory it may use, or a control loop that
  * forbids allocation after start-up because an allocation can block,
  * synchronise the device or fail mid-run.  This call allocates nothing: the
- * per-chunk partial sums go to one fixed device array of 64 MiB that the
- * library defines (every GPU that loads the library holds it until exit).
+ * warps' task counter (256 bytes) and the per-chunk partial sums go to one
+ * fixed device array of 64 MiB that the library defines (every GPU that loads
+ * the library holds it until exit).
  * The paper has no counterpart; this is an interface convenience.
  *
  *   Same arguments, result and determinism as uvc_fluence_streamed; fewer
- *   candidate chunks may be used (at most 64 MiB / (4 * nvec * np) of them),
- *   so the last bits of mu may differ from uvc_fluence_streamed's.
- *   Limit: 4 * nvec * np must not exceed 64 MiB (67,108,864 bytes), else
- *   UVC_E_SCRATCH and nothing is launched.
+ *   candidate chunks may be used (at most (64 MiB - 256) / (4 * nvec * np) of
+ *   them), so the last bits of mu may differ from uvc_fluence_streamed's.
+ *   Limit: 4 * nvec * np must not exceed 64 MiB less 256 bytes (67,108,608
+ *   bytes), else UVC_E_SCRATCH and nothing is launched.
  *   The first call on a device looks up the array's device address for that
  *   device (cudaGetSymbolAddress) and caches it, keyed on the device and its
  *   current context (after a cudaDeviceReset the first call in the new

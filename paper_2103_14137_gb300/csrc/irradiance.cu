@@ -74,12 +74,17 @@ __global__ void __launch_bounds__(kThreads, UVC_IRR_MIN_BLOCKS) k_irradiance(Sce
 // E values of up to kStreamedBlock candidates are staged in shared memory,
 // multiplied by the dwell times and added to the chunk's partial sums
 // partial[s][v][j].  20 candidates per stage keeps a K = 8 lamp's block within
-// a third of an SM's shared memory (three resident blocks).
+// a third of an SM's shared memory (three resident blocks).  A task is a whole
+// chunk of candidates for 32 patches, and its cost varies with the geometry
+// around the patches, so the warps take tasks from a counter (next_task,
+// zeroed before the launch) as they finish instead of a fixed share each;
+// every task's sums are the same whichever warp takes it.
 constexpr int kStreamedBlock = 20;
 template <bool WEDGE>
 __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(SceneView S, const float* __restrict__ cand, int nc,
                                                        LampDev L, const float* __restrict__ t, int nvec,
-                                                       float* __restrict__ partial, int nsplit, int chunk) {
+                                                       float* __restrict__ partial, int nsplit, int chunk,
+                                                       unsigned long long* next_task) {
     extern __shared__ __align__(16) int smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int* stack = smem + warp * S.stack_cap;
@@ -88,9 +93,13 @@ __global__ void __launch_bounds__(kThreads, UVC_STREAMED_MIN_BLOCKS) k_streamed(
     WedgeSmem ws;
     if (WEDGE) ws = wedge_smem(after_stacks + sizeof(float) * kWarpsPerBlock * kStreamedBlock * 32, L.K, warp);
     const int njb = (S.np + 31) >> 5;
-    const int64_t ntask = (int64_t)nsplit * njb;
-    for (int64_t task = (int64_t)blockIdx.x * kWarpsPerBlock + warp; task < ntask;
-         task += (int64_t)gridDim.x * kWarpsPerBlock) {
+    const unsigned long long ntask = (unsigned long long)nsplit * (unsigned long long)njb;
+    for (;;) {
+        unsigned long long tk = 0;
+        if (lane == 0) tk = atomicAdd(next_task, 1ull);
+        tk = __shfl_sync(0xffffffffu, tk, 0);
+        if (tk >= ntask) break;
+        const int64_t task = (int64_t)tk;
         const int s = (int)(task / njb), jb = (int)(task % njb);
         const int j = jb * 32 + lane;
         const PatchLane P = load_patch(S, j);
@@ -163,15 +172,20 @@ int streamed_grid(const SceneView& S, const LampDev& lamp, int* grid) {
     return rc;
 }
 
-void launch_streamed(int grid, const SceneView& S, const float* cand, int64_t nc, const LampDev& lamp,
-                     const float* t, int32_t nvec, float* partial, int64_t nsplit, int chunk, cudaStream_t stream) {
+// next_task: a device counter the launch zeroes first (the warps' task counter).
+int launch_streamed(int grid, const SceneView& S, const float* cand, int64_t nc, const LampDev& lamp,
+                    const float* t, int32_t nvec, float* partial, int64_t nsplit, int chunk,
+                    unsigned long long* next_task, cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(next_task, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return status_from_cuda(e);
     const size_t smem = streamed_smem(S, lamp);
     if (lamp.wedge)
         k_streamed<true><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit,
-                                                           chunk);
+                                                           chunk, next_task);
     else
         k_streamed<false><<<grid, kThreads, smem, stream>>>(S, cand, (int)nc, lamp, t, nvec, partial, (int)nsplit,
-                                                            chunk);
+                                                            chunk, next_task);
+    return UVC_OK;
 }
 
 template <bool COUNT>
@@ -246,19 +260,26 @@ int fluence_streamed(const uvc_scene* sc, const float* cand, int64_t nc, const L
     nsplit = std::max<int64_t>(1, std::min(nsplit, cap));
     const int chunk = (int)((nc + nsplit - 1) / nsplit);
     nsplit = (nc + chunk - 1) / chunk;
-    float* partial = nullptr;
-    if (cudaMallocAsync(&partial, sizeof(float) * (size_t)nsplit * nvec * S.np, stream) != cudaSuccess) {
+    // the task counter in the first 256 bytes, the partial sums after it
+    char* block = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&block), 256 + sizeof(float) * (size_t)nsplit * nvec * S.np,
+                        stream) != cudaSuccess) {
         cudaGetLastError();
         return UVC_E_NOMEM;
     }
+    float* partial = reinterpret_cast<float*>(block + 256);
     const int64_t ntask = nsplit * njb;
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk, stream);
-    const int64_t total = (int64_t)nvec * S.np;
-    k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
-    cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(partial, stream);
-    return status_from_cuda(e);
+    rc = launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk,
+                         reinterpret_cast<unsigned long long*>(block), stream);
+    cudaError_t e = cudaSuccess;
+    if (rc == UVC_OK) {
+        const int64_t total = (int64_t)nvec * S.np;
+        k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(block, stream);
+    return rc != UVC_OK ? rc : status_from_cuda(e);
 }
 
 }  // namespace uvc
@@ -277,6 +298,7 @@ namespace uvc {
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;   // 64 MiB
+constexpr size_t kNoAllocPartialBytes = kNoAllocScratchBytes - 256;   // after the task counter
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float)];
 
 // Device address of g_noalloc_scratch, resolved once per device and context
@@ -351,10 +373,13 @@ int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc,
                              int32_t nvec, float* mu, cudaStream_t stream) {
     if (sc->np == 0) return UVC_OK;
     const size_t per_split = sizeof(float) * (size_t)nvec * (size_t)sc->np;
-    if (per_split > kNoAllocScratchBytes) return UVC_E_SCRATCH;
-    float* partial = nullptr;
-    int rc = noalloc_scratch(&partial);
+    if (per_split > kNoAllocPartialBytes) return UVC_E_SCRATCH;
+    float* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
     if (rc != UVC_OK) return rc;
+    // the task counter in the first 256 bytes, the partial sums after it
+    unsigned long long* next_task = reinterpret_cast<unsigned long long*>(scratch);
+    float* partial = scratch + 256 / sizeof(float);
     SceneView S = view_of(sc);
     if (nc == 0) return status_from_cuda(cudaMemsetAsync(mu, 0, per_split, stream));
     const int njb = (S.np + 31) / 32;
@@ -364,13 +389,14 @@ int fluence_streamed_noalloc(const uvc_scene* sc, const float* cand, int64_t nc,
     const int64_t want = 8 * (int64_t)grid * kWarpsPerBlock;
     int64_t nsplit = (want + njb - 1) / njb;
     nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (nc + 31) / 32));
-    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (int64_t)(kNoAllocScratchBytes / per_split)));
+    nsplit = std::max<int64_t>(1, std::min<int64_t>(nsplit, (int64_t)(kNoAllocPartialBytes / per_split)));
     const int chunk = (int)((nc + nsplit - 1) / nsplit);
     nsplit = (nc + chunk - 1) / chunk;
     const int64_t ntask = nsplit * njb;
     if ((int64_t)grid * kWarpsPerBlock > ntask) grid = (int)((ntask + kWarpsPerBlock - 1) / kWarpsPerBlock);
     // every partial is written before it is read, so the array needs no clearing
-    launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk, stream);
+    rc = launch_streamed(grid, S, cand, nc, lamp, t, nvec, partial, nsplit, chunk, next_task, stream);
+    if (rc != UVC_OK) return rc;
     const int64_t total = (int64_t)nvec * S.np;
     k_reduce_partials<<<(int)((total + 255) / 256), 256, 0, stream>>>(partial, (int)nsplit, nvec, S.np, mu);
     return status_from_cuda(cudaGetLastError());

@@ -407,7 +407,7 @@ def fluence_streamed_noalloc(scene: Scene, cand, lamp: Lamp, t, mu, stream=None)
     the call (their allocator holds the device, or allocation is forbidden
     after start-up): the library's partial sums go to its fixed 64 MiB device
     array.  `mu` (nvec, np) must be supplied by the caller; nothing is
-    allocated here.  Raises UvcError(UVC_E_SCRATCH) when 4*nvec*np > 64 MiB."""
+    allocated here.  Raises UvcError(UVC_E_SCRATCH) when 4*nvec*np > 64 MiB - 256 B."""
     nvec, nc = t.shape
     L = lamp._c()
     rc = library().uvc_fluence_streamed_noalloc(scene.handle, _dev(cand, torch.float32, "cand", (nc, 3)), nc,
