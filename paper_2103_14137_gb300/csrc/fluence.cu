@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(256, 1) k_fluence_tma(const __grid_constant__ 
 // per strip of 128 patches, D (128 patches x 16 vectors, FP32, in tensor
 // memory) takes A_strip^T (128 x nc) times t^T (nc x 16).  TF32 keeps 10 of
 // FP32's 23 fraction bits, so every operand value x is split as x = hi + lo,
-// hi = tf32(x) and lo = tf32(x - hi) (round to nearest), which leaves
+// hi = tf32(x) and lo = tf32(x - hi) (cvt.rna: nearest, ties away), which leaves
 // |x - hi - lo| <= 2^-22 |x|; D takes hi*hi + hi*lo + lo*hi + lo*lo, products
 // of TF32 values being exact in FP32 (one MMA takes a part of A times both
 // parts of t).  Each stage of 32 candidate rows is accumulated from zero into
